@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the KDE-PIC hot path on one GB300 (or N independent replicas).
+
+Workload (default, `--workload landau`): the Landau-damping run with particle-
+wise widths -- N = 2^20 electrons, Ng = 256 nodes, L = 4 pi (k = 0.5),
+density 1 + 0.05 cos(kx), Maxwellian v_th = 1, dt = 0.1; every 50 steps the
+width is re-selected by leave-one-out CV over 64 candidates log-spaced in
+[1, 1e4] and Silverman's particle-wise widths (alpha = 0.5) are recomputed.
+One benchmark step is one such 50-step period: CV pair sums + integral term +
+leave-one-out pass + adaptive widths, then 50 x (sort, deposit, Poisson,
+gather + push + field energy).  All of it runs in libkdepic's CUDA kernels.
+
+`value` counts the definition pairs of the deposit and gather, 2 N Ng per PIC
+step, divided by the device time of the whole period (CV included).  The CV
+pair throughput is reported beside it.  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "deposit+gather particle·node pairs/s; CV pairs/s; serve p50/p99 vs plain"
+UNIT = "pairs/s"
+
+LANDAU = dict(N=1 << 20, Ng=256, L=4 * math.pi, dt=0.1, period=50, n_cand=64, kmin_c=1.0, kmax_c=1e4, alpha=0.5,
+              kappa_min=1.0, kappa_max=1e5, seed=0)
+
+
+def workload_name(w):
+    return "landau_damping N=2^20 Ng=256 dt=0.1 widths every 50 steps (CV over 64 candidates in [1,1e4], alpha=0.5)"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the CV pair kernel: for every candidate, the unordered
+# pairs inside its truncation radius (kernel >= 2^-24 of its peak)
+# ---------------------------------------------------------------------------
+def cv_inradius_pairs(u_np, cands):
+    th = np.sort(u_np.astype(np.float64)) * (2 * math.pi / 2 ** 32)
+    N = th.size
+    ext = np.concatenate([th, th + 2 * math.pi])
+    total = 0
+    for k in cands:
+        s2 = 24.0 * math.log(2.0) / (2.0 * k)
+        if s2 >= 1.0:
+            total += N * (N - 1) // 2
+            continue
+        r = 2.0 * math.asin(math.sqrt(s2))
+        hi = np.searchsorted(ext, th + r, side="right")
+        cnt = np.minimum(hi - np.arange(N) - 1, N - 1)
+        total += int(cnt.sum()) // 2 if r < math.pi else N * (N - 1) // 2
+    return total
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except ValueError:
+            return {}
+    return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------
+def oracle_sample(n_steps=10, N=1 << 12):
+    import kde_inputs as I
+    import oracle as O
+    w = LANDAU
+    O.build()
+    u, v = I.landau_load(w["seed"], N, w["L"], 0.05, 1.0)
+    x = I.from_fixed(u, w["L"])
+    cand = I.log_candidates(w["kmin_c"], w["kmax_c"], w["n_cand"])
+    t0 = time.perf_counter()
+    O.pic_run(x, v.astype(np.float32), w["L"], w["Ng"], w["dt"], n_steps, kappa=np.ones(N), width_every=w["period"],
+              cands=cand, alpha=w["alpha"], kmin=w["kappa_min"], kmax=w["kappa_max"])
+    dt = time.perf_counter() - t0
+    pairs = 2.0 * N * w["Ng"] * n_steps
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return pairs / dt, dt, cores, "%d particles, Ng=%d, %d PIC steps incl. one CV width update over %d candidates" % (
+        N, w["Ng"], n_steps, w["n_cand"])
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(2)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt, cores, sample = oracle_sample(10)
+        vals.append(v)
+        times.append(dt)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(LANDAU), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import kde_inputs as I
+    import paper_1804_11174_gb300 as kp
+    from paper_1804_11174_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = "cuda:%d" % local_rank
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(dev))
+
+    w = LANDAU
+    N, Ng, L, dt, P = w["N"], w["Ng"], w["L"], w["dt"], w["period"]
+    cand = I.log_candidates(w["kmin_c"], w["kmax_c"], w["n_cand"])
+    ctx = kp.Context(local_rank)
+    ctx.reserve(N, Ng, w["n_cand"])
+    # each rank simulates its own realisation (independent replicas, weak scaling)
+    u0, v0 = I.landau_load(w["seed"] + rank, N, L, 0.05, 1.0)
+    u0_t = torch.from_numpy(u0.view(np.int32)).to(dev)
+    v0_t = torch.from_numpy(v0.astype(np.float32)).to(dev)
+    total_steps = P * (args.warmup + args.steps) + P
+    st = kp.PicState(u0_t.clone(), v0_t.clone(), L, Ng, dt, kappa=torch.ones(N, device=dev),
+                     ids=torch.arange(N, dtype=torch.int32, device=dev), width_every=P, cand=cand,
+                     alpha=w["alpha"], kappa_min=w["kappa_min"], kappa_max=w["kappa_max"], max_steps=total_steps)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
+
+    for _ in range(args.warmup):
+        ctx.pic_step(st, P)
+    torch.cuda.synchronize()
+
+    # algorithmic CV work of each timed period (positions at the start of the period)
+    step_ms = []
+    cv_alg = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ctx.profile_enable(True)
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        if rank == 0:
+            cv_alg.append(st.u.cpu().numpy().view(np.uint32).copy())
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.pic_step(st, P)
+        b.record()
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    cv_ms, cv_n = ctx.profile_read("cv_pairs")
+    prof = {k: ctx.profile_read(k) for k in ("deposit", "gather", "sort", "poisson", "cv_grid", "cv_loo")}
+    _, launches = ctx.profile_read("all")
+    ctx.profile_enable(False)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    t_step = float(np.sum(step_ms)) / args.steps  # ms of device time per period
+    if dist:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    pairs_dg = 2.0 * N * Ng * P  # deposit + gather definition pairs per period
+    value = world * pairs_dg / (t_step * 1e-3)
+    cv_def_pairs = w["n_cand"] * N * (N - 1)  # ordered pairs i != j per candidate
+    cv_pairs_per_s = cv_def_pairs / (cv_ms / max(cv_n, 1) * 1e-3) if cv_n else None
+
+    # ---- e2e: the same period through the public API from pinned host buffers ----
+    e2e = None
+    if True:
+        hu = torch.from_numpy(u0.view(np.int32)).pin_memory()
+        hv = torch.from_numpy(v0.astype(np.float32)).pin_memory()
+        hk = torch.ones(N).pin_memory()
+        out_u = torch.empty(N, dtype=torch.int32).pin_memory()
+        out_v = torch.empty(N, dtype=torch.float32).pin_memory()
+        out_w = torch.empty(P, dtype=torch.float64).pin_memory()
+        e2e_steps = max(1, min(args.steps, 3))
+        st2 = kp.PicState(torch.empty(N, dtype=torch.int32, device=dev), torch.empty(N, device=dev), L, Ng, dt,
+                          kappa=torch.empty(N, device=dev), width_every=P, cand=cand, alpha=w["alpha"],
+                          kappa_min=w["kappa_min"], kappa_max=w["kappa_max"], max_steps=P)
+        torch.cuda.synchronize()
+        e_ms = []
+        for _ in range(e2e_steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            st2.u.copy_(hu, non_blocking=True)
+            st2.v.copy_(hv, non_blocking=True)
+            st2.kappa.copy_(hk, non_blocking=True)
+            st2.c.step = 0
+            ctx.pic_step(st2, P)
+            out_u.copy_(st2.u, non_blocking=True)
+            out_v.copy_(st2.v, non_blocking=True)
+            out_w.copy_(st2.energy[:P], non_blocking=True)
+            b.record()
+            b.synchronize()
+            e_ms.append(a.elapsed_time(b))
+        e_t = float(np.mean(e_ms))
+        e2e = {"value": world * pairs_dg / (e_t * 1e-3), "unit": UNIT, "h2d_bytes_per_step": N * 12,
+               "d2h_bytes_per_step": N * 8 + P * 8, "ms_per_step": e_t}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (CV pair sums, bound by the exp2 unit) ----
+    alg = [cv_inradius_pairs(u, cand) for u in cv_alg]
+    alg_per_launch = float(np.mean(alg))
+    cv_launch_ms = cv_ms / max(cv_n, 1)
+    achieved = alg_per_launch / (cv_launch_ms * 1e-3)
+    ms_p, ops_p = ctx.probe_exp2(1 << 14)
+    ex2_peak = ops_p / (ms_p * 1e-3)
+    fm_ms, fm_ops = ctx.probe_fma(1 << 14)
+    roof = {"bound": "alu", "kernel": "cv_pairs_kernel", "achieved": achieved / 1e12, "peak": ex2_peak / 1e12,
+            "unit": "Tex2/s", "frac": achieved / ex2_peak, "traffic": None,
+            "peak_source": "measured ex2.approx.ftz.f32 stream on this GPU (kde_probe_exp2)",
+            "fma_peak_tflops": 2.0 * fm_ops / (fm_ms * 1e-3) / 1e12,
+            "algorithmic_units_per_launch": alg_per_launch,
+            "unit_def": "one exp2 per (unordered pair inside the candidate's truncation radius, candidate)",
+            "avg_launch_ms": cv_launch_ms, "launches": cv_n}
+
+    try:
+        cpu_v, cpu_dt, cores, sample = oracle_sample(5, 1 << 12)
+        cpu = {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": cpu_dt}
+    except Exception as e:  # the oracle needs gcc; report its absence instead of failing the bench
+        cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "unavailable: %s" % e}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(w), "N": N, "Ng": Ng, "dt": dt, "pic_steps_per_step": P,
+                   "n_cand": w["n_cand"], "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "cv_pairs_per_s": cv_pairs_per_s,
+        "cv_ms_per_step": cv_launch_ms,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "wall_s": wall,
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

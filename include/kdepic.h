@@ -1,0 +1,215 @@
+/*
+ * kdepic.h -- C ABI of the GB300 (sm_103a) KDE particle-in-cell hot path.
+ *
+ * Method: Wu & Qin, "Reducing Noise for PIC Simulations Using Kernel Density
+ * Estimation Algorithm" (arXiv 1804.11174).  The library deposits particle
+ * charge on a 1D periodic grid with von Mises shape functions (Sec. II.A,
+ * Eq. vonMises; Eq. kde), gathers the field back through the same kernels,
+ * selects widths by leave-one-out cross-validation (Sec. II.B, Eq. cv_def),
+ * adapts them per particle (Sec. II.C) and advances an electrostatic
+ * leap-frog PIC cycle (Sec. III.A).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Domain x in [0, L) is periodic; theta = 2 pi x / L.  Positions are passed
+ *   as 32-bit periodic fixed-point codes u = floor(x / L * 2^32) (uint32).
+ *   Grid node g sits at x_g = g L / Ng.
+ * - Kernel: K_kappa(theta) = exp(kappa (cos theta - 1)) / (2 pi I0e(kappa)),
+ *   I0e(kappa) = exp(-kappa) I0(kappa).  kappa must be finite, in (0, 1e6].
+ * - Pointers: every array argument is a DEVICE pointer unless its comment says
+ *   "host".  The caller owns every buffer; the library never frees or keeps a
+ *   caller pointer past the call (pic_step updates the caller's state arrays
+ *   in place).  The context owns only its internal workspace.
+ * - Precision: arrays documented as `real` are float32 by default and float64
+ *   when the call's flags include KDE_F64.  Positions are always uint32.
+ * - Ordering: calls enqueue work on the context's stream and return without
+ *   synchronising, except those that return host values (kde_cv, kde_sync).
+ * - Errors: every call returns a kde_status.  Arguments are validated on the
+ *   host before anything is launched; on failure nothing is enqueued and
+ *   kde_last_error() describes the problem.  Device-side problems (a width out
+ *   of range, a wait that ran out of iterations) set a status word on the
+ *   device that the next kde_sync() (or kde_cv) reports as KDE_EDEVICE.
+ * - Workspace: the first call at a new problem size may grow the context's
+ *   workspace with cudaMalloc.  kde_reserve() grows it up front (do that before
+ *   capturing calls into a CUDA graph).
+ * - Determinism: for fixed inputs and sizes every result is bitwise
+ *   reproducible (fixed summation orders; the deposit combines per-chunk sums
+ *   with integer atomics).
+ */
+#ifndef KDEPIC_H
+#define KDEPIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kde_ctx kde_ctx;
+typedef int kde_status;
+
+#define KDE_OK 0
+#define KDE_EINVAL 1   /* invalid argument (host-side validation) */
+#define KDE_ENOMEM 2   /* workspace allocation failed */
+#define KDE_ECUDA 3    /* a CUDA runtime call failed */
+#define KDE_EDEVICE 4  /* a kernel reported a problem through the device status word */
+#define KDE_ENOTSUP 5  /* combination of options not supported */
+
+/* flags */
+#define KDE_F64 0x1u         /* real arrays are float64 and arithmetic is FP64 */
+#define KDE_POISSON_FD 0x2u  /* finite-difference Poisson (Sec. III.A) instead of spectral */
+#define KDE_CV_SCALE 0x4u    /* kde_cv: candidates scale per-particle widths kappa_rel */
+
+/* Maximum grid size accepted by deposit / gather / Poisson / pic_step. */
+#define KDE_MAX_NG 4096
+
+/* Create a context bound to `device` and `stream` (a cudaStream_t; NULL selects
+ * the legacy default stream).  *out receives the context; destroy it with
+ * kde_destroy.  Returns KDE_ECUDA if the device cannot be used. */
+kde_status kde_create(kde_ctx **out, int device, void *stream);
+
+/* Release the context and its workspace (synchronises its stream first). */
+kde_status kde_destroy(kde_ctx *ctx);
+
+/* Rebind the context to another stream of the same device. */
+kde_status kde_set_stream(kde_ctx *ctx, void *stream);
+
+/* Human-readable description of the last failure on this context (never NULL). */
+const char *kde_last_error(const kde_ctx *ctx);
+
+/* Wait for the context's stream and report the device status word
+ * (KDE_EDEVICE with a description if a kernel flagged a problem; the word is
+ * cleared by this call). */
+kde_status kde_sync(kde_ctx *ctx);
+
+/* Grow the workspace for problems of up to N particles, grids of up to Ng nodes
+ * and up to n_cand CV candidates, so that later calls allocate nothing. */
+kde_status kde_reserve(kde_ctx *ctx, int64_t N, int32_t Ng, int32_t n_cand);
+
+/* Position encoding: u_i = floor(x_i / L * 2^32) after wrapping x_i into [0, L).
+ * x: device float64[N]; u_out: device uint32[N].  N >= 0, L > 0. */
+kde_status kde_pack_positions(kde_ctx *ctx, const double *x, int64_t N, double L, uint32_t *u_out);
+
+/* Deposit (Eq. kde at the grid nodes; per-particle widths as in Sec. II.C):
+ *   rho_g = sum_i w_i (2 pi / L) K_{kappa_i}(theta_g - theta_i),  g = 0..Ng-1.
+ * u: uint32[N] positions in any order.  kappa: real[N] per-particle widths, or
+ * NULL to use kappa_uniform for every particle.  weight: real[N] non-negative
+ * particle weights, or NULL for w_i = L / N (mean density 1).  rho_out:
+ * real[Ng].  Terms below 2^-24 of a kernel's peak may be skipped (truncated
+ * support).  N >= 0 (N = 0 gives zeros), 1 <= Ng <= KDE_MAX_NG, L > 0.
+ * Flags: KDE_F64. */
+kde_status kde_deposit(kde_ctx *ctx, const uint32_t *u, const void *kappa, double kappa_uniform,
+                       const void *weight, int64_t N, int32_t Ng, double L, void *rho_out,
+                       uint32_t flags);
+
+/* Poisson solve on the periodic grid for the total charge density
+ *   rho_total_g = background + charge * rho_g :
+ * spectral (default): E_m = rho_m / (i k_m), k_m = 2 pi m / L, E_0 = 0 and, for
+ * even Ng, E_{Ng/2} = 0; KDE_POISSON_FD: the finite-difference scheme of
+ * Sec. III.A, whose Fourier symbol replaces k_m by (2/dx) tan(pi m / Ng).
+ * rho: real[Ng]; E_out: real[Ng] (must not alias rho).  Also writes the field
+ * energy 1/2 sum_g E_g^2 dx to energy_out (device float64[1]) if not NULL.
+ * Flags: KDE_F64, KDE_POISSON_FD. */
+kde_status kde_poisson(kde_ctx *ctx, const void *rho, int32_t Ng, double L, double charge,
+                       double background, void *E_out, double *energy_out, uint32_t flags);
+
+/* Gather through the deposit's kernels:
+ *   out_i = sum_g (2 pi / Ng) K_{kappa_i}(theta_g - theta_i) field_g.
+ * u: uint32[N] (any order); kappa: real[N] or NULL (kappa_uniform); field:
+ * real[Ng]; out: real[N] in the order of u.  Flags: KDE_F64. */
+kde_status kde_gather(kde_ctx *ctx, const uint32_t *u, const void *kappa, double kappa_uniform,
+                      int64_t N, const void *field, int32_t Ng, double L, void *out,
+                      uint32_t flags);
+
+/* Leave-one-out cross-validation over candidate widths (Sec. II.B, Eq. cv_def):
+ *   CV(c) = int fhat_c^2 dx - (2 / (n (n-1))) sum_i sum_{j != i} K_{kappa_jc}(x_i - x_j),
+ * in x units (the kernel in x units is (2 pi / L) K).  Widths for candidate c:
+ * kappa_jc = cand[c] (uniform), or cand[c] * kappa_rel[j] with KDE_CV_SCALE.
+ * u: uint32[N] (any order), N >= 2; kappa_rel: float32[N] (KDE_CV_SCALE only);
+ * cand: HOST float64[n_cand], 1 <= n_cand <= 256, each kappa in (0, 1e6];
+ * cv_out: HOST float64[n_cand]; argmin_out: HOST int32 (smallest index on exact
+ * ties), may be NULL; loo_out: float32[N] or NULL -- the leave-one-out density
+ * (2 pi/L)(1/(n-1)) sum_{j != i} K_{kappa_j*}(theta_i - theta_j) at the selected
+ * candidate, in the order of u.  Pair sums run in FP32 with per-tile FP64
+ * accumulation; the integral term is an exact trapezoid sum on a grid fine
+ * enough for the narrowest candidate; the final combination is FP64.  Pairs
+ * whose kernel value is below 2^-24 of the peak may be skipped.  Synchronises.
+ * Flags: KDE_CV_SCALE. */
+kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64_t N, double L,
+                  const double *cand, int32_t n_cand, double *cv_out, int32_t *argmin_out,
+                  float *loo_out, uint32_t flags);
+
+/* Particle-wise widths (Sec. II.C, Silverman): with the pilot density at the
+ * CV width kappa_star, f~_i = ((n-1) loo_i + K_{kappa*}(0)) / n (x units),
+ * log g = mean_i log f~_i, lambda_i = (f~_i / g)^(-alpha) and
+ * kappa_i = kappa_star / lambda_i^2, clamped to [kappa_min, kappa_max].
+ * loo: float32[N] as returned by kde_cv; kappa_out: float32[N].  The log-mean
+ * is reduced in FP64.  N >= 2. */
+kde_status kde_adapt_widths(kde_ctx *ctx, const float *loo, int64_t N, double L, double kappa_star,
+                            double alpha, double kappa_min, double kappa_max, float *kappa_out);
+
+/* State of one electrostatic PIC run (Sec. III.A).  The caller owns all arrays.
+ * pic_step reorders particles (u, v, kappa and id move together) by cell. */
+typedef struct pic_state {
+    uint32_t *u;          /* device uint32[N] positions (in/out) */
+    void *v;              /* device real[N] velocities v^{n-1/2} (in/out) */
+    void *kappa;          /* device real[N] per-particle widths (in/out), or NULL for uniform */
+    void *kappa_norm;     /* device real[N] scratch kept equal to 1/(2 pi I0e(kappa_i)) by the
+                             library; required when kappa != NULL */
+    uint32_t *id;         /* device uint32[N] particle labels moved with the particles, or NULL */
+    int64_t N;            /* particles, >= 1 */
+    int32_t Ng;           /* grid nodes, 1..KDE_MAX_NG */
+    double L, dt;         /* domain length and time step */
+    double qm;            /* charge-to-mass ratio of the particles (-1 for electrons) */
+    double charge;        /* charge per unit weight of the particles (-1 for electrons) */
+    double background;    /* uniform neutralising background density (ions), usually 1 */
+    double kappa_uniform; /* width when kappa == NULL (updated by the width schedule) */
+    int32_t width_every;  /* > 0: run CV + width update every `width_every` steps */
+    const double *cand;   /* HOST float64[n_cand] uniform-width candidates for the schedule */
+    int32_t n_cand;
+    double alpha;         /* Silverman sensitivity (0 = keep the uniform CV width) */
+    double kappa_min, kappa_max; /* clamp for particle-wise widths */
+    double *energy;       /* device float64[steps] field energy per step (indexed by step), or NULL */
+    double *kappa_star;   /* device float64[steps] CV width in force per step, or NULL */
+    int64_t step;         /* step counter (in/out); step 0 gets a half velocity kick */
+    uint32_t flags;       /* KDE_F64, KDE_POISSON_FD; PIC_NO_BACKSTEP */
+} pic_state;
+
+#define PIC_NO_BACKSTEP 0x100u /* do not halve the first kick at step 0 */
+
+/* Advance the run by n_steps leap-frog steps.  Each step: (width update when
+ * width_every > 0 and step % width_every == 0), counting sort by cell,
+ * deposit, Poisson, field energy, gather, push.  At step 0 the velocity kick
+ * is halved (v^{1/2} = v^0 + (q/m) E^0 dt / 2) unless PIC_NO_BACKSTEP.
+ * Stream-ordered; no host synchronisation. */
+kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps);
+
+/* Damping rate (Sec. III.B) from a field-energy history on the HOST: half the
+ * slope of ln W through the first two strict local maxima at steps >= 1.
+ * energy: HOST float64[n]; gamma_out: HOST.  Returns KDE_EINVAL if fewer than
+ * two maxima exist. */
+kde_status kde_damping_rate(const double *energy, int64_t n, double dt, double *gamma_out);
+
+/* Measurement support: throughput probes used to derive the roofline of the
+ * pair kernels (not part of the method).  Each launches a dependency-free
+ * stream of `iters` operations per thread on all SMs and writes the elapsed
+ * device time in ms to *ms_out (synchronises). */
+kde_status kde_probe_exp2(kde_ctx *ctx, int64_t iters, double *ms_out, int64_t *ops_out);
+kde_status kde_probe_fma(kde_ctx *ctx, int64_t iters, double *ms_out, int64_t *ops_out);
+
+/* Measurement support: while enabled, the library records CUDA events on its
+ * stream around the launches of selected kernels and counts every kernel it
+ * launches.  kde_profile_enable(ctx, on) synchronises, clears the record and
+ * switches recording on or off.  kde_profile_read(ctx, kernel, &ms, &n)
+ * synchronises and returns the summed device time and launch count of one
+ * kernel: 0 CV pair sums, 1 deposit, 2 gather(+push), 3 sort scatter,
+ * 4 Poisson, 5 CV integral-term deposit, 6 CV leave-one-out; kernel = -1
+ * returns the number of all kernel launches in *n. */
+kde_status kde_profile_enable(kde_ctx *ctx, int on);
+kde_status kde_profile_read(kde_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KDEPIC_H */

@@ -65,6 +65,7 @@ def _load():
                 "or_pic_run": (_I, [_P, _P, _P, _I, _D, _I64, _I, _D, _D, _D, _D, _D, _I, _I, _I,
                                     _P, _I, _D, _D, _D, _I, _I, _P, _P]),
                 "or_damping_rate": (_I, [_P, _I, _D, _P, _P, _P]),
+                "or_kde_at": (None, [_P, _P, _D, _P, _I64, _D, _P, _I64, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -109,6 +110,17 @@ def deposit(x, Ng: int, L: float, kappa=None, kappa_u: float = 0.0, w=None) -> n
     rho = np.empty(Ng, dtype=np.float64)
     _load().or_deposit(_ptr(x), _ptr(k), float(kappa_u), _ptr(ww), x.size, int(Ng), float(L), _ptr(rho))
     return rho
+
+
+def kde_at(x, xp, L: float, kappa=None, kappa_u: float = 0.0, w=None) -> np.ndarray:
+    """The deposit's density (Eq. kde, x units) at arbitrary points xp."""
+    x = _f64(x)
+    xp = _f64(xp)
+    k = None if kappa is None else _f64(kappa)
+    ww = None if w is None else _f64(w)
+    out = np.empty(xp.size, dtype=np.float64)
+    _load().or_kde_at(_ptr(x), _ptr(k), float(kappa_u), _ptr(ww), x.size, float(L), _ptr(xp), xp.size, _ptr(out))
+    return out
 
 
 def gather(x, E, L: float, kappa=None, kappa_u: float = 0.0) -> np.ndarray:

@@ -483,3 +483,25 @@ int or_damping_rate(const double *W, int n, double dt, double *gamma, int *p1, i
     if (p2) *p2 = idx[1];
     return 0;
 }
+
+/* Eq. (kde) at arbitrary points: value of the deposit's density (x units) at
+ * positions xp[p] -- the same definition as or_deposit, one output at a time,
+ * for sampled checks of large problems. */
+void or_kde_at(const double *x, const double *kappa, double kappa_u, const double *w, int64_t N, double L,
+               const double *xp, int64_t np, double *out)
+{
+    double *norm = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    for (int64_t i = 0; i < N; ++i) norm[i] = 1.0 / (OR_TWO_PI * or_i0e(kappa ? kappa[i] : kappa_u));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t p = 0; p < np; ++p) {
+        double tp = OR_TWO_PI * xp[p] / L, acc = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            double ti = OR_TWO_PI * x[i] / L;
+            double k = kappa ? kappa[i] : kappa_u;
+            double wi = w ? w[i] : L / (double)N;
+            acc += wi * (OR_TWO_PI / L) * norm[i] * exp(k * (cos(tp - ti) - 1.0));
+        }
+        out[p] = acc;
+    }
+    free(norm);
+}

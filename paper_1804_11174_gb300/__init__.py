@@ -1,0 +1,309 @@
+"""GB300 (sm_103a) KDE particle-in-cell hot path: thin Python binding of libkdepic.
+
+Method: Wu & Qin, "Reducing Noise for PIC Simulations Using Kernel Density
+Estimation Algorithm" (arXiv 1804.11174).  Every computation runs in the CUDA
+kernels of `libkdepic.so` behind the C ABI of `include/kdepic.h`; this module
+only marshals arguments (torch tensors supply device memory and streams) and
+turns status codes into exceptions.  There is no CPU fallback: if the library
+is missing, importing the binding raises.
+
+Function names follow the C entry points: `Context.deposit` calls
+`kde_deposit`, `Context.cv` calls `kde_cv`, `Context.pic_step` calls
+`pic_step`, and so on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["Context", "PicState", "KdeError", "load_library", "LIB_PATH", "F64", "POISSON_FD", "CV_SCALE",
+           "PIC_NO_BACKSTEP", "MAX_NG"]
+
+LIB_PATH = _build.LIB
+F64 = 0x1
+POISSON_FD = 0x2
+CV_SCALE = 0x4
+PIC_NO_BACKSTEP = 0x100
+MAX_NG = 4096
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_U32 = ctypes.c_uint32
+
+
+class KdeError(RuntimeError):
+    """A libkdepic call returned a non-zero status."""
+
+    def __init__(self, name, code, msg):
+        super().__init__("%s failed with status %d: %s" % (name, code, msg))
+        self.code = code
+
+
+class _PicState(ctypes.Structure):
+    _fields_ = [
+        ("u", _P), ("v", _P), ("kappa", _P), ("kappa_norm", _P), ("id", _P),
+        ("N", _I64), ("Ng", _I32),
+        ("L", _D), ("dt", _D), ("qm", _D), ("charge", _D), ("background", _D), ("kappa_uniform", _D),
+        ("width_every", _I32), ("cand", _P), ("n_cand", _I32),
+        ("alpha", _D), ("kappa_min", _D), ("kappa_max", _D),
+        ("energy", _P), ("kappa_star", _P), ("step", _I64), ("flags", _U32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libkdepic.so (build it first with `__graft_entry__.build()`)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError("libkdepic.so not found at %s: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')" % p)
+    lib = ctypes.CDLL(p)
+    S = ctypes.c_int
+    sigs = {
+        "kde_create": (S, [ctypes.POINTER(_P), ctypes.c_int, _P]),
+        "kde_destroy": (S, [_P]),
+        "kde_set_stream": (S, [_P, _P]),
+        "kde_last_error": (ctypes.c_char_p, [_P]),
+        "kde_sync": (S, [_P]),
+        "kde_reserve": (S, [_P, _I64, _I32, _I32]),
+        "kde_pack_positions": (S, [_P, _P, _I64, _D, _P]),
+        "kde_deposit": (S, [_P, _P, _P, _D, _P, _I64, _I32, _D, _P, _U32]),
+        "kde_poisson": (S, [_P, _P, _I32, _D, _D, _D, _P, _P, _U32]),
+        "kde_gather": (S, [_P, _P, _P, _D, _I64, _P, _I32, _D, _P, _U32]),
+        "kde_cv": (S, [_P, _P, _P, _I64, _D, _P, _I32, _P, _P, _P, _U32]),
+        "kde_adapt_widths": (S, [_P, _P, _I64, _D, _D, _D, _D, _D, _P]),
+        "pic_step": (S, [_P, ctypes.POINTER(_PicState), _I32]),
+        "kde_damping_rate": (S, [_P, _I64, _D, _P]),
+        "kde_probe_exp2": (S, [_P, _I64, _P, _P]),
+        "kde_probe_fma": (S, [_P, _I64, _P, _P]),
+        "kde_profile_enable": (S, [_P, ctypes.c_int]),
+        "kde_profile_read": (S, [_P, ctypes.c_int, _P, _P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """One kde_ctx bound to a CUDA device and stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        self.lib = load_library()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = _P()
+        rc = self.lib.kde_create(ctypes.byref(h), int(device), _P(stream.cuda_stream))
+        if rc != 0:
+            raise KdeError("kde_create", rc, "cannot use CUDA device %d" % device)
+        self.h = h
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, name, rc):
+        if rc != 0:
+            raise KdeError(name, rc, self.lib.kde_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.kde_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check("kde_set_stream", self.lib.kde_set_stream(self.h, _P(stream.cuda_stream)))
+
+    def sync(self):
+        self._check("kde_sync", self.lib.kde_sync(self.h))
+
+    def reserve(self, N: int, Ng: int, n_cand: int = 0):
+        self._check("kde_reserve", self.lib.kde_reserve(self.h, int(N), int(Ng), int(n_cand)))
+
+    def _new(self, n, dtype):
+        torch = _torch()
+        return torch.empty(int(n), dtype=dtype, device="cuda:%d" % self.device)
+
+    # -- C ABI entry points -------------------------------------------------
+    def pack_positions(self, x, L: float, out=None):
+        torch = _torch()
+        out = self._new(x.numel(), torch.int32) if out is None else out
+        self._check("kde_pack_positions", self.lib.kde_pack_positions(self.h, _ptr(x), x.numel(), float(L), _ptr(out)))
+        return out
+
+    def deposit(self, u, Ng: int, L: float, kappa=None, kappa_uniform: float = 0.0, weight=None, out=None,
+                dtype=None):
+        """kde_deposit: rho_g = sum_i w_i (2pi/L) K_{kappa_i}(theta_g - theta_i)."""
+        torch = _torch()
+        dtype = dtype or (kappa.dtype if kappa is not None else torch.float32)
+        out = self._new(Ng, dtype) if out is None else out
+        flags = F64 if out.dtype == torch.float64 else 0
+        self._check("kde_deposit", self.lib.kde_deposit(self.h, _ptr(u), _ptr(kappa), float(kappa_uniform),
+                                                        _ptr(weight), u.numel(), int(Ng), float(L), _ptr(out), flags))
+        return out
+
+    def poisson(self, rho, L: float, charge: float = -1.0, background: float = 1.0, fd: bool = False, out=None,
+                energy=None):
+        """kde_poisson: E from dE/dx = background + charge * rho (spectral or FD)."""
+        torch = _torch()
+        out = self._new(rho.numel(), rho.dtype) if out is None else out
+        flags = (F64 if rho.dtype == torch.float64 else 0) | (POISSON_FD if fd else 0)
+        self._check("kde_poisson", self.lib.kde_poisson(self.h, _ptr(rho), rho.numel(), float(L), float(charge),
+                                                        float(background), _ptr(out), _ptr(energy), flags))
+        return out
+
+    def gather(self, u, field, L: float, kappa=None, kappa_uniform: float = 0.0, out=None):
+        """kde_gather: E_i = sum_g (2pi/Ng) K_{kappa_i}(theta_g - theta_i) field_g."""
+        torch = _torch()
+        out = self._new(u.numel(), field.dtype) if out is None else out
+        flags = F64 if field.dtype == torch.float64 else 0
+        self._check("kde_gather", self.lib.kde_gather(self.h, _ptr(u), _ptr(kappa), float(kappa_uniform), u.numel(),
+                                                      _ptr(field), field.numel(), float(L), _ptr(out), flags))
+        return out
+
+    def cv(self, u, L: float, cand, kappa_rel=None, loo=None, want_loo: bool = False):
+        """kde_cv: CV(kappa_c) (x units) for every candidate; returns (cv, argmin, loo)."""
+        torch = _torch()
+        cand = np.ascontiguousarray(cand, dtype=np.float64)
+        cv = np.empty(cand.size, dtype=np.float64)
+        am = ctypes.c_int32()
+        if want_loo and loo is None:
+            loo = self._new(u.numel(), torch.float32)
+        flags = CV_SCALE if kappa_rel is not None else 0
+        self._check("kde_cv", self.lib.kde_cv(self.h, _ptr(u), _ptr(kappa_rel), u.numel(), float(L),
+                                              cand.ctypes.data, cand.size, cv.ctypes.data, ctypes.addressof(am),
+                                              _ptr(loo), flags))
+        return cv, am.value, loo
+
+    def adapt_widths(self, loo, L: float, kappa_star: float, alpha: float = 0.5, kappa_min: float = 0.0,
+                     kappa_max: float = 1e6, out=None):
+        """kde_adapt_widths: Silverman particle-wise widths from leave-one-out densities."""
+        torch = _torch()
+        out = self._new(loo.numel(), torch.float32) if out is None else out
+        self._check("kde_adapt_widths", self.lib.kde_adapt_widths(self.h, _ptr(loo), loo.numel(), float(L),
+                                                                  float(kappa_star), float(alpha), float(kappa_min),
+                                                                  float(kappa_max), _ptr(out)))
+        return out
+
+    def pic_step(self, state: "PicState", n_steps: int):
+        """pic_step: advance the run by n_steps leap-frog steps (stream-ordered)."""
+        if state.max_steps and state.c.step + int(n_steps) > state.max_steps:
+            raise KdeError("pic_step", 1, "energy history holds %d steps; step %d + %d would overflow it"
+                           % (state.max_steps, state.c.step, n_steps))
+        state._sync_in()
+        self._check("pic_step", self.lib.pic_step(self.h, ctypes.byref(state.c), int(n_steps)))
+
+    PROF = {"cv_pairs": 0, "deposit": 1, "gather": 2, "sort": 3, "poisson": 4, "cv_grid": 5, "cv_loo": 6}
+
+    def profile_enable(self, on: bool = True):
+        """kde_profile_enable: start (or stop) recording per-kernel device times."""
+        self._check("kde_profile_enable", self.lib.kde_profile_enable(self.h, int(on)))
+
+    def profile_read(self, kernel: str):
+        """kde_profile_read: (total ms, launches) of one kernel since profile_enable;
+        kernel='all' gives (0, number of all kernel launches)."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        kid = -1 if kernel == "all" else self.PROF[kernel]
+        self._check("kde_profile_read", self.lib.kde_profile_read(self.h, kid, ctypes.addressof(ms),
+                                                                  ctypes.addressof(n)))
+        return ms.value, n.value
+
+    def probe_exp2(self, iters: int):
+        ms = ctypes.c_double()
+        ops = ctypes.c_int64()
+        self._check("kde_probe_exp2", self.lib.kde_probe_exp2(self.h, int(iters), ctypes.addressof(ms),
+                                                              ctypes.addressof(ops)))
+        return ms.value, ops.value
+
+    def probe_fma(self, iters: int):
+        ms = ctypes.c_double()
+        ops = ctypes.c_int64()
+        self._check("kde_probe_fma", self.lib.kde_probe_fma(self.h, int(iters), ctypes.addressof(ms),
+                                                            ctypes.addressof(ops)))
+        return ms.value, ops.value
+
+
+def damping_rate(energy, dt: float) -> float:
+    """kde_damping_rate: half the slope of ln W through its first two maxima after t = 0."""
+    lib = load_library()
+    W = np.ascontiguousarray(energy, dtype=np.float64)
+    g = ctypes.c_double()
+    rc = lib.kde_damping_rate(W.ctypes.data, W.size, float(dt), ctypes.addressof(g))
+    if rc != 0:
+        raise KdeError("kde_damping_rate", rc, "fewer than two energy maxima")
+    return g.value
+
+
+class PicState:
+    """Device state of one PIC run; tensors are owned here, the struct mirrors pic_state."""
+
+    def __init__(self, u, v, L: float, Ng: int, dt: float, kappa=None, kappa_uniform: float = 0.0, ids=None,
+                 qm: float = -1.0, charge: float = -1.0, background: float = 1.0, width_every: int = 0,
+                 cand=None, alpha: float = 0.5, kappa_min: float = 0.0, kappa_max: float = 1e6,
+                 max_steps: int = 0, fd: bool = False, backstep: bool = True):
+        torch = _torch()
+        self.u, self.v, self.kappa, self.id = u, v, kappa, ids
+        f64 = v.dtype == torch.float64
+        self.kappa_norm = torch.empty_like(kappa) if kappa is not None else None
+        self.cand = None if cand is None else np.ascontiguousarray(cand, dtype=np.float64)
+        dev = u.device
+        self.energy = torch.zeros(max(max_steps, 1), dtype=torch.float64, device=dev)
+        self.kappa_star = torch.zeros(max(max_steps, 1), dtype=torch.float64, device=dev)
+        self.max_steps = max_steps
+        c = _PicState()
+        c.N = u.numel()
+        c.Ng = int(Ng)
+        c.L, c.dt, c.qm, c.charge, c.background = float(L), float(dt), float(qm), float(charge), float(background)
+        c.kappa_uniform = float(kappa_uniform)
+        c.width_every = int(width_every)
+        c.n_cand = 0 if self.cand is None else self.cand.size
+        c.alpha, c.kappa_min, c.kappa_max = float(alpha), float(kappa_min), float(kappa_max)
+        c.step = 0
+        c.flags = (F64 if f64 else 0) | (POISSON_FD if fd else 0) | (0 if backstep else PIC_NO_BACKSTEP)
+        self.c = c
+
+    def _sync_in(self):
+        c = self.c
+        c.u, c.v = _ptr(self.u), _ptr(self.v)
+        c.kappa, c.kappa_norm, c.id = _ptr(self.kappa), _ptr(self.kappa_norm), _ptr(self.id)
+        c.cand = None if self.cand is None else self.cand.ctypes.data
+        ok = self.max_steps > 0
+        c.energy = _ptr(self.energy) if ok else None
+        c.kappa_star = _ptr(self.kappa_star) if ok else None
+
+    @property
+    def step(self) -> int:
+        return self.c.step

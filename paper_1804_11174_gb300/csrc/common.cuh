@@ -1,0 +1,314 @@
+// common.cuh -- internal definitions shared by the translation units of libkdepic.
+//
+// Position code: u = floor(x / L * 2^32); theta / 2 = pi u / 2^32.  All pair
+// kernels evaluate the von Mises kernel as
+//     exp(kappa (cos d - 1)) = exp(-2 kappa sin^2(d/2)) = 2^(-(beta sin(d/2))^2),
+//     beta = sqrt(2 kappa log2 e),
+// with sin(d/2) from the angle-difference identity on per-point half-angle
+// sines and cosines, so one pair costs a few FMAs and one exp2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <algorithm>
+#include <tuple>
+#include <vector>
+
+#include "../../include/kdepic.h"
+
+#define KDE_PI 3.14159265358979323846
+#define KDE_TWO_PI 6.28318530717958647692
+#define KDE_LOG2E 1.44269504088896340736
+#define KDE_LN2 0.69314718055994530942
+
+// A kernel term whose exponent 2 kappa sin^2(d/2) log2 e exceeds the cut is
+// below 2^-cut of the kernel's peak and may be skipped: 2^-24 in FP32, 2^-64
+// in FP64 (below the rounding of either precision).
+#define KDE_XCUT 24.0
+#define KDE_XCUT64 64.0
+template <typename T> struct KdeCut { static constexpr double x = KDE_XCUT; };
+template <> struct KdeCut<double> { static constexpr double x = KDE_XCUT64; };
+#define KDE_KAPPA_MAX 1.0e6
+
+// device status word codes (first failure wins)
+#define KDE_DEV_KAPPA_RANGE 1u
+#define KDE_DEV_WAIT_TIMEOUT 2u
+#define KDE_DEV_BAD_ARG 3u
+
+// workspace slots owned by a context
+enum WsSlot {
+    WS_SORT_COUNTS = 0,
+    WS_SORT_STARTS,
+    WS_SORT_U,
+    WS_SORT_P0,
+    WS_SORT_P1,
+    WS_SORT_P2,
+    WS_SORT_P3,
+    WS_SORT_PERM,
+    WS_NORM,
+    WS_ACC,
+    WS_GRID0,
+    WS_GRID1,
+    WS_WMAX,
+    WS_CV_SC,
+    WS_CV_TILE,
+    WS_CV_KR,
+    WS_CV_LNORM,
+    WS_CV_PART,
+    WS_CV_F2,
+    WS_CV_TOT,
+    WS_CV_OUT,
+    WS_CV_CAND,
+    WS_CV_ACC,
+    WS_CV_LOO,
+    WS_CV_RED,
+    WS_PIC_E,
+    WS_PIC_LOO,
+    WS_PIC_KS,
+    WS_NSLOTS
+};
+
+// kernels timed by the profiling hook (kde_profile_enable / kde_profile_read)
+enum KdeProfId { PROF_CV_PAIRS = 0, PROF_DEPOSIT, PROF_GATHER, PROF_SORT, PROF_POISSON, PROF_CV_GRID, PROF_CV_LOO,
+                 PROF_NIDS };
+
+struct kde_ctx {
+    int device = 0;
+    // profiling: event pairs recorded around selected launches while enabled
+    bool prof_on = false;
+    long long launches = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    unsigned int *d_status = nullptr;  // [0] code, [1] detail
+    void *ws[WS_NSLOTS] = {};
+    size_t ws_bytes[WS_NSLOTS] = {};
+    // cached tables keyed by (Ng, precision): half-angle sines/cosines of the nodes
+    std::map<std::pair<int, int>, void *> node_tab;
+    // cached Green's functions keyed by (Ng, L bits, fd, precision)
+    std::map<std::tuple<int, uint64_t, int, int>, void *> green_tab;
+};
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+kde_status kde_fail(kde_ctx *ctx, kde_status code, const char *fmt, ...);
+kde_status kde_cuda_check(kde_ctx *ctx, cudaError_t e, const char *what);
+void *kde_ws(kde_ctx *ctx, WsSlot slot, size_t bytes);  // grows the slot; nullptr + error on failure
+const void *kde_node_table(kde_ctx *ctx, int Ng, bool f64);
+const void *kde_green_table(kde_ctx *ctx, int Ng, double L, bool fd, bool f64);
+double kde_host_i0e(double x);  // scaled Bessel I0e in FP64 on the host (uniform widths)
+
+#define KDE_TRY(expr)                       \
+    do {                                    \
+        kde_status _s = (expr);             \
+        if (_s != KDE_OK) return _s;        \
+    } while (0)
+#define KDE_CUDA(ctx, expr, what)                                   \
+    do {                                                            \
+        cudaError_t _e = (expr);                                    \
+        if (_e != cudaSuccess) return kde_cuda_check(ctx, _e, what); \
+    } while (0)
+#define KDE_LAUNCHED(ctx, what)                        \
+    do {                                               \
+        ++(ctx)->launches;                             \
+        KDE_CUDA(ctx, cudaGetLastError(), what);       \
+    } while (0)
+
+// profiling hook: when enabled, records an event pair around a launch on the
+// context's stream
+cudaEvent_t kde_prof_event(kde_ctx *ctx);
+struct KdeProfScope {
+    kde_ctx *c;
+    int id;
+    cudaEvent_t b = nullptr;
+    KdeProfScope(kde_ctx *ctx, int i) : c(ctx), id(i)
+    {
+        if (c->prof_on) {
+            b = kde_prof_event(c);
+            cudaEventRecord(b, c->stream);
+        }
+    }
+    ~KdeProfScope()
+    {
+        if (b) {
+            cudaEvent_t e = kde_prof_event(c);
+            cudaEventRecord(e, c->stream);
+            c->prof.push_back({id, {b, e}});
+        }
+    }
+};
+
+// number of nodes on each side of a particle's cell that its truncated kernel
+// can reach: ceil(r / dtheta), r = 2 asin(sqrt(XCUT ln2 / (2 kappa))), or Ng
+// when the support is the whole circle
+__host__ __device__ inline int kde_window_nodes(double kappa, int Ng)
+{
+    double s2 = KDE_XCUT * KDE_LN2 / (2.0 * kappa);
+    if (s2 >= 1.0) return Ng;
+    double r = 2.0 * asin(sqrt(s2));
+    double w = ceil(r * Ng / KDE_TWO_PI);
+    return w >= Ng ? Ng : (int)w;
+}
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float kde_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ double kde_ex2(double x) { return exp2(x); }
+
+__device__ __forceinline__ void kde_flag(unsigned int *status, unsigned code, unsigned detail)
+{
+    if (status && atomicCAS(status, 0u, code) == 0u) status[1] = detail;
+}
+
+// half-angle sine and cosine of the position code: theta / 2 = pi u / 2^32.
+// FP32: the code is split as u = hi 2^16 + lo so that both arguments of
+// sincospif are exact floats, then recombined by the angle-sum identity.
+__device__ __forceinline__ void kde_half_sincos(uint32_t u, float &s, float &c)
+{
+    float sh, ch, sl, cl;
+    sincospif((float)(u >> 16) * (1.0f / 65536.0f), &sh, &ch);
+    sincospif((float)(u & 0xFFFFu) * (1.0f / 4294967296.0f), &sl, &cl);
+    s = fmaf(sh, cl, ch * sl);
+    c = fmaf(ch, cl, -sh * sl);
+}
+__device__ __forceinline__ void kde_half_sincos(uint32_t u, double &s, double &c)
+{
+    sincospi((double)u * (1.0 / 4294967296.0), &s, &c);
+}
+
+// cell index of a position on an Ng-node grid: floor(u Ng / 2^32)
+__device__ __forceinline__ int kde_cell(uint32_t u, int Ng)
+{
+    return (int)(((uint64_t)u * (uint64_t)Ng) >> 32);
+}
+
+// scaled modified Bessel function I0e(x) = exp(-x) I0(x) in FP64 (power series
+// below 30, Hankel asymptotic expansion above)
+__host__ __device__ inline double kde_i0e(double x)
+{
+    if (x < 0) x = -x;
+    if (x < 30.0) {
+        double q = 0.25 * x * x, term = 1.0, sum = 1.0;
+        for (int k = 1; k < 200; ++k) {
+            term *= q / ((double)k * (double)k);
+            sum += term;
+            if (term < 1e-17 * sum) break;
+        }
+        return sum * exp(-x);
+    }
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 60; ++k) {
+        double nx = term * (2.0 * k - 1.0) * (2.0 * k - 1.0) / (8.0 * x * k);
+        if (nx >= term) break;
+        term = nx;
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum / sqrt(KDE_TWO_PI * x);
+}
+
+// von Mises normalisation 1 / (2 pi I0e(kappa))
+__host__ __device__ inline double kde_norm(double kappa) { return 1.0 / (KDE_TWO_PI * kde_i0e(kappa)); }
+
+// exact power-of-two scale for the int64 fixed-point grid accumulators: the
+// largest possible node value is `bound`, kept below 2^62
+__host__ __device__ inline double kde_acc_scale(double bound)
+{
+    int e;
+    frexp(bound > 0 ? bound : 1.0, &e);  // bound < 2^e
+    return ldexp(1.0, 62 - e);
+}
+
+// ---------------------------------------------------------------------------
+// internal launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------
+// counting sort by bin = floor(u nbins / 2^32), stable.  Moves u and up to four
+// payload arrays (element size 4 or 8 bytes); writes the source index of every
+// output slot to perm_out when not null.
+struct SortPayload {
+    const void *src;
+    void *dst;
+    int elem;
+};
+kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, uint32_t *u_out,
+                           const SortPayload *pl, int npl, uint32_t *perm_out);
+
+// deposit of cell-sorted particles into int64 accumulators acc[Ng] (zeroed
+// here).  Particle j contributes w_j * coef * norm_j * exp(-2 kappa_j sin^2(..)).
+// Arrays may be null (then the uniform scalar is used; norm null with a kappa
+// array means "compute the norm from the width").  `bound` is the largest
+// possible node value; with wmax_bits it is N * coef * norm_bound * w_max.
+template <typename T>
+kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,
+                              const T *w, T w_u, int64_t N, int Ng, double coef, long long *acc, double bound,
+                              const unsigned int *wmax_bits, double norm_bound);
+template <typename T>
+kde_status kde_acc_to_real(kde_ctx *ctx, const long long *acc, int Ng, double bound, const unsigned int *wmax_bits,
+                           double wscale, T *out);
+
+// Poisson solve of rho_total = background + charge * rho, rho given as a real
+// array or as int64 accumulators (value = acc * acc_inv)
+template <typename T>
+kde_status kde_poisson_impl(kde_ctx *ctx, const T *rho, const long long *acc, double acc_inv, int Ng, double L,
+                            double charge, double background, bool fd, T *E_out);
+template <typename T>
+kde_status kde_energy_impl(kde_ctx *ctx, const T *E, int Ng, double L, double *energy_out);
+
+struct PushArgs {
+    const void *v_in;        // sorted velocities
+    uint32_t *u_out;         // updated positions (sorted order)
+    void *v_out;
+    void *kappa_out;         // widths written back (sorted order), or null
+    const void *norm_in;
+    void *norm_out;
+    const uint32_t *id_in;
+    uint32_t *id_out;
+    double kick;             // velocity kick factor (1/2 on the first step)
+    double qm_dt;
+    double dt_scale;         // dt * 2^32 / L
+    double *energy;          // field energy slot for this step, or null
+    const double *kstar_in;  // CV width in force (device), or null for the uniform width
+    double *kstar_out;
+    double dx;
+};
+template <typename T>
+kde_status kde_gather_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,
+                             int64_t N, const T *field, int Ng, double coef, T *out, const uint32_t *perm,
+                             const PushArgs *push);
+
+// candidate widths (or scale factors) for the CV kernels, passed by value
+struct CandList {
+    int n;
+    int scale_mode;
+    double k[256];
+};
+
+// CV on the device without host synchronisation.  u: positions (any order);
+// cand_host: host float64[n_cand] in the caller's order.  Results stay on the
+// device: cv_dev float64[n_cand] (caller's order), argmin_dev int32, loo
+// (float32, order of u, at the argmin) when not null, kstar_dev float64 (the
+// selected candidate) when not null.
+kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64_t N, double L,
+                         const double *cand_host, int n_cand, bool scale_mode, double *cv_dev, int *argmin_dev,
+                         float *loo, double *kstar_dev);
+
+// Silverman widths from leave-one-out densities; kstar from the device when
+// kstar_dev is not null.  Writes widths (and norms when norm_out is not null)
+// as float or double.
+kde_status kde_adapt_device(kde_ctx *ctx, const float *loo, int64_t N, double L, const double *kstar_dev,
+                            double kstar_host, double alpha, double kmin, double kmax, void *kappa_out,
+                            void *norm_out, bool f64);

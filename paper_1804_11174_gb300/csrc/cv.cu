@@ -1,0 +1,710 @@
+// cv.cu -- leave-one-out cross-validation over candidate widths (Sec. II.B,
+// Eq. cv_def) and Silverman's particle-wise widths (Sec. II.C).
+//
+// CV_theta(c) = int fhat_c^2 dtheta - 2/(n(n-1)) sum_i sum_{j != i} K_{kappa_jc}(theta_i - theta_j)
+//
+// Pair term.  Particles are bin-sorted and cut into tiles of CV_T = 256.  A CTA
+// owns one "row" tile (one particle per thread, kept in registers) and walks
+// "column" tiles outward from its own; each column tile's half-angle (sin,
+// cos) pairs are staged into shared memory with a 1D TMA bulk copy
+// (cp.async.bulk + mbarrier, double-buffered).  For a pair the kernel forms
+// s = sin((theta_j - theta_i)/2) by the angle-difference identity (2 FMA-pipe
+// ops), s^2 once, and then for every active candidate one FMUL/FFMA, one
+// ex2.approx and one FADD.  Candidates are sorted by width; a tile pair whose
+// angular gap exceeds a candidate's truncation radius (kernel < 2^-24 of its
+// peak) skips that candidate, and the walk stops when no candidate reaches.
+// Uniform widths are symmetric, so only unordered tile pairs are visited
+// (weight 2 off the diagonal); per-particle widths visit ordered pairs.
+// Per-thread FP32 sums of one tile are reduced across the warp and added to
+// FP64 accumulators; per-CTA partials are reduced in a fixed order, so the
+// result is deterministic.
+//
+// Integral term: exact trapezoid sum of fhat^2 on a power-of-two grid fine
+// enough for each candidate (deposit.cu).  Combination and argmin in FP64.
+#include "common.cuh"
+
+#define CV_T 256
+#define CV_WARPS (CV_T / 32)
+#define CV_G 8
+#define CV_MAXC 256
+#define CV_WAIT_LIMIT (1u << 26)
+
+// internal candidate order (ascending width) plus the map back to the caller's order
+struct CvCands {
+    int n;
+    int scale_mode;
+    float k[CV_MAXC];      // sorted candidate widths (uniform) or scale factors
+    int orig[CV_MAXC];     // sorted position -> caller index
+};
+
+kde_status kde_cv_integral_term(kde_ctx *ctx, const uint32_t *u_sorted, int64_t N, const float *kappa_rel,
+                                const float *lnorm, const unsigned int *krmax_bits, const CandList &cl,
+                                double *f2_out);
+
+// ---------------------------------------------------------------------------
+// TMA / mbarrier helpers (bounded waits)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// returns false if the phase did not complete within CV_WAIT_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    for (unsigned it = 0; it < CV_WAIT_LIMIT; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// geometry helpers
+// ---------------------------------------------------------------------------
+// circular gap (in position-code units) between the code intervals of two tiles
+__device__ __forceinline__ uint32_t tile_gap(uint2 a, uint2 b)
+{
+    if ((uint32_t)(b.x - a.x) <= (uint32_t)(a.y - a.x)) return 0u;  // b starts inside a
+    if ((uint32_t)(a.x - b.x) <= (uint32_t)(b.y - b.x)) return 0u;  // a starts inside b
+    uint32_t g1 = b.x - a.y, g2 = a.x - b.y;
+    return g1 < g2 ? g1 : g2;
+}
+// largest width whose truncated kernel still reaches across a gap
+__device__ __forceinline__ float reach_kappa(uint32_t gap)
+{
+    if (gap == 0u) return 3.0e38f;
+    float s = sinpif((float)gap * (1.0f / 4294967296.0f));  // sin(gap_theta / 2)
+    return (float)(KDE_XCUT * KDE_LN2 / 2.0) / (s * s);
+}
+
+// ---------------------------------------------------------------------------
+// prep: per-particle half-angle (sin, cos); per-tile code interval, widened to
+// whole sort bins so that tile intervals are monotone along the sorted order;
+// for per-particle widths also the exponent factor, the tile's smallest width,
+// the global extremes and log2 of every (particle, candidate) normalisation
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(CV_T)
+    cv_prep_kernel(const uint32_t *u, const float *kr, int64_t N, int bin_shift, float2 *sc, uint2 *tile_u,
+                   float *tile_kmin, float *k2rel, unsigned int *kr_bits, CandList cl, float *lnorm,
+                   unsigned int *status)
+{
+    __shared__ float skmin[CV_WARPS];
+    const int64_t j = (int64_t)blockIdx.x * CV_T + threadIdx.x;
+    const bool valid = j < N;
+    uint32_t uu = valid ? u[j] : 0u;
+    float s = 0.f, c = 1.f;
+    if (valid) kde_half_sincos(uu, s, c);
+    sc[j] = make_float2(s, c);
+    if (threadIdx.x == 0) {
+        int64_t last = (int64_t)blockIdx.x * CV_T + CV_T - 1;
+        if (last >= N) last = N - 1;
+        uint32_t b0 = u[(int64_t)blockIdx.x * CV_T] >> bin_shift, b1 = u[last] >> bin_shift;
+        tile_u[blockIdx.x] = make_uint2(b0 << bin_shift, ((b1 + 1u) << bin_shift) - 1u);
+    }
+    if (kr) {
+        float k = valid ? kr[j] : 1.0f;
+        if (valid && !(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
+            kde_flag(status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
+            k = 1.0f;
+        }
+        k2rel[j] = (float)(-2.0 * KDE_LOG2E) * k;
+        float km = valid ? k : 3.0e38f;
+        if (valid) {
+            atomicMax(&kr_bits[0], __float_as_uint(k));
+            atomicMin(&kr_bits[1], __float_as_uint(k));
+            for (int q = 0; q < cl.n; ++q) lnorm[(size_t)q * N + j] = (float)log2(kde_norm(cl.k[q] * (double)k));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) km = fminf(km, __shfl_xor_sync(0xffffffffu, km, o));
+        if ((threadIdx.x & 31) == 0) skmin[threadIdx.x >> 5] = km;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < CV_WARPS; ++w) km = fminf(km, skmin[w]);
+            tile_kmin[blockIdx.x] = fminf(km, skmin[0]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tile walk: from row tile a, the column tiles whose gap a kernel of width
+// Kthr can bridge form (at most) a forward run a, a+1, ... and a backward run
+// a-1, a-2, ... (tile intervals are monotone, so the forward and backward gaps
+// are monotone in the step).  The walk visits both runs once each.
+// ---------------------------------------------------------------------------
+struct Walk {
+    int phase, k, F;
+};
+
+__device__ __forceinline__ bool walk_next(Walk &w, int a, int NT, const uint2 *tile_u, uint2 ta, float Kthr, int &b,
+                                          int &d)
+{
+    for (;;) {
+        if (w.phase == 0) {
+            if (w.k >= NT) {
+                w.phase = 2;
+                return false;
+            }
+            int bb = (a + w.k) % NT;
+            if (w.k == 0 || Kthr <= reach_kappa(tile_gap(ta, tile_u[bb]))) {
+                b = bb;
+                d = w.k;
+                w.F = w.k;
+                ++w.k;
+                return true;
+            }
+            w.phase = 1;
+            w.k = 1;
+        } else if (w.phase == 1) {
+            if (w.k >= NT - w.F) {
+                w.phase = 2;
+                return false;
+            }
+            int bb = ((a - w.k) % NT + NT) % NT;
+            if (Kthr <= reach_kappa(tile_gap(ta, tile_u[bb]))) {
+                b = bb;
+                d = -w.k;
+                ++w.k;
+                return true;
+            }
+            w.phase = 2;
+            return false;
+        } else {
+            return false;
+        }
+    }
+}
+
+// unordered tile pairs are visited from the tile with the smaller forward
+// offset: d = (b - a) mod NT <= NT/2, and for even NT the half-way pair only
+// from the first half
+__device__ __forceinline__ bool canonical_pair(int a, int b, int NT)
+{
+    int d = ((b - a) % NT + NT) % NT;
+    if (2 * d < NT) return true;
+    if (2 * d == NT) return a < NT / 2;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// pair totals over all active candidates
+// ---------------------------------------------------------------------------
+struct CvPairArgs {
+    const float2 *sc;
+    int64_t N;
+    int NT;
+    int splits;
+    const uint2 *tile_u;
+    const float *tile_kmin;  // per-particle widths only
+    const float *k2rel;
+    const float *lnorm;
+    double *part;  // [gridDim.x][n]
+    unsigned int *status;
+};
+
+template <bool SCALE>
+__device__ __forceinline__ int active_candidates(const CvCands &cc, uint32_t gap, float kmin)
+{
+    float kr = reach_kappa(gap);
+    int c = 0;
+    if (SCALE) {
+        while (c < cc.n && cc.k[c] * kmin <= kr) ++c;
+    } else {
+        while (c < cc.n && cc.k[c] <= kr) ++c;
+    }
+    return c;
+}
+
+template <bool SCALE>
+__global__ void __launch_bounds__(CV_T) cv_pairs_kernel(CvPairArgs A, CvCands cc)
+{
+    __shared__ __align__(128) float2 buf[2][CV_T];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double wacc[CV_WARPS][CV_MAXC];
+    __shared__ int s_stop;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int a = blockIdx.x / A.splits, sidx = blockIdx.x % A.splits;
+    const int NT = A.NT;
+    for (int c = tid; c < CV_WARPS * CV_MAXC; c += CV_T) (&wacc[0][0])[c] = 0.0;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    const int64_t j = (int64_t)a * CV_T + tid;
+    const bool rvalid = j < A.N;
+    const float2 me = A.sc[j];
+    const float rmask = rvalid ? 1.0f : 0.0f;
+    const float k2r = SCALE ? (rvalid ? A.k2rel[j] : 0.f) : 0.f;
+    const uint2 ta = A.tile_u[a];
+    const float kmin_a = SCALE ? A.tile_kmin[a] : 1.0f;
+    const float Kthr = cc.k[0] * kmin_a;  // the widest kernel of this row tile
+    __syncthreads();
+
+    Walk w{0, 0, 0};
+    int cnt = 0;
+    // next column tile assigned to this CTA (every CTA of the row walks the same sequence)
+    auto fetch = [&](int &b, int &d) -> bool {
+        while (walk_next(w, a, NT, A.tile_u, ta, Kthr, b, d)) {
+            if (!SCALE && !canonical_pair(a, b, NT)) continue;
+            if ((cnt++) % A.splits == sidx) return true;
+        }
+        return false;
+    };
+    int b_cur = 0, d_cur = 0;
+    bool have = fetch(b_cur, d_cur);
+    if (have && tid == 0) tma_load_1d(buf[0], A.sc + (size_t)b_cur * CV_T, CV_T * sizeof(float2), &bar[0]);
+    bool pending[2] = {have, false};
+    unsigned phase[2] = {0u, 0u};
+    bool failed = false;
+    for (int k = 0; have; ++k) {
+        const int cur = k & 1;
+        int b_nxt = 0, d_nxt = 0;
+        const bool next = fetch(b_nxt, d_nxt);
+        if (next && tid == 0)
+            tma_load_1d(buf[cur ^ 1], A.sc + (size_t)b_nxt * CV_T, CV_T * sizeof(float2), &bar[cur ^ 1]);
+        pending[cur ^ 1] = next;
+        const bool ok = mbar_wait(&bar[cur], phase[cur]);
+        phase[cur] ^= 1u;
+        pending[cur] = false;
+        if (tid == 0) s_stop = ok ? 0 : 1;
+        __syncthreads();
+        if (s_stop) {
+            failed = true;
+            break;
+        }
+        const int b = b_cur;
+        const int nact = active_candidates<SCALE>(cc, tile_gap(ta, A.tile_u[b]), kmin_a);
+        if (nact > 0) {
+            const int64_t col0 = (int64_t)b * CV_T;
+            const int ncol = (int)(A.N - col0 < CV_T ? A.N - col0 : CV_T);
+            const bool diag = (d_cur == 0);
+            const float wgt = (!SCALE && !diag) ? 2.0f : 1.0f;
+            const float2 *t = buf[cur];
+            for (int cg = 0; cg < nact; cg += CV_G) {
+                float kk[CV_G], ll[CV_G], acc[CV_G];
+#pragma unroll
+                for (int q = 0; q < CV_G; ++q) {
+                    int c = cg + q < nact ? cg + q : nact - 1;
+                    if (SCALE) {
+                        kk[q] = cc.k[c] * k2r;
+                        ll[q] = rvalid ? A.lnorm[(size_t)c * A.N + j] : 0.f;
+                    } else {
+                        kk[q] = (float)(-2.0 * KDE_LOG2E) * cc.k[c];
+                        ll[q] = 0.f;
+                    }
+                    acc[q] = 0.f;
+                }
+                if (!diag) {
+#pragma unroll 2
+                    for (int i = 0; i < ncol; ++i) {
+                        float2 o = t[i];
+                        float s = me.x * o.y - me.y * o.x;
+                        float s2 = s * s;
+#pragma unroll
+                        for (int q = 0; q < CV_G; ++q) acc[q] += kde_ex2(SCALE ? fmaf(s2, kk[q], ll[q]) : s2 * kk[q]);
+                    }
+                } else {
+                    for (int i = 0; i < ncol; ++i) {
+                        if (i == tid) continue;
+                        float2 o = t[i];
+                        float s = me.x * o.y - me.y * o.x;
+                        float s2 = s * s;
+#pragma unroll
+                        for (int q = 0; q < CV_G; ++q) acc[q] += kde_ex2(SCALE ? fmaf(s2, kk[q], ll[q]) : s2 * kk[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < CV_G; ++q) {
+                    float v = acc[q] * rmask;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0 && cg + q < nact) wacc[warp][cg + q] += (double)wgt * (double)v;
+                }
+            }
+        }
+        __syncthreads();  // buffer `cur` is free again
+        b_cur = b_nxt;
+        d_cur = d_nxt;
+        have = next;
+    }
+    if (failed && tid == 0) kde_flag(A.status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
+    // drain any copy still in flight before the CTA's shared memory goes away
+    for (int q = 0; q < 2; ++q)
+        if (pending[q] && !mbar_wait(&bar[q], phase[q]) && tid == 0)
+            kde_flag(A.status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
+    __syncthreads();
+    for (int c = tid; c < cc.n; c += CV_T) {
+        double s = 0.0;
+        for (int ww = 0; ww < CV_WARPS; ++ww) s += wacc[ww][c];
+        A.part[(size_t)blockIdx.x * cc.n + c] = s;
+    }
+}
+
+// per-candidate sum of CTA partials in CTA order
+__global__ void cv_reduce_kernel(const double *part, int nblocks, int n, double *tot)
+{
+    const int c = blockIdx.x;
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) s += part[(size_t)b * n + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tot[c] = red[0];
+}
+
+// CV in x units for every candidate (caller's order), argmin (smallest caller
+// index on exact ties) and the selected width
+__global__ void cv_combine_kernel(const double *f2, const double *tot, CvCands cc, CandList cl, int64_t N,
+                                  double L, double *cv_out, int *argmin, double *kstar)
+{
+    if (threadIdx.x != 0) return;
+    const double n = (double)N, xs = KDE_TWO_PI / L;
+    for (int c = 0; c < cc.n; ++c) {
+        double t = tot[c];
+        if (!cc.scale_mode) t *= kde_norm((double)cl.k[c]);
+        cv_out[cc.orig[c]] = xs * (f2[c] - 2.0 * t / (n * (n - 1.0)));
+    }
+    int best = 0;
+    for (int c = 1; c < cc.n; ++c)
+        if (cv_out[c] < cv_out[best]) best = c;
+    *argmin = best;
+    if (kstar) {
+        // the caller-order candidate value
+        for (int c = 0; c < cc.n; ++c)
+            if (cc.orig[c] == best) *kstar = cl.k[c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// leave-one-out sums at the selected candidate (rows = targets, columns =
+// sources with their own kernels), written in the caller's particle order
+// ---------------------------------------------------------------------------
+struct CvLooArgs {
+    const float2 *sc;
+    int64_t N;
+    int NT;
+    const uint2 *tile_u;
+    const float *tile_kmin;
+    const float *k2rel;
+    const float *lnorm;
+    const uint32_t *perm;
+    const int *argmin;  // caller index
+    const unsigned int *kr_bits;  // [0] largest, [1] smallest per-particle width (float bits)
+    CvCands cc;
+    double xs;  // 2 pi / L
+    float *loo;
+};
+
+template <bool SCALE>
+__global__ void __launch_bounds__(CV_T) cv_loo_kernel(CvLooArgs A)
+{
+    __shared__ float2 tsc[CV_T];
+    __shared__ float2 tkl[CV_T];
+    const int tid = threadIdx.x;
+    const int a = blockIdx.x, NT = A.NT;
+    // sorted position of the selected candidate
+    const int best = *A.argmin;
+    int cs = 0;
+    for (int c = 0; c < A.cc.n; ++c)
+        if (A.cc.orig[c] == best) cs = c;
+    const float kc = A.cc.k[cs];
+    const int64_t i = (int64_t)a * CV_T + tid;
+    const bool rvalid = i < A.N;
+    const float2 me = A.sc[i];
+    const uint2 ta = A.tile_u[a];
+    // sources carry their own widths: walk with the smallest width anywhere (a bound)
+    const float Kthr = SCALE ? kc * __uint_as_float(A.kr_bits[1]) : kc;
+    const float kk = (float)(-2.0 * KDE_LOG2E) * kc;
+    double sum = 0.0;
+    Walk w{0, 0, 0};
+    int b, d;
+    while (walk_next(w, a, NT, A.tile_u, ta, Kthr, b, d)) {
+        if (SCALE && !(kc * A.tile_kmin[b] <= reach_kappa(tile_gap(ta, A.tile_u[b])))) continue;
+        const int64_t j = (int64_t)b * CV_T + tid;
+        __syncthreads();
+        tsc[tid] = A.sc[j];
+        if (SCALE) {
+            float k2 = j < A.N ? A.k2rel[j] * kc : 0.f;
+            float l = j < A.N ? A.lnorm[(size_t)cs * A.N + j] : 0.f;
+            tkl[tid] = make_float2(k2, l);
+        }
+        __syncthreads();
+        const int ncol = (int)(A.N - (int64_t)b * CV_T < CV_T ? A.N - (int64_t)b * CV_T : CV_T);
+        float acc = 0.f;
+        for (int q = 0; q < ncol; ++q) {
+            if (d == 0 && q == tid) continue;
+            float2 o = tsc[q];
+            float s = me.x * o.y - me.y * o.x;
+            float s2 = s * s;
+            if (SCALE) {
+                float2 p = tkl[q];
+                acc += kde_ex2(fmaf(s2, p.x, p.y));
+            } else {
+                acc += kde_ex2(s2 * kk);
+            }
+        }
+        sum += (double)acc;
+    }
+    if (!rvalid) return;
+    if (!SCALE) sum *= kde_norm((double)kc);
+    const double loo = A.xs * sum / (double)(A.N - 1);
+    A.loo[A.perm ? A.perm[i] : i] = (float)loo;
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64_t N, double L,
+                         const double *cand_host, int n_cand, bool scale_mode, double *cv_dev, int *argmin_dev,
+                         float *loo, double *kstar_dev)
+{
+    // candidates: internal ascending order
+    CandList cl{};
+    CvCands cc{};
+    cl.n = cc.n = n_cand;
+    cl.scale_mode = cc.scale_mode = scale_mode ? 1 : 0;
+    std::vector<int> idx(n_cand);
+    for (int c = 0; c < n_cand; ++c) idx[c] = c;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cand_host[x] < cand_host[y]; });
+    for (int c = 0; c < n_cand; ++c) {
+        cl.k[c] = cand_host[idx[c]];
+        cc.k[c] = (float)cand_host[idx[c]];
+        cc.orig[c] = idx[c];
+    }
+    // bin sort (4096 bins at most; about 16 particles per bin)
+    int nbins = 64;
+    while (nbins < 4096 && (int64_t)nbins * 16 < N) nbins <<= 1;
+    const int NT = (int)((N + CV_T - 1) / CV_T);
+    const int64_t Np = (int64_t)NT * CV_T;
+    uint32_t *us = (uint32_t *)kde_ws(ctx, WS_SORT_U, (size_t)Np * 4);
+    uint32_t *perm = (uint32_t *)kde_ws(ctx, WS_SORT_PERM, (size_t)Np * 4);
+    float *krs = scale_mode ? (float *)kde_ws(ctx, WS_SORT_P0, (size_t)Np * 4) : nullptr;
+    float2 *sc = (float2 *)kde_ws(ctx, WS_CV_SC, (size_t)Np * sizeof(float2));
+    uint2 *tile_u = (uint2 *)kde_ws(ctx, WS_CV_TILE, (size_t)NT * sizeof(uint2) + (size_t)NT * 4 + 64);
+    float *tile_kmin = scale_mode ? (float *)(tile_u + NT) : nullptr;
+    float *k2rel = scale_mode ? (float *)kde_ws(ctx, WS_CV_KR, (size_t)Np * 4) : nullptr;
+    float *lnorm = scale_mode ? (float *)kde_ws(ctx, WS_CV_LNORM, (size_t)n_cand * N * 4) : nullptr;
+    unsigned int *krmax = (unsigned int *)kde_ws(ctx, WS_WMAX, 64);  // [0] max, [1] min width bits
+    double *f2 = (double *)kde_ws(ctx, WS_CV_F2, (size_t)n_cand * 8);
+    double *tot = (double *)kde_ws(ctx, WS_CV_TOT, (size_t)n_cand * 8);
+    if (!us || !perm || !sc || !tile_u || !krmax || !f2 || !tot || (scale_mode && (!krs || !k2rel || !lnorm)))
+        return KDE_ENOMEM;
+    SortPayload pl[1];
+    int npl = 0;
+    if (scale_mode) pl[npl++] = SortPayload{kappa_rel, krs, 4};
+    KDE_TRY(kde_sort_by_bin(ctx, u, N, nbins, us, pl, npl, perm));
+    KDE_CUDA(ctx, cudaMemsetAsync(krmax, 0, 4, ctx->stream), "kappa max memset");
+    KDE_CUDA(ctx, cudaMemsetAsync(krmax + 1, 0x7f, 4, ctx->stream), "kappa min memset");
+    int bin_shift = 32;
+    for (int nb = nbins; nb > 1; nb >>= 1) --bin_shift;
+    cv_prep_kernel<<<NT, CV_T, 0, ctx->stream>>>(us, krs, N, bin_shift, sc, tile_u, tile_kmin, k2rel, krmax, cl,
+                                                  lnorm, ctx->d_status);
+    KDE_LAUNCHED(ctx, "cv_prep_kernel");
+
+    // pair totals
+    int splits = 1;
+    while ((int64_t)NT * splits < 2LL * ctx->sm_count && splits < NT) ++splits;
+    const int nblocks = NT * splits;
+    double *part = (double *)kde_ws(ctx, WS_CV_PART, (size_t)nblocks * n_cand * 8);
+    if (!part) return KDE_ENOMEM;
+    CvPairArgs A{};
+    A.sc = sc;
+    A.N = N;
+    A.NT = NT;
+    A.splits = splits;
+    A.tile_u = tile_u;
+    A.tile_kmin = tile_kmin;
+    A.k2rel = k2rel;
+    A.lnorm = lnorm;
+    A.part = part;
+    A.status = ctx->d_status;
+    {
+        KdeProfScope _ps(ctx, PROF_CV_PAIRS);
+        if (scale_mode) cv_pairs_kernel<true><<<nblocks, CV_T, 0, ctx->stream>>>(A, cc);
+        else cv_pairs_kernel<false><<<nblocks, CV_T, 0, ctx->stream>>>(A, cc);
+    }
+    KDE_LAUNCHED(ctx, "cv_pairs_kernel");
+    cv_reduce_kernel<<<n_cand, 256, 0, ctx->stream>>>(part, nblocks, n_cand, tot);
+    KDE_LAUNCHED(ctx, "cv_reduce_kernel");
+
+    // integral term on fine grids
+    KDE_TRY(kde_cv_integral_term(ctx, us, N, krs, lnorm, krmax, cl, f2));
+
+    cv_combine_kernel<<<1, 32, 0, ctx->stream>>>(f2, tot, cc, cl, N, L, cv_dev, argmin_dev, kstar_dev);
+    KDE_LAUNCHED(ctx, "cv_combine_kernel");
+
+    if (loo) {
+        CvLooArgs B{};
+        B.sc = sc;
+        B.N = N;
+        B.NT = NT;
+        B.tile_u = tile_u;
+        B.tile_kmin = tile_kmin;
+        B.k2rel = k2rel;
+        B.lnorm = lnorm;
+        B.perm = perm;
+        B.argmin = argmin_dev;
+        B.kr_bits = krmax;
+        B.cc = cc;
+        B.xs = KDE_TWO_PI / L;
+        B.loo = loo;
+        {
+            KdeProfScope _ps(ctx, PROF_CV_LOO);
+            if (scale_mode) cv_loo_kernel<true><<<NT, CV_T, 0, ctx->stream>>>(B);
+            else cv_loo_kernel<false><<<NT, CV_T, 0, ctx->stream>>>(B);
+        }
+        KDE_LAUNCHED(ctx, "cv_loo_kernel");
+    }
+    return KDE_OK;
+}
+
+extern "C" kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64_t N, double L,
+                             const double *cand, int32_t n_cand, double *cv_out, int32_t *argmin_out, float *loo_out,
+                             uint32_t flags)
+{
+    if (!ctx) return KDE_EINVAL;
+    const bool scale = (flags & KDE_CV_SCALE) != 0;
+    if (flags & ~KDE_CV_SCALE) return kde_fail(ctx, KDE_ENOTSUP, "kde_cv: unsupported flags 0x%x", flags);
+    if (N < 2 || N > 0xFFFFFFFFll || !(L > 0) || !u || !cand || !cv_out || n_cand < 1 || n_cand > CV_MAXC)
+        return kde_fail(ctx, KDE_EINVAL, "kde_cv: need 2 <= N < 2^32, L > 0, 1 <= n_cand <= %d, non-null arrays",
+                        CV_MAXC);
+    if (scale && !kappa_rel) return kde_fail(ctx, KDE_EINVAL, "kde_cv: KDE_CV_SCALE needs kappa_rel");
+    for (int c = 0; c < n_cand; ++c)
+        if (!(cand[c] > 0 && cand[c] <= KDE_KAPPA_MAX))
+            return kde_fail(ctx, KDE_EINVAL, "kde_cv: candidate %d = %g outside (0, 1e6]", c, cand[c]);
+    cudaSetDevice(ctx->device);
+    double *cvd = (double *)kde_ws(ctx, WS_CV_OUT, (size_t)n_cand * 8 + 64);
+    if (!cvd) return KDE_ENOMEM;
+    int *amin = (int *)(cvd + n_cand);
+    KDE_TRY(kde_cv_device(ctx, u, scale ? kappa_rel : nullptr, N, L, cand, n_cand, scale, cvd, amin, loo_out,
+                          nullptr));
+    KDE_CUDA(ctx, cudaMemcpyAsync(cv_out, cvd, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, ctx->stream), "cv copy");
+    int am = 0;
+    KDE_CUDA(ctx, cudaMemcpyAsync(&am, amin, 4, cudaMemcpyDeviceToHost, ctx->stream), "argmin copy");
+    KDE_TRY(kde_sync(ctx));
+    if (argmin_out) *argmin_out = am;
+    return KDE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Silverman particle-wise widths (Sec. II.C)
+// ---------------------------------------------------------------------------
+#define AD_BLOCKS 256
+__global__ void adapt_logsum_kernel(const float *loo, int64_t N, double K0, double *part)
+{
+    __shared__ double red[256];
+    const double n = (double)N;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)AD_BLOCKS * 256)
+        s += log(((n - 1.0) * (double)loo[i] + K0) / n);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+template <typename T>
+__global__ void adapt_apply_kernel(const float *loo, int64_t N, double xs, const double *kstar_dev, double kstar_h,
+                                   const double *part, double alpha, double kmin, double kmax, T *kappa_out,
+                                   T *norm_out)
+{
+    __shared__ double s_logg, s_K0, s_ks;
+    if (threadIdx.x == 0) {
+        double ks = kstar_dev ? *kstar_dev : kstar_h;
+        double s = 0.0;
+        for (int b = 0; b < AD_BLOCKS; ++b) s += part[b];
+        s_logg = s / (double)N;
+        s_ks = ks;
+        s_K0 = xs * kde_norm(ks);
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double n = (double)N;
+    double f = ((n - 1.0) * (double)loo[i] + s_K0) / n;
+    // lambda = (f/g)^-alpha, kappa = kappa* / lambda^2
+    double k = s_ks * exp(2.0 * alpha * (log(f) - s_logg));
+    k = k < kmin ? kmin : (k > kmax ? kmax : k);
+    kappa_out[i] = (T)k;
+    if (norm_out) norm_out[i] = (T)kde_norm((double)(T)k);
+}
+
+// the log-mean needs K0 = (2 pi / L) norm(kappa*) before kappa* is known on the host
+__global__ void adapt_logsum_dev_kernel(const float *loo, int64_t N, double xs, const double *kstar_dev, double kstar_h,
+                                        double *part)
+{
+    __shared__ double red[256];
+    const double n = (double)N;
+    const double K0 = xs * kde_norm(kstar_dev ? *kstar_dev : kstar_h);
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)AD_BLOCKS * 256)
+        s += log(((n - 1.0) * (double)loo[i] + K0) / n);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+kde_status kde_adapt_device(kde_ctx *ctx, const float *loo, int64_t N, double L, const double *kstar_dev,
+                            double kstar_host, double alpha, double kmin, double kmax, void *kappa_out,
+                            void *norm_out, bool f64)
+{
+    double *part = (double *)kde_ws(ctx, WS_CV_RED, AD_BLOCKS * 8);
+    if (!part) return KDE_ENOMEM;
+    const double xs = KDE_TWO_PI / L;
+    adapt_logsum_dev_kernel<<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part);
+    KDE_LAUNCHED(ctx, "adapt_logsum_kernel");
+    unsigned grid = (unsigned)((N + 255) / 256);
+    if (f64)
+        adapt_apply_kernel<double><<<grid, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part, alpha, kmin,
+                                                                   kmax, (double *)kappa_out, (double *)norm_out);
+    else
+        adapt_apply_kernel<float><<<grid, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part, alpha, kmin,
+                                                                  kmax, (float *)kappa_out, (float *)norm_out);
+    KDE_LAUNCHED(ctx, "adapt_apply_kernel");
+    return KDE_OK;
+}
+
+extern "C" kde_status kde_adapt_widths(kde_ctx *ctx, const float *loo, int64_t N, double L, double kappa_star,
+                                       double alpha, double kappa_min, double kappa_max, float *kappa_out)
+{
+    if (!ctx) return KDE_EINVAL;
+    if (N < 2 || !loo || !kappa_out || !(L > 0) || !(kappa_star > 0 && kappa_star <= KDE_KAPPA_MAX) ||
+        !(alpha >= 0) || !(kappa_min <= kappa_max))
+        return kde_fail(ctx, KDE_EINVAL, "kde_adapt_widths: bad arguments");
+    cudaSetDevice(ctx->device);
+    return kde_adapt_device(ctx, loo, N, L, nullptr, kappa_star, alpha, kappa_min, kappa_max, kappa_out, nullptr,
+                            false);
+}

@@ -1,0 +1,437 @@
+// deposit.cu -- KDE deposit (Eq. kde evaluated at the grid nodes).
+//
+//   rho_g = sum_i w_i (2 pi / L) norm(kappa_i) exp(-2 kappa_i sin^2((theta_g - theta_i)/2))
+//
+// Layout: particles are counting-sorted by cell.  One CTA takes a chunk of
+// DEP_CHUNK consecutive sorted particles, stages (beta sin, beta cos, w*norm)
+// of each in shared memory, and finds the node range its particles' truncated
+// kernels can reach (first/last cell +- the widest window).  Lanes own nodes
+// (node-owner formulation): a warp sweeps 32 consecutive nodes over a slice of
+// the chunk, so every particle value is a shared-memory broadcast and each
+// lane accumulates in a register without atomics.  Slices are combined in a
+// fixed order in shared memory.  Chunk partials are converted to int64 fixed
+// point (an exact power-of-two scale below the largest possible node value)
+// and added with integer atomics, so the grid sum is exact and independent of
+// the order in which chunks finish: results are bitwise reproducible.
+#include "common.cuh"
+
+#define DEP_THREADS 256
+#define DEP_WARPS (DEP_THREADS / 32)
+#define DEP_CHUNK 1024
+#define CV_MAXM 8192
+
+template <typename T> struct V2;
+template <> struct V2<float> { typedef float2 t; };
+template <> struct V2<double> { typedef double2 t; };
+
+template <typename T> struct DepRec {
+    T bs, bc, wn;
+};
+
+template <typename T> struct DepSrc {
+    const uint32_t *u;
+    int64_t N;
+    const T *kappa;      // per-particle widths, or nullptr
+    T kappa_u;           // uniform width
+    T kscale;            // widths are kscale * kappa[j] (CV scale mode), else 1
+    const T *norm;       // per-particle norm, or nullptr (computed from the width when kappa != nullptr)
+    const float *lnorm;  // log2 of per-particle norm (CV scale mode), or nullptr
+    T norm_u;            // uniform norm
+    const T *w;          // per-particle weights, or nullptr
+    T w_u;               // uniform weight
+    T coef;              // 2 pi / L (x units) or 1 (theta units)
+    int Ng;
+    const typename V2<T>::t *nodes;  // (sin, cos) of half node angles; nullptr: Ng is a power of two
+    long long *acc;
+    double bound;                    // largest possible node value
+    const unsigned int *wmax_bits;   // if not null: bound = N * coef * norm_bound * w_max (float bits)
+    double norm_bound;
+    unsigned int *status;
+};
+
+__device__ __forceinline__ int window_nodes_f(float kappa, int Ng, float xcut)
+{
+    float s2 = xcut * (float)(KDE_LN2 / 2.0) / kappa;
+    if (s2 >= 1.0f) return Ng;
+    float r = 2.0f * asinf(sqrtf(s2));
+    int w = (int)ceilf(r * (float)Ng * (float)(1.0 / KDE_TWO_PI)) + 1;
+    return w >= Ng ? Ng : w;
+}
+
+template <typename T>
+__device__ __forceinline__ void node_sc(const DepSrc<T> &S, int g, T &s, T &c)
+{
+    if (S.nodes) {
+        typename V2<T>::t v = S.nodes[g];
+        s = v.x;
+        c = v.y;
+    } else {
+        // power-of-two grid: g / Ng is exact
+        float sf, cf;
+        sincospif((float)g / (float)S.Ng, &sf, &cf);
+        s = sf;
+        c = cf;
+    }
+}
+
+template <typename T>
+__device__ void deposit_chunk_body(const DepSrc<T> &S, int64_t chunk, DepRec<T> *rec, T *part, int *red)
+{
+    const int64_t i0 = chunk * DEP_CHUNK;
+    if (i0 >= S.N) return;
+    const int n = (int)(S.N - i0 < DEP_CHUNK ? S.N - i0 : DEP_CHUNK);
+    const int Ng = S.Ng;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    int wloc = 0;
+    for (int t = tid; t < n; t += DEP_THREADS) {
+        int64_t j = i0 + t;
+        uint32_t uu = S.u[j];
+        T k = S.kappa ? S.kscale * S.kappa[j] : S.kappa_u;
+        if (!(k > (T)0 && k <= (T)KDE_KAPPA_MAX)) {
+            kde_flag(S.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
+            k = (T)KDE_KAPPA_MAX;
+        }
+        T nm;
+        if (S.lnorm) nm = (T)exp2f(S.lnorm[j]);
+        else if (S.norm) nm = S.norm[j];
+        else if (S.kappa) nm = (T)kde_norm((double)k);
+        else nm = S.norm_u;
+        T wj = S.w ? S.w[j] : S.w_u;
+        T sh, ch;
+        kde_half_sincos(uu, sh, ch);
+        T beta = sqrt((T)(2.0 * KDE_LOG2E) * k);
+        rec[t].bs = beta * sh;
+        rec[t].bc = beta * ch;
+        rec[t].wn = wj * S.coef * nm;
+        int wn_ = window_nodes_f((float)k, Ng, (float)KdeCut<T>::x);
+        wloc = wn_ > wloc ? wn_ : wloc;
+    }
+    // block maximum of the window
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        int v = __shfl_xor_sync(0xffffffffu, wloc, o);
+        wloc = v > wloc ? v : wloc;
+    }
+    if (lane == 0) red[warp] = wloc;
+    __syncthreads();
+    int W = 0;
+#pragma unroll
+    for (int k = 0; k < DEP_WARPS; ++k) W = red[k] > W ? red[k] : W;
+    const int c_first = kde_cell(S.u[i0], Ng), c_last = kde_cell(S.u[i0 + n - 1], Ng);
+    int g_lo = c_first - W;
+    int R = c_last + W - g_lo + 1;
+    if (R >= Ng || c_last < c_first) {
+        g_lo = 0;
+        R = Ng;
+    }
+    const int ngroups = (R + 31) >> 5;
+
+    double bound = S.bound;
+    if (S.wmax_bits) bound = (double)S.N * (double)S.coef * S.norm_bound * (double)__uint_as_float(*S.wmax_bits);
+    const double scale = kde_acc_scale(bound);
+
+    if (ngroups >= DEP_WARPS) {
+        for (int gi = warp; gi < ngroups; gi += DEP_WARPS) {
+            int r = gi * 32 + lane;
+            int g = g_lo + r;
+            g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
+            T Sg, Cg;
+            node_sc(S, r < R ? g : 0, Sg, Cg);
+            T acc = 0;
+#pragma unroll 4
+            for (int p = 0; p < n; ++p) {
+                DepRec<T> q = rec[p];
+                T s = Sg * q.bc - Cg * q.bs;
+                acc += kde_ex2(-s * s) * q.wn;
+            }
+            if (r < R) {
+                long long v = __double2ll_rn((double)acc * scale);
+                if (v) atomicAdd((unsigned long long *)&S.acc[g], (unsigned long long)v);
+            }
+        }
+        return;
+    }
+    const int slices = DEP_WARPS / ngroups;
+    const int gi = warp % ngroups, sl = warp / ngroups;
+    if (sl < slices) {
+        int p0 = (int)((int64_t)n * sl / slices), p1 = (int)((int64_t)n * (sl + 1) / slices);
+        int r = gi * 32 + lane;
+        int g = g_lo + r;
+        g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
+        T Sg, Cg;
+        node_sc(S, r < R ? g : 0, Sg, Cg);
+        T acc = 0;
+#pragma unroll 4
+        for (int p = p0; p < p1; ++p) {
+            DepRec<T> q = rec[p];
+            T s = Sg * q.bc - Cg * q.bs;
+            acc += kde_ex2(-s * s) * q.wn;
+        }
+        part[sl * (DEP_WARPS * 32) + r] = acc;
+    }
+    __syncthreads();
+    for (int r = tid; r < ngroups * 32; r += DEP_THREADS) {
+        if (r >= R) continue;
+        T acc = 0;
+        for (int k = 0; k < slices; ++k) acc += part[k * (DEP_WARPS * 32) + r];
+        int g = g_lo + r;
+        g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
+        long long v = __double2ll_rn((double)acc * scale);
+        if (v) atomicAdd((unsigned long long *)&S.acc[g], (unsigned long long)v);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DEP_THREADS) deposit_chunk_kernel(DepSrc<T> S)
+{
+    __shared__ DepRec<T> rec[DEP_CHUNK];
+    __shared__ T part[DEP_WARPS * 32 * DEP_WARPS];
+    __shared__ int red[DEP_WARPS];
+    deposit_chunk_body<T>(S, blockIdx.x, rec, part, red);
+}
+
+// acc -> real values
+template <typename T>
+__global__ void acc_to_real_kernel(const long long *acc, int Ng, double bound, const unsigned int *wmax_bits,
+                                   double wscale, T *out)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Ng) return;
+    double b = wmax_bits ? wscale * (double)__uint_as_float(*wmax_bits) : bound;
+    out[g] = (T)((double)acc[g] / kde_acc_scale(b));
+}
+
+// largest weight (non-negative floats order like their bit patterns)
+template <typename T>
+__global__ void wmax_kernel(const T *w, int64_t N, unsigned int *wmax_bits, unsigned int *status)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    for (; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = (float)w[i];
+        if (!(v >= 0.f) || isinf(v)) kde_flag(status, KDE_DEV_BAD_ARG, (unsigned)i);
+        else m = fmaxf(m, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // round the maximum up by one ulp so that the float bound of a double weight still bounds it
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(wmax_bits, __float_as_uint(m) + 1u);
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,
+                              const T *w, T w_u, int64_t N, int Ng, double coef, long long *acc, double bound,
+                              const unsigned int *wmax_bits, double norm_bound)
+{
+    KDE_CUDA(ctx, cudaMemsetAsync(acc, 0, (size_t)Ng * sizeof(long long), ctx->stream), "acc memset");
+    if (N == 0) return KDE_OK;
+    const void *nodes = kde_node_table(ctx, Ng, sizeof(T) == 8);
+    if (!nodes) return KDE_ENOMEM;
+    DepSrc<T> S{};
+    S.u = u;
+    S.N = N;
+    S.kappa = kappa;
+    S.kappa_u = kappa_u;
+    S.kscale = (T)1;
+    S.norm = norm;
+    S.lnorm = nullptr;
+    S.norm_u = norm_u;
+    S.w = w;
+    S.w_u = w_u;
+    S.coef = (T)coef;
+    S.Ng = Ng;
+    S.nodes = (const typename V2<T>::t *)nodes;
+    S.acc = acc;
+    S.bound = bound;
+    S.wmax_bits = wmax_bits;
+    S.norm_bound = norm_bound;
+    S.status = ctx->d_status;
+    unsigned grid = (unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK);
+    {
+        KdeProfScope _ps(ctx, PROF_DEPOSIT);
+    deposit_chunk_kernel<T><<<grid, DEP_THREADS, 0, ctx->stream>>>(S);
+    }
+    KDE_LAUNCHED(ctx, "deposit_chunk_kernel");
+    return KDE_OK;
+}
+
+template <typename T>
+kde_status kde_acc_to_real(kde_ctx *ctx, const long long *acc, int Ng, double bound, const unsigned int *wmax_bits,
+                           double wscale, T *out)
+{
+    acc_to_real_kernel<T><<<(Ng + 255) / 256, 256, 0, ctx->stream>>>(acc, Ng, bound, wmax_bits, wscale, out);
+    KDE_LAUNCHED(ctx, "acc_to_real_kernel");
+    return KDE_OK;
+}
+
+template kde_status kde_deposit_sorted<float>(kde_ctx *, const uint32_t *, const float *, float, const float *, float,
+                                              const float *, float, int64_t, int, double, long long *, double,
+                                              const unsigned int *, double);
+template kde_status kde_deposit_sorted<double>(kde_ctx *, const uint32_t *, const double *, double, const double *,
+                                               double, const double *, double, int64_t, int, double, long long *,
+                                               double, const unsigned int *, double);
+template kde_status kde_acc_to_real<float>(kde_ctx *, const long long *, int, double, const unsigned int *, double,
+                                           float *);
+template kde_status kde_acc_to_real<double>(kde_ctx *, const long long *, int, double, const unsigned int *, double,
+                                            double *);
+
+// ---------------------------------------------------------------------------
+// CV integral term: the deposit of every candidate on its own power-of-two
+// grid of M_c points (theta units, w = 1/N), one grid per blockIdx.y.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int cv_grid_points(double kappa_max)
+{
+    // the trapezoid rule on M points integrates fhat^2 exactly up to aliased
+    // modes near M/2, whose weight A_{M/2}^2 ~ exp(-(M/2)^2 / kappa) is below
+    // 1e-17 once M >= 12.5 sqrt(kappa)
+    double need = 12.5 * sqrt(kappa_max) + 1.0;
+    int M = 64;
+    while (M < need && M < CV_MAXM) M <<= 1;
+    return M;
+}
+
+__global__ void __launch_bounds__(DEP_THREADS)
+    cv_grid_deposit_kernel(const uint32_t *u, int64_t N, const float *kappa_rel, const float *lnorm,
+                           const unsigned int *krmax_bits, CandList cl, long long *acc, unsigned int *status)
+{
+    __shared__ DepRec<float> rec[DEP_CHUNK];
+    __shared__ float part[DEP_WARPS * 32 * DEP_WARPS];
+    __shared__ int red[DEP_WARPS];
+    const int c = blockIdx.y;
+    DepSrc<float> S{};
+    S.u = u;
+    S.N = N;
+    S.coef = 1.0f;
+    S.w = nullptr;
+    S.w_u = (float)(1.0 / (double)N);
+    S.nodes = nullptr;
+    S.acc = acc + (size_t)c * CV_MAXM;
+    S.status = status;
+    S.wmax_bits = nullptr;
+    double kmax;
+    if (cl.scale_mode) {
+        kmax = cl.k[c] * (double)__uint_as_float(*krmax_bits);
+        S.kappa = kappa_rel;
+        S.kscale = (float)cl.k[c];
+        S.lnorm = lnorm + (size_t)c * N;
+        S.norm = nullptr;
+        S.bound = kde_norm(kmax);  // N * (1/N) * largest norm
+    } else {
+        kmax = cl.k[c];
+        S.kappa = nullptr;
+        S.kappa_u = (float)cl.k[c];
+        S.kscale = 1.0f;
+        S.lnorm = nullptr;
+        S.norm = nullptr;
+        S.norm_u = (float)kde_norm(kmax);
+        S.bound = kde_norm(kmax);
+    }
+    S.Ng = cv_grid_points(kmax);
+    deposit_chunk_body<float>(S, blockIdx.x, rec, part, red);
+}
+
+// FP64 trapezoid sum of fhat^2 on each candidate's grid: f2[c] = (2 pi / M) sum_g fhat_g^2
+__global__ void cv_grid_square_kernel(const long long *acc, const float *kappa_rel_unused,
+                                      const unsigned int *krmax_bits, CandList cl, double *f2)
+{
+    const int c = blockIdx.x;
+    double kmax = cl.scale_mode ? cl.k[c] * (double)__uint_as_float(*krmax_bits) : cl.k[c];
+    const int M = cv_grid_points(kmax);
+    const double inv = 1.0 / kde_acc_scale(kde_norm(kmax));
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int g = threadIdx.x; g < M; g += blockDim.x) {
+        double f = (double)acc[(size_t)c * CV_MAXM + g] * inv;
+        s += f * f;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) f2[c] = KDE_TWO_PI / M * red[0];
+    (void)kappa_rel_unused;
+}
+
+kde_status kde_cv_integral_term(kde_ctx *ctx, const uint32_t *u_sorted, int64_t N, const float *kappa_rel,
+                                const float *lnorm, const unsigned int *krmax_bits, const CandList &cl,
+                                double *f2_out)
+{
+    long long *acc = (long long *)kde_ws(ctx, WS_CV_ACC, (size_t)cl.n * CV_MAXM * sizeof(long long));
+    if (!acc) return KDE_ENOMEM;
+    KDE_CUDA(ctx, cudaMemsetAsync(acc, 0, (size_t)cl.n * CV_MAXM * sizeof(long long), ctx->stream), "cv acc memset");
+    dim3 grid((unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK), (unsigned)cl.n);
+    {
+        KdeProfScope _ps(ctx, PROF_CV_GRID);
+    cv_grid_deposit_kernel<<<grid, DEP_THREADS, 0, ctx->stream>>>(u_sorted, N, kappa_rel, lnorm, krmax_bits, cl, acc,
+                                                                    ctx->d_status);
+    }
+    KDE_LAUNCHED(ctx, "cv_grid_deposit_kernel");
+    cv_grid_square_kernel<<<cl.n, 256, 0, ctx->stream>>>(acc, kappa_rel, krmax_bits, cl, f2_out);
+    KDE_LAUNCHED(ctx, "cv_grid_square_kernel");
+    return KDE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+template <typename T>
+static kde_status deposit_api(kde_ctx *ctx, const uint32_t *u, const T *kappa, double kappa_u, const T *weight,
+                              int64_t N, int Ng, double L, T *rho_out)
+{
+    cudaSetDevice(ctx->device);
+    long long *acc = (long long *)kde_ws(ctx, WS_ACC, (size_t)Ng * sizeof(long long));
+    if (!acc) return KDE_ENOMEM;
+    if (N == 0) {
+        KDE_CUDA(ctx, cudaMemsetAsync(rho_out, 0, (size_t)Ng * sizeof(T), ctx->stream), "rho memset");
+        return KDE_OK;
+    }
+    uint32_t *us = (uint32_t *)kde_ws(ctx, WS_SORT_U, (size_t)N * 4);
+    T *ks = kappa ? (T *)kde_ws(ctx, WS_SORT_P0, (size_t)N * sizeof(T)) : nullptr;
+    T *ws = weight ? (T *)kde_ws(ctx, WS_SORT_P1, (size_t)N * sizeof(T)) : nullptr;
+    if (!us || (kappa && !ks) || (weight && !ws)) return KDE_ENOMEM;
+    SortPayload pl[2];
+    int npl = 0;
+    if (kappa) pl[npl++] = SortPayload{kappa, ks, (int)sizeof(T)};
+    if (weight) pl[npl++] = SortPayload{weight, ws, (int)sizeof(T)};
+    KDE_TRY(kde_sort_by_bin(ctx, u, N, Ng, us, pl, npl, nullptr));
+    const double coef = KDE_TWO_PI / L;
+    double norm_u = kappa ? 0.0 : kde_norm(kappa_u);
+    double norm_bound = kappa ? kde_norm(KDE_KAPPA_MAX) : norm_u;
+    double w_u = L / (double)N;
+    unsigned int *wmax = nullptr;
+    double bound = (double)N * w_u * coef * norm_bound;
+    if (weight) {
+        wmax = (unsigned int *)kde_ws(ctx, WS_WMAX, 64);
+        if (!wmax) return KDE_ENOMEM;
+        KDE_CUDA(ctx, cudaMemsetAsync(wmax, 0, 4, ctx->stream), "wmax memset");
+        int blocks = (int)((N + 255) / 256);
+        blocks = blocks > ctx->sm_count * 8 ? ctx->sm_count * 8 : blocks;
+        wmax_kernel<T><<<blocks, 256, 0, ctx->stream>>>(weight, N, wmax, ctx->d_status);
+        KDE_LAUNCHED(ctx, "wmax_kernel");
+    }
+    KDE_TRY(kde_deposit_sorted<T>(ctx, us, ks, (T)kappa_u, nullptr, (T)norm_u, ws, (T)w_u, N, Ng, coef, acc, bound,
+                                  wmax, norm_bound));
+    return kde_acc_to_real<T>(ctx, acc, Ng, bound, wmax, (double)N * coef * norm_bound, rho_out);
+}
+
+extern "C" kde_status kde_deposit(kde_ctx *ctx, const uint32_t *u, const void *kappa, double kappa_uniform,
+                                  const void *weight, int64_t N, int32_t Ng, double L, void *rho_out, uint32_t flags)
+{
+    if (!ctx) return KDE_EINVAL;
+    if (N < 0 || Ng < 1 || Ng > KDE_MAX_NG || !(L > 0) || !rho_out || (N > 0 && !u))
+        return kde_fail(ctx, KDE_EINVAL, "kde_deposit: need N >= 0, 1 <= Ng <= %d, L > 0, non-null u and rho_out",
+                        KDE_MAX_NG);
+    if (!kappa && !(kappa_uniform > 0 && kappa_uniform <= KDE_KAPPA_MAX))
+        return kde_fail(ctx, KDE_EINVAL, "kde_deposit: kappa_uniform must be in (0, 1e6]");
+    if (N > 0xFFFFFFFFll) return kde_fail(ctx, KDE_EINVAL, "kde_deposit: N must be below 2^32");
+    if (flags & ~KDE_F64) return kde_fail(ctx, KDE_ENOTSUP, "kde_deposit: unsupported flags 0x%x", flags);
+    if (flags & KDE_F64)
+        return deposit_api<double>(ctx, u, (const double *)kappa, kappa_uniform, (const double *)weight, N, Ng, L,
+                                   (double *)rho_out);
+    return deposit_api<float>(ctx, u, (const float *)kappa, kappa_uniform, (const float *)weight, N, Ng, L,
+                              (float *)rho_out);
+}

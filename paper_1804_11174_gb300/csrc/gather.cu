@@ -1,0 +1,276 @@
+// gather.cu -- field interpolation through the deposit's kernels, fused with
+// the leap-frog push of the PIC cycle (Sec. III.A).
+//
+//   E_i = (2 pi / Ng) norm(kappa_i) sum_g E_g exp(-2 kappa_i sin^2((theta_g - theta_i)/2))
+//
+// Layout: the whole grid (half-angle sine, cosine, field) sits in shared
+// memory.  Threads own particles (cell-sorted, so a warp's particles share a
+// few cells); each warp sweeps one node window covering all of its lanes'
+// truncated supports, so every node read is a shared-memory broadcast.  The
+// push, the write-back of the particle state and (block 0) the field energy
+// ride in the same kernel.
+#include "common.cuh"
+
+#define GAT_THREADS 256
+
+struct __align__(16) GNodeD {
+    double x, y, z, w;
+};
+template <typename T> struct GNode;
+template <> struct GNode<float> { typedef float4 t; };
+template <> struct GNode<double> { typedef GNodeD t; };
+
+template <typename T> struct V2g;
+template <> struct V2g<float> { typedef float2 t; };
+template <> struct V2g<double> { typedef double2 t; };
+
+template <typename T> struct GatherArgs {
+    const uint32_t *u;
+    const T *kappa;
+    T kappa_u;
+    const T *norm;
+    T norm_u;
+    int64_t N;
+    const T *field;
+    int Ng;
+    const typename V2g<T>::t *nodes;
+    T coef;  // 2 pi / Ng
+    T *out;
+    const uint32_t *perm;
+    // push (active when u_out != nullptr)
+    const T *v_in;
+    uint32_t *u_out;
+    T *v_out;
+    T *kappa_out;
+    const T *norm_in;
+    T *norm_out;
+    const uint32_t *id_in;
+    uint32_t *id_out;
+    T kick_qm_dt;
+    T dt_scale;
+    double *energy;
+    const double *kstar_in;
+    double *kstar_out;
+    double dx;
+    unsigned int *status;
+};
+
+__device__ __forceinline__ int window_nodes_g(float kappa, int Ng, float xcut)
+{
+    float s2 = xcut * (float)(KDE_LN2 / 2.0) / kappa;
+    if (s2 >= 1.0f) return Ng;
+    float r = 2.0f * asinf(sqrtf(s2));
+    int w = (int)ceilf(r * (float)Ng * (float)(1.0 / KDE_TWO_PI)) + 1;
+    return w >= Ng ? Ng : w;
+}
+
+__device__ __forceinline__ uint32_t advance_position(uint32_t u, float d)
+{
+    // d = displacement in units of 2^-32 L
+    if (fabsf(d) < 2147483520.0f) return u + (uint32_t)__float2int_rn(d);
+    d = fmodf(d, 4294967296.0f);
+    return u + (uint32_t)(long long)__float2ll_rn(d);
+}
+__device__ __forceinline__ uint32_t advance_position(uint32_t u, double d)
+{
+    d = fmod(d, 4294967296.0);
+    return u + (uint32_t)(long long)__double2ll_rn(d);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GAT_THREADS) gather_kernel(GatherArgs<T> A)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    typename GNode<T>::t *node = (typename GNode<T>::t *)sm;
+    const int Ng = A.Ng;
+    for (int g = threadIdx.x; g < Ng; g += GAT_THREADS) {
+        typename V2g<T>::t sc = A.nodes[g];
+        typename GNode<T>::t q;
+        q.x = sc.x;
+        q.y = sc.y;
+        q.z = A.field[g];
+        q.w = 0;
+        node[g] = q;
+    }
+    if (blockIdx.x == 0 && A.energy) {
+        __shared__ double red[GAT_THREADS];
+        double s = 0.0;
+        for (int g = threadIdx.x; g < Ng; g += GAT_THREADS) s += (double)A.field[g] * (double)A.field[g];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = GAT_THREADS / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            A.energy[0] = 0.5 * red[0] * A.dx;
+            if (A.kstar_out) A.kstar_out[0] = A.kstar_in ? A.kstar_in[0] : (double)A.kappa_u;
+        }
+    }
+    __syncthreads();
+
+    const int64_t j = (int64_t)blockIdx.x * GAT_THREADS + threadIdx.x;
+    const bool valid = j < A.N;
+    uint32_t uu = valid ? A.u[j] : 0u;
+    T k = A.kappa ? (valid ? A.kappa[j] : (T)1) : A.kappa_u;
+    if (valid && !(k > (T)0 && k <= (T)KDE_KAPPA_MAX)) {
+        kde_flag(A.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
+        k = (T)KDE_KAPPA_MAX;
+    }
+    T nm = A.norm ? (valid ? A.norm[j] : (T)0) : (A.kappa ? (T)kde_norm((double)k) : A.norm_u);
+    T sh, ch;
+    kde_half_sincos(uu, sh, ch);
+    T beta = sqrt((T)(2.0 * KDE_LOG2E) * k);
+    const T bs = beta * sh, bc = beta * ch;
+    const int cell = kde_cell(uu, Ng);
+    const int W = window_nodes_g((float)k, Ng, (float)KdeCut<T>::x);
+    // warp-uniform window [lo, hi] covering every valid lane's support
+    int lo = valid ? cell - W : 0x3fffffff, hi = valid ? cell + W : -0x3fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    int len = hi - lo + 1;
+    if (len >= Ng) {
+        lo = 0;
+        len = Ng;
+    }
+    if (len <= 0) return;  // whole warp past the end
+    int g = lo % Ng;
+    if (g < 0) g += Ng;
+    T acc0 = 0, acc1 = 0;
+    int t = 0;
+    for (; t + 1 < len; t += 2) {
+        typename GNode<T>::t q0 = node[g];
+        int g1 = g + 1 == Ng ? 0 : g + 1;
+        typename GNode<T>::t q1 = node[g1];
+        g = g1 + 1 == Ng ? 0 : g1 + 1;
+        T s0 = q0.x * bc - q0.y * bs;
+        T s1 = q1.x * bc - q1.y * bs;
+        acc0 += kde_ex2(-s0 * s0) * q0.z;
+        acc1 += kde_ex2(-s1 * s1) * q1.z;
+    }
+    if (t < len) {
+        typename GNode<T>::t q0 = node[g];
+        T s0 = q0.x * bc - q0.y * bs;
+        acc0 += kde_ex2(-s0 * s0) * q0.z;
+    }
+    if (!valid) return;
+    const T Ei = (acc0 + acc1) * nm * A.coef;
+    if (A.u_out) {
+        T v = A.v_in[j] + A.kick_qm_dt * Ei;
+        A.v_out[j] = v;
+        A.u_out[j] = advance_position(uu, v * A.dt_scale);
+        if (A.kappa_out) A.kappa_out[j] = k;
+        if (A.norm_out) A.norm_out[j] = A.norm_in[j];
+        if (A.id_out) A.id_out[j] = A.id_in[j];
+    } else {
+        A.out[A.perm ? A.perm[j] : j] = Ei;
+    }
+}
+
+template <typename T>
+static kde_status launch_gather(kde_ctx *ctx, GatherArgs<T> &A)
+{
+    const void *nodes = kde_node_table(ctx, A.Ng, sizeof(T) == 8);
+    if (!nodes) return KDE_ENOMEM;
+    A.nodes = (const typename V2g<T>::t *)nodes;
+    A.status = ctx->d_status;
+    size_t smem = (size_t)A.Ng * sizeof(typename GNode<T>::t);
+    static bool attr[2] = {false, false};
+    if (!attr[sizeof(T) == 8]) {
+        cudaFuncSetAttribute(gather_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             KDE_MAX_NG * (int)sizeof(typename GNode<T>::t));
+        attr[sizeof(T) == 8] = true;
+    }
+    unsigned grid = (unsigned)((A.N + GAT_THREADS - 1) / GAT_THREADS);
+    if (grid == 0) grid = 1;
+    {
+        KdeProfScope _ps(ctx, PROF_GATHER);
+    gather_kernel<T><<<grid, GAT_THREADS, smem, ctx->stream>>>(A);
+    }
+    KDE_LAUNCHED(ctx, "gather_kernel");
+    return KDE_OK;
+}
+
+template <typename T>
+kde_status kde_gather_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,
+                             int64_t N, const T *field, int Ng, double coef, T *out, const uint32_t *perm,
+                             const PushArgs *push)
+{
+    GatherArgs<T> A{};
+    A.u = u;
+    A.kappa = kappa;
+    A.kappa_u = kappa_u;
+    A.norm = norm;
+    A.norm_u = norm_u;
+    A.N = N;
+    A.field = field;
+    A.Ng = Ng;
+    A.coef = (T)coef;
+    A.out = out;
+    A.perm = perm;
+    if (push) {
+        A.v_in = (const T *)push->v_in;
+        A.u_out = push->u_out;
+        A.v_out = (T *)push->v_out;
+        A.kappa_out = (T *)push->kappa_out;
+        A.norm_in = (const T *)push->norm_in;
+        A.norm_out = (T *)push->norm_out;
+        A.id_in = push->id_in;
+        A.id_out = push->id_out;
+        A.kick_qm_dt = (T)(push->kick * push->qm_dt);
+        A.dt_scale = (T)push->dt_scale;
+        A.energy = push->energy;
+        A.kstar_in = push->kstar_in;
+        A.kstar_out = push->kstar_out;
+        A.dx = push->dx;
+    }
+    return launch_gather<T>(ctx, A);
+}
+
+template kde_status kde_gather_sorted<float>(kde_ctx *, const uint32_t *, const float *, float, const float *, float,
+                                             int64_t, const float *, int, double, float *, const uint32_t *,
+                                             const PushArgs *);
+template kde_status kde_gather_sorted<double>(kde_ctx *, const uint32_t *, const double *, double, const double *,
+                                              double, int64_t, const double *, int, double, double *,
+                                              const uint32_t *, const PushArgs *);
+
+// ---------------------------------------------------------------------------
+template <typename T>
+static kde_status gather_api(kde_ctx *ctx, const uint32_t *u, const T *kappa, double kappa_u, int64_t N,
+                             const T *field, int Ng, double L, T *out)
+{
+    cudaSetDevice(ctx->device);
+    uint32_t *us = (uint32_t *)kde_ws(ctx, WS_SORT_U, (size_t)N * 4);
+    uint32_t *perm = (uint32_t *)kde_ws(ctx, WS_SORT_PERM, (size_t)N * 4);
+    T *ks = kappa ? (T *)kde_ws(ctx, WS_SORT_P0, (size_t)N * sizeof(T)) : nullptr;
+    if (!us || !perm || (kappa && !ks)) return KDE_ENOMEM;
+    SortPayload pl[1];
+    int npl = 0;
+    if (kappa) pl[npl++] = SortPayload{kappa, ks, (int)sizeof(T)};
+    KDE_TRY(kde_sort_by_bin(ctx, u, N, Ng, us, pl, npl, perm));
+    double norm_u = kappa ? 0.0 : kde_norm(kappa_u);
+    return kde_gather_sorted<T>(ctx, us, ks, (T)kappa_u, nullptr, (T)norm_u, N, field, Ng, KDE_TWO_PI / Ng, out, perm,
+                                nullptr);
+}
+
+extern "C" kde_status kde_gather(kde_ctx *ctx, const uint32_t *u, const void *kappa, double kappa_uniform, int64_t N,
+                                 const void *field, int32_t Ng, double L, void *out, uint32_t flags)
+{
+    if (!ctx) return KDE_EINVAL;
+    if (N < 0 || Ng < 1 || Ng > KDE_MAX_NG || !(L > 0) || !field || (N > 0 && (!u || !out)))
+        return kde_fail(ctx, KDE_EINVAL, "kde_gather: need N >= 0, 1 <= Ng <= %d, L > 0, non-null arrays",
+                        KDE_MAX_NG);
+    if (!kappa && !(kappa_uniform > 0 && kappa_uniform <= KDE_KAPPA_MAX))
+        return kde_fail(ctx, KDE_EINVAL, "kde_gather: kappa_uniform must be in (0, 1e6]");
+    if (N > 0xFFFFFFFFll) return kde_fail(ctx, KDE_EINVAL, "kde_gather: N must be below 2^32");
+    if (flags & ~KDE_F64) return kde_fail(ctx, KDE_ENOTSUP, "kde_gather: unsupported flags 0x%x", flags);
+    if (N == 0) return KDE_OK;
+    if (flags & KDE_F64)
+        return gather_api<double>(ctx, u, (const double *)kappa, kappa_uniform, N, (const double *)field, Ng, L,
+                                  (double *)out);
+    return gather_api<float>(ctx, u, (const float *)kappa, kappa_uniform, N, (const float *)field, Ng, L,
+                             (float *)out);
+}

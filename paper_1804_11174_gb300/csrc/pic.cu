@@ -1,0 +1,143 @@
+// pic.cu -- the electrostatic PIC cycle of Sec. III.A on the device.
+//
+// Per step (all stream-ordered, no host synchronisation):
+//   [width update: CV over the uniform candidates, kappa* = argmin on the
+//    device, leave-one-out pilot densities, Silverman widths + norms]
+//   counting sort by cell (positions, velocities, widths, norms, labels)
+//   deposit -> int64 grid accumulators
+//   Poisson solve straight from the accumulators (mean removed in FP64)
+//   gather + leap-frog push + write-back + field energy (one kernel)
+#include "common.cuh"
+
+template <typename T>
+__global__ void norm_from_kappa_kernel(const T *kappa, int64_t N, T *norm, unsigned int *status)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double k = (double)kappa[i];
+    if (!(k > 0 && k <= KDE_KAPPA_MAX)) {
+        kde_flag(status, KDE_DEV_KAPPA_RANGE, (unsigned)i);
+        k = KDE_KAPPA_MAX;
+    }
+    norm[i] = (T)kde_norm(k);
+}
+
+template <typename T>
+static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
+{
+    const int64_t N = st->N;
+    const int Ng = st->Ng;
+    const double L = st->L;
+    const bool per = st->kappa != nullptr;
+    const bool sched = st->width_every > 0 && st->n_cand > 0;
+    const bool fd = (st->flags & KDE_POISSON_FD) != 0;
+    T *norm_arr = (T *)st->kappa_norm;
+
+    // the width update (CV) shares the sort slots; size them for it up front and
+    // fetch the pointers again after every update, since a slot may be regrown
+    const size_t npad = (size_t)((N + 255) / 256) * 256;
+    uint32_t *us = nullptr, *ids = nullptr;
+    T *vs = nullptr, *ks = nullptr, *ns = nullptr;
+    auto fetch_ws = [&]() -> bool {
+        us = (uint32_t *)kde_ws(ctx, WS_SORT_U, npad * 4);
+        vs = (T *)kde_ws(ctx, WS_SORT_P0, npad * sizeof(T));
+        ks = per ? (T *)kde_ws(ctx, WS_SORT_P1, npad * sizeof(T)) : nullptr;
+        ns = per ? (T *)kde_ws(ctx, WS_SORT_P2, npad * sizeof(T)) : nullptr;
+        ids = st->id ? (uint32_t *)kde_ws(ctx, WS_SORT_P3, npad * 4) : nullptr;
+        return us && vs && (!per || (ks && ns)) && (!st->id || ids);
+    };
+    if (!fetch_ws()) return KDE_ENOMEM;
+    long long *acc = (long long *)kde_ws(ctx, WS_ACC, (size_t)Ng * 8);
+    T *E = (T *)kde_ws(ctx, WS_GRID0, (size_t)Ng * sizeof(T));
+    float *loo = sched ? (float *)kde_ws(ctx, WS_PIC_LOO, (size_t)N * 4) : nullptr;
+    double *ks_dev = sched ? (double *)kde_ws(ctx, WS_PIC_KS, 64) : nullptr;
+    double *cv_dev = sched ? (double *)kde_ws(ctx, WS_CV_OUT, (size_t)st->n_cand * 8 + 64) : nullptr;
+    if (!acc || !E || (sched && (!loo || !ks_dev || !cv_dev))) return KDE_ENOMEM;
+    int *amin_dev = sched ? (int *)(cv_dev + st->n_cand) : nullptr;
+
+    if (per) {
+        norm_from_kappa_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>((const T *)st->kappa, N,
+                                                                                      norm_arr, ctx->d_status);
+        KDE_LAUNCHED(ctx, "norm_from_kappa_kernel");
+    }
+    const double coef = KDE_TWO_PI / L;
+    const double w_u = L / (double)N;
+    for (int s = 0; s < n_steps; ++s) {
+        const int64_t step = st->step;
+        const bool update = sched && step % st->width_every == 0;
+        if (update) {
+            KDE_TRY(kde_cv_device(ctx, st->u, nullptr, N, L, st->cand, st->n_cand, false, cv_dev, amin_dev, loo,
+                                  ks_dev));
+            KDE_TRY(kde_adapt_device(ctx, loo, N, L, ks_dev, 0.0, st->alpha, st->kappa_min, st->kappa_max, st->kappa,
+                                     norm_arr, sizeof(T) == 8));
+            if (!fetch_ws()) return KDE_ENOMEM;
+        }
+        SortPayload pl[4];
+        int npl = 0;
+        pl[npl++] = SortPayload{st->v, vs, (int)sizeof(T)};
+        if (per) {
+            pl[npl++] = SortPayload{st->kappa, ks, (int)sizeof(T)};
+            pl[npl++] = SortPayload{norm_arr, ns, (int)sizeof(T)};
+        }
+        if (st->id) pl[npl++] = SortPayload{st->id, ids, 4};
+        KDE_TRY(kde_sort_by_bin(ctx, st->u, N, Ng, us, pl, npl, nullptr));
+
+        const double norm_u = per ? 0.0 : kde_norm(st->kappa_uniform);
+        const double norm_bound = per ? kde_norm(KDE_KAPPA_MAX) : norm_u;
+        const double bound = (double)N * w_u * coef * norm_bound;
+        KDE_TRY(kde_deposit_sorted<T>(ctx, us, ks, (T)st->kappa_uniform, ns, (T)norm_u, nullptr, (T)w_u, N, Ng, coef,
+                                      acc, bound, nullptr, norm_bound));
+        KDE_TRY(kde_poisson_impl<T>(ctx, nullptr, acc, 1.0 / kde_acc_scale(bound), Ng, L, st->charge,
+                                    st->background, fd, E));
+
+        PushArgs pa{};
+        pa.v_in = vs;
+        pa.u_out = st->u;
+        pa.v_out = st->v;
+        pa.kappa_out = per ? st->kappa : nullptr;
+        pa.norm_in = ns;
+        pa.norm_out = per ? norm_arr : nullptr;
+        pa.id_in = ids;
+        pa.id_out = st->id;
+        pa.kick = (step == 0 && !(st->flags & PIC_NO_BACKSTEP)) ? 0.5 : 1.0;
+        pa.qm_dt = st->qm * st->dt;
+        pa.dt_scale = st->dt * 4294967296.0 / L;
+        pa.energy = st->energy ? st->energy + step : nullptr;
+        pa.kstar_in = update || sched ? ks_dev : nullptr;
+        pa.kstar_out = st->kappa_star ? st->kappa_star + step : nullptr;
+        pa.dx = L / Ng;
+        KDE_TRY(kde_gather_sorted<T>(ctx, us, ks, (T)st->kappa_uniform, ns, (T)norm_u, N, E, Ng, KDE_TWO_PI / Ng,
+                                     nullptr, nullptr, &pa));
+        st->step = step + 1;
+    }
+    return KDE_OK;
+}
+
+extern "C" kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps)
+{
+    if (!ctx) return KDE_EINVAL;
+    if (!st || n_steps < 0) return kde_fail(ctx, KDE_EINVAL, "pic_step: null state or negative step count");
+    if (st->N < 1 || st->N > 0xFFFFFFFFll || st->Ng < 1 || st->Ng > KDE_MAX_NG || !(st->L > 0) || !(st->dt > 0) ||
+        !st->u || !st->v || st->step < 0)
+        return kde_fail(ctx, KDE_EINVAL, "pic_step: need 1 <= N < 2^32, 1 <= Ng <= %d, L > 0, dt > 0, u and v",
+                        KDE_MAX_NG);
+    if (st->flags & ~(KDE_F64 | KDE_POISSON_FD | PIC_NO_BACKSTEP))
+        return kde_fail(ctx, KDE_ENOTSUP, "pic_step: unsupported flags 0x%x", st->flags);
+    if (st->kappa && !st->kappa_norm)
+        return kde_fail(ctx, KDE_EINVAL, "pic_step: per-particle widths need the kappa_norm array");
+    if (!st->kappa && !(st->kappa_uniform > 0 && st->kappa_uniform <= KDE_KAPPA_MAX))
+        return kde_fail(ctx, KDE_EINVAL, "pic_step: kappa_uniform must be in (0, 1e6]");
+    if (st->width_every > 0 && st->n_cand > 0) {
+        if (!st->kappa || !st->cand || st->n_cand > 256 || st->N < 2 || !(st->alpha >= 0) ||
+            !(st->kappa_min <= st->kappa_max))
+            return kde_fail(ctx, KDE_EINVAL,
+                            "pic_step: the width schedule needs a kappa array, 1..256 host candidates, N >= 2, "
+                            "alpha >= 0 and kappa_min <= kappa_max");
+        for (int c = 0; c < st->n_cand; ++c)
+            if (!(st->cand[c] > 0 && st->cand[c] <= KDE_KAPPA_MAX))
+                return kde_fail(ctx, KDE_EINVAL, "pic_step: candidate %d outside (0, 1e6]", c);
+    }
+    cudaSetDevice(ctx->device);
+    if (st->flags & KDE_F64) return pic_run<double>(ctx, st, n_steps);
+    return pic_run<float>(ctx, st, n_steps);
+}

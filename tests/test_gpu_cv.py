@@ -1,0 +1,143 @@
+"""GPU parity of the cross-validation (Eq. cv_def) and Silverman widths against the oracle.
+
+Tolerance for CV values: 2e-6 of max |CV|.  The pair term is a mean of FP32
+kernel values (per-term rounding ~1e-7, independent across pairs) accumulated
+in FP64; the integral term is an exact trapezoid sum whose nodes are FP32
+deposits (~1e-6 relative), so 2e-6 bounds both.  The selected width must be
+the oracle's unless the oracle's two best values are closer than ten times
+that tolerance (then the choice is reported, not failed, and both must be
+among the oracle's near-best).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import kde_inputs as I
+from conftest import to_dev, to_dev_u
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-6
+
+
+def check_curve(cv, am, ref, tol=TOL):
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(cv - ref)) <= tol * scale, np.max(np.abs(cv - ref)) / scale
+    order = np.argsort(ref)
+    gap = ref[order[1]] - ref[order[0]]
+    if gap > 10 * tol * scale:
+        assert am == int(order[0])
+    else:
+        assert ref[am] - ref[order[0]] <= 10 * tol * scale
+
+
+@pytest.mark.parametrize("N", [2, 3, 255, 256, 257, 3000])
+def test_cv_uniform_small(ctx, oracle, N):
+    L = 2 * math.pi
+    u = I.cv_sweep_load(N, N)
+    x = I.from_fixed(u, L)
+    cand = I.log_candidates(1.0, 1e4, 16)
+    cv, am, loo = ctx.cv(to_dev_u(u), L, cand, want_loo=True)
+    if N <= 300:
+        ref = np.array([oracle.cv_dense(x, L, kappa_u=c)[0] for c in cand])
+        _, _, _, loo_ref = oracle.cv_dense(x, L, kappa_u=cand[am], want_loo=True)
+    else:
+        ref = np.array([oracle.cv_fourier(x, L, c)[0] for c in cand])
+        _, _, _, loo_ref = oracle.cv_fourier(x, L, cand[am], want_loo=True)
+    check_curve(cv, am, ref)
+    np.testing.assert_allclose(loo.cpu().numpy(), loo_ref, rtol=1e-5, atol=1e-7 * np.max(loo_ref))
+
+
+def test_cv_uniform_other_domain(ctx, oracle):
+    # x units: CV scales with 2 pi / L
+    L = 4 * math.pi
+    u, _ = I.landau_load(4, 2000, L)
+    x = I.from_fixed(u, L)
+    cand = np.array([3.0, 30.0, 300.0, 3000.0])
+    cv, am, _ = ctx.cv(to_dev_u(u), L, cand)
+    ref = np.array([oracle.cv_fourier(x, L, c)[0] for c in cand])
+    check_curve(cv, am, ref)
+
+
+def test_cv_unsorted_candidates_and_ties(ctx, oracle):
+    L = 2 * math.pi
+    u = I.cv_sweep_load(5, 1000)
+    x = I.from_fixed(u, L)
+    cand = np.array([500.0, 2.0, 50.0, 50.0, 5000.0])
+    cv, am, _ = ctx.cv(to_dev_u(u), L, cand)
+    ref = np.array([oracle.cv_fourier(x, L, c)[0] for c in cand])
+    check_curve(cv, am, ref)
+    assert cv[2] == cv[3]
+    if am in (2, 3):
+        assert am == 2  # smallest index on an exact tie
+
+
+def test_cv_scale_mode(ctx, oracle):
+    L = 4 * math.pi
+    N = 1500
+    u, _ = I.landau_load(6, N, L)
+    x = I.from_fixed(u, L)
+    kr = I.log_uniform(6, I.STREAM_KAPPA, N, 5.0, 5e3).astype(np.float32)
+    scales = 10.0 ** ((np.arange(16) - 8) / 8.0)
+    cv, am, loo = ctx.cv(to_dev_u(u), L, scales, kappa_rel=to_dev(kr), want_loo=True)
+    ref = np.array([oracle.cv_dense(x, L, kappa=s * kr.astype(np.float64))[0] for s in scales])
+    check_curve(cv, am, ref)
+    _, _, _, loo_ref = oracle.cv_dense(x, L, kappa=scales[am] * kr.astype(np.float64), want_loo=True)
+    np.testing.assert_allclose(loo.cpu().numpy(), loo_ref, rtol=1e-5, atol=1e-7 * np.max(loo_ref))
+
+
+def test_cv_duplicate_points(ctx, oracle):
+    L = 1.0
+    u = np.repeat(np.array([10, 2 ** 31, 3 * 2 ** 30], dtype=np.uint32), 100)
+    x = I.from_fixed(u, L)
+    cand = np.array([1.0, 10.0, 100.0])
+    cv, am, _ = ctx.cv(to_dev_u(u), L, cand)
+    ref = np.array([oracle.cv_fourier(x, L, c)[0] for c in cand])
+    check_curve(cv, am, ref)
+
+
+def test_cv_rejects_bad_arguments(ctx, kp):
+    u = to_dev_u(np.arange(10, dtype=np.uint32))
+    with pytest.raises(kp.KdeError):
+        ctx.cv(u[:1], 1.0, [1.0])
+    with pytest.raises(kp.KdeError):
+        ctx.cv(u, 1.0, [0.0])
+    with pytest.raises(kp.KdeError):
+        ctx.cv(u, 1.0, np.ones(300))
+
+
+def test_cv_deterministic(ctx):
+    L = 2 * math.pi
+    u = to_dev_u(I.cv_sweep_load(3, 50_000))
+    cand = I.log_candidates(1.0, 1e4, 8)
+    a, _, la = ctx.cv(u, L, cand, want_loo=True)
+    b, _, lb = ctx.cv(u, L, cand, want_loo=True)
+    assert np.array_equal(a, b) and torch.equal(la, lb)
+
+
+def test_cv_sweep_full_size(ctx, oracle):
+    # the CV-sweep workload: N = 2^18 mixture positions, 64 candidates in [1, 1e4]
+    L = 2 * math.pi
+    u = I.cv_sweep_load(0, 1 << 18)
+    x = I.from_fixed(u, L)
+    cand = I.log_candidates(1.0, 1e4, 64)
+    cv, am, loo = ctx.cv(to_dev_u(u), L, cand, want_loo=True)
+    ref = np.array([oracle.cv_fourier(x, L, c)[0] for c in cand])
+    check_curve(cv, am, ref)
+    _, _, _, loo_ref = oracle.cv_fourier(x, L, cand[am], want_loo=True)
+    idx = np.arange(0, 1 << 18, 61)
+    np.testing.assert_allclose(loo.cpu().numpy()[idx], loo_ref[idx], rtol=1e-5, atol=1e-7 * np.max(loo_ref))
+
+
+def test_adapt_widths(ctx, oracle):
+    L = 2 * math.pi
+    N = 20_000
+    u = I.cv_sweep_load(2, N)
+    x = I.from_fixed(u, L)
+    _, _, _, loo = oracle.cv_fourier(x, L, 300.0, want_loo=True)
+    loo32 = loo.astype(np.float32)
+    k = ctx.adapt_widths(to_dev(loo32), L, 300.0, 0.5, 10.0, 1e4).cpu().numpy()
+    ref = oracle.adapt_widths(loo32.astype(np.float64), L, 300.0, 0.5, 10.0, 1e4)
+    np.testing.assert_allclose(k, ref, rtol=2e-6)

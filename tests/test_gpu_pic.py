@@ -1,0 +1,156 @@
+"""GPU parity of the PIC cycle (Sec. III.A) against the oracle, plus invariants.
+
+* one step: energy, velocities and positions (matched through particle labels)
+  within FP32 rounding (1e-5 relative; positions within 1e-6 L);
+* the cold Langmuir run in FP64 with the width chosen once by CV: the same
+  width as the oracle, the energy history within 1e-7 relative, and the
+  oscillation frequency of the leap-frog/smoothing dispersion relation;
+* the Landau run with particle-wise widths updated every 50 steps: the same CV
+  widths and a damping rate within 1e-3 of the oracle's on the same ensemble;
+* momentum conservation, bitwise determinism and bitwise resume.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.special as sp
+import torch
+
+import kde_inputs as I
+from conftest import to_dev, to_dev_u
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def make_state(kp, u, v, L, Ng, dt, steps, dtype=torch.float32, kappa=None, **kw):
+    N = u.size
+    ids = torch.arange(N, dtype=torch.int32, device=DEV)
+    kap = None if kappa is None else to_dev(kappa, dtype)
+    return kp.PicState(to_dev_u(u), to_dev(v, dtype), L, Ng, dt, kappa=kap, ids=ids, max_steps=steps, **kw)
+
+
+def unsort(st, L):
+    ids = st.id.cpu().numpy().view(np.uint32).astype(np.int64)
+    order = np.argsort(ids)
+    x = I.from_fixed(st.u.cpu().numpy().view(np.uint32), L)[order]
+    v = st.v.double().cpu().numpy()[order]
+    k = None if st.kappa is None else st.kappa.double().cpu().numpy()[order]
+    return x, v, k
+
+
+@pytest.mark.parametrize("per_particle", [False, True])
+def test_one_step(ctx, kp, oracle, per_particle):
+    L, Ng, dt, N = 4 * math.pi, 64, 0.1, 4096
+    u, v = I.landau_load(2, N, L, 0.05, 1.0)
+    v32 = v.astype(np.float32)
+    kap = I.log_uniform(2, I.STREAM_KAPPA, N, 20.0, 200.0).astype(np.float32) if per_particle else None
+    st = make_state(kp, u, v32, L, Ng, dt, 2, kappa=kap, kappa_uniform=60.0)
+    ctx.pic_step(st, 2)
+    ctx.sync()
+    r = oracle.pic_run(I.from_fixed(u, L), v32, L, Ng, dt, 2,
+                       kappa=None if kap is None else kap.astype(np.float64), kappa_u=60.0)
+    np.testing.assert_allclose(st.energy.cpu().numpy()[:2], r["energy"], rtol=1e-5)
+    x, vv, _ = unsort(st, L)
+    dxp = np.abs((x - r["x"] + L / 2) % L - L / 2)
+    assert dxp.max() <= 1e-6 * L
+    assert np.linalg.norm(vv - r["v"]) <= 1e-5 * np.linalg.norm(r["v"])
+
+
+def test_langmuir_fp64_width_once(ctx, kp, oracle):
+    # cold Langmuir wave, FP64, 200 steps, width chosen once at t = 0 by CV over
+    # 16 candidates in [1, 1e3]
+    L, Ng, dt, N, steps = 4 * math.pi, 64, 0.1, 4096, 200
+    u, v = I.langmuir_load(N, L, 0.01)
+    cand = I.log_candidates(1.0, 1e3, 16)
+    st = make_state(kp, u, v, L, Ng, dt, steps, dtype=torch.float64, kappa=np.ones(N), width_every=steps,
+                    cand=cand, alpha=0.0, kappa_min=1.0, kappa_max=1e3)
+    ctx.pic_step(st, steps)
+    ctx.sync()
+    r = oracle.pic_run(I.from_fixed(u, L), v, L, Ng, dt, steps, kappa=np.ones(N), width_every=steps,
+                       cands=cand, alpha=0.0, kmin=1.0, kmax=1e3)
+    ks = st.kappa_star.cpu().numpy()
+    assert ks[0] == r["kstar"][0]
+    W = st.energy.cpu().numpy()
+    np.testing.assert_allclose(W, r["energy"], rtol=1e-7)
+    kap = ks[0]
+    t = dt * np.arange(steps)
+    A1 = sp.ive(1, kap) / sp.ive(0, kap)
+    w_th = (2 / dt) * math.asin(dt * A1 / 2)
+    p, _ = so.curve_fit(lambda t, a, w: a * np.cos(w * t) ** 2, t, W, p0=[W[0], w_th])
+    assert p[1] == pytest.approx(w_th, rel=2e-4)
+
+
+def _landau_run(ctx, kp, oracle, N, steps):
+    L, Ng, dt = 4 * math.pi, 256, 0.1
+    u, v = I.landau_load(0, N, L, 0.05, 1.0)
+    v32 = v.astype(np.float32)
+    cand = I.log_candidates(1.0, 1e4, 64)
+    st = make_state(kp, u, v32, L, Ng, dt, steps, kappa=np.ones(N), width_every=50, cand=cand, alpha=0.5,
+                    kappa_min=1.0, kappa_max=1e5)
+    ctx.pic_step(st, steps)
+    ctx.sync()
+    r = oracle.pic_run(I.from_fixed(u, L), v32, L, Ng, dt, steps, kappa=np.ones(N), width_every=50, cands=cand,
+                       alpha=0.5, kmin=1.0, kmax=1e5)
+    ks = st.kappa_star.cpu().numpy()
+    assert ks[0] == r["kstar"][0] and ks[50] == r["kstar"][50]
+    g_gpu = kp.damping_rate(st.energy.cpu().numpy(), dt)
+    g_or = oracle.damping_rate(r["energy"], dt)[0]
+    assert abs(g_gpu - g_or) <= 1e-3, (g_gpu, g_or)
+    return g_gpu
+
+
+def test_landau_damping_matches_oracle(ctx, kp, oracle):
+    _landau_run(ctx, kp, oracle, 1 << 14, 60)
+
+
+@pytest.mark.slow
+def test_landau_damping_full_size(ctx, kp, oracle):
+    g = _landau_run(ctx, kp, oracle, 1 << 20, 60)
+    assert abs(g + 0.153) < 0.02
+
+
+def test_momentum_conserved_uniform_width(ctx, kp):
+    L, Ng, dt, N = 4 * math.pi, 128, 0.1, 1 << 16
+    u, v = I.landau_load(9, N, L, 0.05, 1.0)
+    st = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 20, kappa_uniform=300.0)
+    p0 = st.v.double().sum().item()
+    ctx.pic_step(st, 20)
+    ctx.sync()
+    p1 = st.v.double().sum().item()
+    assert abs(p1 - p0) <= 1e-5 * st.v.double().abs().sum().item()
+
+
+def test_deterministic_and_resume(ctx, kp):
+    L, Ng, dt, N = 4 * math.pi, 256, 0.1, 50_000
+    u, v = I.landau_load(4, N, L, 0.05, 1.0)
+    cand = I.log_candidates(1.0, 1e4, 16)
+    kw = dict(kappa=np.ones(N), width_every=5, cand=cand, alpha=0.5, kappa_min=1.0, kappa_max=1e5)
+    a = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 12, **kw)
+    b = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 12, **kw)
+    ctx.pic_step(a, 12)
+    ctx.pic_step(b, 6)
+    # checkpoint: copy the state into fresh buffers and continue from step 6
+    c = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 12, **kw)
+    c.u.copy_(b.u)
+    c.v.copy_(b.v)
+    c.kappa.copy_(b.kappa)
+    c.id.copy_(b.id)
+    c.energy.copy_(b.energy)
+    c.c.step = b.step
+    ctx.pic_step(c, 6)
+    ctx.sync()
+    for t in ("u", "v", "kappa", "id", "energy"):
+        assert torch.equal(getattr(a, t), getattr(c, t)), t
+
+
+def test_pic_rejects_bad_state(ctx, kp):
+    u = to_dev_u(np.arange(100, dtype=np.uint32))
+    v = torch.zeros(100, device=DEV)
+    st = kp.PicState(u, v, 1.0, 5000, 0.1, kappa_uniform=10.0)
+    with pytest.raises(kp.KdeError):
+        ctx.pic_step(st, 1)
+    st = kp.PicState(u, v, 1.0, 64, 0.1, kappa_uniform=10.0, width_every=5, cand=[1.0, 10.0])
+    with pytest.raises(kp.KdeError):  # the width schedule needs a kappa array
+        ctx.pic_step(st, 1)
