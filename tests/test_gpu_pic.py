@@ -3,7 +3,7 @@
 * one step: energy, velocities and positions (matched through particle labels)
   within FP32 rounding (1e-5 relative; positions within 1e-6 L);
 * the cold Langmuir run in FP64 with the width chosen once by CV: the same
-  width as the oracle, the energy history within 1e-7 relative, and the
+  width as the oracle, the energy history within 1e-7 of its peak, and the
   oscillation frequency of the leap-frog/smoothing dispersion relation;
 * the Landau run with particle-wise widths updated every 50 steps: the same CV
   widths and a damping rate within 1e-3 of the oracle's on the same ensemble;
@@ -73,7 +73,9 @@ def test_langmuir_fp64_width_once(ctx, kp, oracle):
     ks = st.kappa_star.cpu().numpy()
     assert ks[0] == r["kstar"][0]
     W = st.energy.cpu().numpy()
-    np.testing.assert_allclose(W, r["energy"], rtol=1e-7)
+    # relative to the peak energy: W(t) passes through zero twice a period, and the
+    # GPU's 32-bit fixed-point positions differ from the oracle's doubles by < 2^-32 L
+    assert np.max(np.abs(W - r["energy"])) <= 1e-7 * np.max(r["energy"])
     kap = ks[0]
     t = dt * np.arange(steps)
     A1 = sp.ive(1, kap) / sp.ive(0, kap)
