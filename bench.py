@@ -334,18 +334,71 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_cv_sweep(args, rank, world, local_rank):
+    """The CV-sweep workload: N = 2^18 positions from 0.7 U + 0.3 vonMises(pi, 20) on
+    [0, 2 pi), 64 candidates log-spaced in [1, 1e4]; one step = one kde_cv call (pair
+    sums, integral term, argmin, leave-one-out pass).  value = CV definition pairs/s."""
+    import torch
+
+    import kde_inputs as I
+    import paper_1804_11174_gb300 as kp
+    from paper_1804_11174_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = "cuda:%d" % local_rank
+    N, L = 1 << 18, 2 * math.pi
+    cand = I.log_candidates(1.0, 1e4, 64)
+    u_np = I.cv_sweep_load(rank, N)
+    u = torch.from_numpy(u_np.view(np.int32)).to(dev)
+    ctx = kp.Context(local_rank)
+    loo = torch.empty(N, device=dev)
+    for _ in range(args.warmup):
+        ctx.cv(u, L, cand, loo=loo)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ms = []
+    ctx.profile_enable(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        t0 = time.perf_counter()
+        ctx.cv(u, L, cand, loo=loo)
+        ms.append(1e3 * (time.perf_counter() - t0))
+    cv_ms, cv_n = ctx.profile_read("cv_pairs")
+    _, launches = ctx.profile_read("all")
+    ctx.profile_enable(False)
+    t = float(np.mean(ms))
+    if rank == 0:
+        alg = cv_inradius_pairs(u_np, cand)
+        ms_p, ops_p = ctx.probe_exp2(1 << 14)
+        peak = ops_p / (ms_p * 1e-3)
+        ach = alg / (cv_ms / cv_n * 1e-3)
+        line = {"metric": METRIC, "value": world * 64 * N * (N - 1) / (t * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "cv_sweep N=2^18 mixture 0.7U+0.3vM(pi,20), 64 candidates in [1,1e4]"},
+                "gpu_launches": launches,
+                "roofline": {"bound": "alu", "kernel": "cv_pairs_kernel", "achieved": ach / 1e12, "peak": peak / 1e12,
+                             "unit": "Tex2/s", "frac": ach / peak, "traffic": None,
+                             "avg_launch_ms": cv_ms / cv_n}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "cv_sweep":
+        run_cv_sweep(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
