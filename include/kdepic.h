@@ -102,6 +102,32 @@ kde_status kde_deposit(kde_ctx *ctx, const uint32_t *u, const void *kappa, doubl
                        const void *weight, int64_t N, int32_t Ng, double L, void *rho_out,
                        uint32_t flags);
 
+/* Allocation-free deposit.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory once they run -- code
+ * recording work into CUDA graphs, hosts whose allocator policy forbids device
+ * allocations after start-up, and real-time loops that may not block on the
+ * driver's allocator.  It computes what kde_deposit computes (same arguments,
+ * same flags, same result within FP32 rounding) but takes a cudaStream_t
+ * instead of a context, never calls cudaMalloc or cudaFree, and keeps all of
+ * its scratch in one file-scope device array of KDE_NOALLOC_SCRATCH_BYTES
+ * (98,560 bytes) that every GPU which loads the library holds until the
+ * process exits.  Limits: Ng <= KDE_NOALLOC_MAX_NG (4096); larger grids return
+ * KDE_EINVAL.  Particles may come in any order; cell-sorted input runs fastest
+ * (an unsorted chunk falls back to every node of the grid).  The first call on
+ * a device (with that device current) looks up the array's device address; make
+ * that first call before any stream capture.  All calls share the one array,
+ * which keeps the previous call's contents (the accumulators are cleared at
+ * the start of each call): calls that overlap on the GPU -- on different
+ * streams or from different host threads -- race and must be serialised by the
+ * caller.  Out-of-range widths are clamped to 1e6 without a device status
+ * report (there is no context to hold one).  Returns KDE_EINVAL on bad
+ * arguments and KDE_ECUDA if the CUDA runtime refuses a launch or copy. */
+#define KDE_NOALLOC_MAX_NG 4096
+#define KDE_NOALLOC_SCRATCH_BYTES 98560
+kde_status kde_deposit_noalloc(void *stream, const uint32_t *u, const void *kappa, double kappa_uniform,
+                               const void *weight, int64_t N, int32_t Ng, double L, void *rho_out,
+                               uint32_t flags);
+
 /* Poisson solve on the periodic grid for the total charge density
  *   rho_total_g = background + charge * rho_g :
  * spectral (default): E_m = rho_m / (i k_m), k_m = 2 pi m / L, E_0 = 0 and, for

@@ -88,6 +88,7 @@ def load_library(path: str | None = None):
         "kde_probe_exp2": (S, [_P, _I64, _P, _P]),
         "kde_probe_fma": (S, [_P, _I64, _P, _P]),
         "kde_profile_enable": (S, [_P, ctypes.c_int]),
+        "kde_deposit_noalloc": (S, [_P, _P, _P, _D, _P, _I64, _I32, _D, _P, _U32]),
         "kde_profile_read": (S, [_P, ctypes.c_int, _P, _P]),
     }
     for name, (res, args) in sigs.items():
@@ -254,6 +255,24 @@ class Context:
         self._check("kde_probe_fma", self.lib.kde_probe_fma(self.h, int(iters), ctypes.addressof(ms),
                                                             ctypes.addressof(ops)))
         return ms.value, ops.value
+
+
+def deposit_noalloc(u, Ng: int, L: float, kappa=None, kappa_uniform: float = 0.0, weight=None, out=None,
+                    dtype=None, stream=None):
+    """kde_deposit_noalloc: the deposit without a context or any device allocation by the
+    library (its scratch is a fixed device array; `out` may be preallocated by the caller)."""
+    torch = _torch()
+    lib = load_library()
+    dtype = dtype or (kappa.dtype if kappa is not None else torch.float32)
+    if out is None:
+        out = torch.empty(int(Ng), dtype=dtype, device=u.device)
+    stream = stream or torch.cuda.current_stream(u.device)
+    flags = F64 if out.dtype == torch.float64 else 0
+    rc = lib.kde_deposit_noalloc(_P(stream.cuda_stream), _ptr(u), _ptr(kappa), float(kappa_uniform), _ptr(weight),
+                                 u.numel(), int(Ng), float(L), _ptr(out), flags)
+    if rc != 0:
+        raise KdeError("kde_deposit_noalloc", rc, "invalid arguments or CUDA launch failure")
+    return out
 
 
 def damping_rate(energy, dt: float) -> float:

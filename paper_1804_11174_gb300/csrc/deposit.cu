@@ -13,6 +13,8 @@
 // point (an exact power-of-two scale below the largest possible node value)
 // and added with integer atomics, so the grid sum is exact and independent of
 // the order in which chunks finish: results are bitwise reproducible.
+#include <mutex>
+
 #include "common.cuh"
 
 #define DEP_THREADS 256
@@ -74,8 +76,9 @@ __device__ __forceinline__ void node_sc(const DepSrc<T> &S, int g, T &s, T &c)
     }
 }
 
-template <typename T>
-__device__ void deposit_chunk_body(const DepSrc<T> &S, int64_t chunk, DepRec<T> *rec, T *part, int *red)
+template <typename T, bool UNSORTED = false>
+__device__ void deposit_chunk_body(const DepSrc<T> &S, int64_t chunk, DepRec<T> *rec, T *part, int *red,
+                                   int *cmm = nullptr)
 {
     const int64_t i0 = chunk * DEP_CHUNK;
     if (i0 >= S.N) return;
@@ -84,9 +87,15 @@ __device__ void deposit_chunk_body(const DepSrc<T> &S, int64_t chunk, DepRec<T> 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     int wloc = 0;
+    int cmin = 0x7fffffff, cmax = -1;
     for (int t = tid; t < n; t += DEP_THREADS) {
         int64_t j = i0 + t;
         uint32_t uu = S.u[j];
+        if (UNSORTED) {
+            int cc = kde_cell(uu, S.Ng);
+            cmin = cc < cmin ? cc : cmin;
+            cmax = cc > cmax ? cc : cmax;
+        }
         T k = S.kappa ? S.kscale * S.kappa[j] : S.kappa_u;
         if (!(k > (T)0 && k <= (T)KDE_KAPPA_MAX)) {
             kde_flag(S.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
@@ -118,7 +127,31 @@ __device__ void deposit_chunk_body(const DepSrc<T> &S, int64_t chunk, DepRec<T> 
     int W = 0;
 #pragma unroll
     for (int k = 0; k < DEP_WARPS; ++k) W = red[k] > W ? red[k] : W;
-    const int c_first = kde_cell(S.u[i0], Ng), c_last = kde_cell(S.u[i0 + n - 1], Ng);
+    int c_first, c_last;
+    if (UNSORTED) {
+        // particles in any order: the chunk's linear cell range (a range that wraps
+        // around the grid falls back to the whole grid below)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+            cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+        }
+        if (lane == 0) {
+            cmm[warp] = cmin;
+            cmm[DEP_WARPS + warp] = cmax;
+        }
+        __syncthreads();
+        c_first = cmm[0];
+        c_last = cmm[DEP_WARPS];
+#pragma unroll
+        for (int k = 1; k < DEP_WARPS; ++k) {
+            c_first = min(c_first, cmm[k]);
+            c_last = max(c_last, cmm[DEP_WARPS + k]);
+        }
+    } else {
+        c_first = kde_cell(S.u[i0], Ng);
+        c_last = kde_cell(S.u[i0 + n - 1], Ng);
+    }
     int g_lo = c_first - W;
     int R = c_last + W - g_lo + 1;
     if (R >= Ng || c_last < c_first) {
@@ -434,4 +467,130 @@ extern "C" kde_status kde_deposit(kde_ctx *ctx, const uint32_t *u, const void *k
                                    (double *)rho_out);
     return deposit_api<float>(ctx, u, (const float *)kappa, kappa_uniform, (const float *)weight, N, Ng, L,
                               (float *)rho_out);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free deposit.
+//
+// Some callers cannot call cudaMalloc once they are running: code that records
+// its work into a CUDA graph or runs under a host allocator policy that
+// forbids device allocations after start-up, plugins that must not touch the
+// host process's memory pools, and real-time loops that may not block on the
+// driver's allocator.  kde_deposit_noalloc serves them: it needs no context and
+// no workspace.  Particles may come in any order (nothing is sorted); every
+// scratch byte it uses -- the int64 grid accumulators, the node table and the
+// largest-weight word -- lives in the file-scope array below, which every GPU
+// that loads this library holds (KDE_NOALLOC_SCRATCH_BYTES) until the process
+// exits.  Every call shares that one array: calls that overlap on the GPU
+// (concurrent streams, or several host threads) race on it.
+// ---------------------------------------------------------------------------
+#define NOALLOC_ACC_OFF 0
+#define NOALLOC_NODE_OFF (KDE_MAX_NG * 8)
+#define NOALLOC_WMAX_OFF (NOALLOC_NODE_OFF + KDE_MAX_NG * 16)
+static_assert(KDE_NOALLOC_SCRATCH_BYTES >= NOALLOC_WMAX_OFF + 256, "scratch layout exceeds the declared size");
+
+static __device__ __align__(256) unsigned char kde_noalloc_scratch[KDE_NOALLOC_SCRATCH_BYTES];
+
+template <typename T>
+__global__ void __launch_bounds__(DEP_THREADS) deposit_chunk_unsorted_kernel(DepSrc<T> S)
+{
+    __shared__ DepRec<T> rec[DEP_CHUNK];
+    __shared__ T part[DEP_WARPS * 32 * DEP_WARPS];
+    __shared__ int red[DEP_WARPS];
+    __shared__ int cmm[2 * DEP_WARPS];
+    deposit_chunk_body<T, true>(S, blockIdx.x, rec, part, red, cmm);
+}
+
+template <typename T2>
+__global__ void noalloc_node_kernel(T2 *tab, int Ng)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Ng) return;
+    double s, c;
+    sincospi((double)g / (double)Ng, &s, &c);
+    tab[g].x = s;
+    tab[g].y = c;
+}
+
+// device address of the scratch array, looked up once per device with that
+// device current (the host-side symbol is only a stand-in)
+static std::mutex g_noalloc_mu;
+static std::map<int, unsigned char *> g_noalloc_addr;
+
+static unsigned char *noalloc_scratch_address(int device)
+{
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(device);
+    if (it != g_noalloc_addr.end()) return it->second;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, kde_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    g_noalloc_addr[device] = (unsigned char *)p;
+    return (unsigned char *)p;
+}
+
+template <typename T>
+static kde_status deposit_noalloc_impl(cudaStream_t stream, unsigned char *scr, const uint32_t *u, const T *kappa,
+                                       double kappa_u, const T *weight, int64_t N, int Ng, double L, T *rho_out)
+{
+    long long *acc = (long long *)(scr + NOALLOC_ACC_OFF);
+    typename V2<T>::t *nodes = (typename V2<T>::t *)(scr + NOALLOC_NODE_OFF);
+    unsigned int *wmax = (unsigned int *)(scr + NOALLOC_WMAX_OFF);
+    if (cudaMemsetAsync(acc, 0, (size_t)Ng * sizeof(long long), stream) != cudaSuccess) return KDE_ECUDA;
+    if (N == 0) return cudaMemsetAsync(rho_out, 0, (size_t)Ng * sizeof(T), stream) == cudaSuccess ? KDE_OK : KDE_ECUDA;
+    noalloc_node_kernel<typename V2<T>::t><<<(Ng + 255) / 256, 256, 0, stream>>>(nodes, Ng);
+    const double coef = KDE_TWO_PI / L;
+    const double norm_u = kappa ? 0.0 : kde_norm(kappa_u);
+    const double norm_bound = kappa ? kde_norm(KDE_KAPPA_MAX) : norm_u;
+    const double w_u = L / (double)N;
+    const double bound = (double)N * w_u * coef * norm_bound;
+    if (weight) {
+        if (cudaMemsetAsync(wmax, 0, 4, stream) != cudaSuccess) return KDE_ECUDA;
+        int blocks = (int)((N + 255) / 256);
+        blocks = blocks > 1024 ? 1024 : blocks;
+        wmax_kernel<T><<<blocks, 256, 0, stream>>>(weight, N, wmax, nullptr);
+    }
+    DepSrc<T> S{};
+    S.u = u;
+    S.N = N;
+    S.kappa = kappa;
+    S.kappa_u = (T)kappa_u;
+    S.kscale = (T)1;
+    S.norm_u = (T)norm_u;
+    S.w = weight;
+    S.w_u = (T)w_u;
+    S.coef = (T)coef;
+    S.Ng = Ng;
+    S.nodes = nodes;
+    S.acc = acc;
+    S.bound = bound;
+    S.wmax_bits = weight ? wmax : nullptr;
+    S.norm_bound = norm_bound;
+    S.status = nullptr;
+    deposit_chunk_unsorted_kernel<T><<<(unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK), DEP_THREADS, 0, stream>>>(S);
+    acc_to_real_kernel<T><<<(Ng + 255) / 256, 256, 0, stream>>>(acc, Ng, bound, weight ? wmax : nullptr,
+                                                                (double)N * coef * norm_bound, rho_out);
+    return cudaGetLastError() == cudaSuccess ? KDE_OK : KDE_ECUDA;
+}
+
+extern "C" kde_status kde_deposit_noalloc(void *stream, const uint32_t *u, const void *kappa, double kappa_uniform,
+                                          const void *weight, int64_t N, int32_t Ng, double L, void *rho_out,
+                                          uint32_t flags)
+{
+    if (N < 0 || N > 0xFFFFFFFFll || Ng < 1 || Ng > KDE_NOALLOC_MAX_NG || !(L > 0) || !rho_out || (N > 0 && !u))
+        return KDE_EINVAL;
+    if (!kappa && !(kappa_uniform > 0 && kappa_uniform <= KDE_KAPPA_MAX)) return KDE_EINVAL;
+    if (flags & ~KDE_F64) return KDE_ENOTSUP;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return KDE_ECUDA;
+    unsigned char *scr = noalloc_scratch_address(device);
+    if (!scr) return KDE_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (flags & KDE_F64)
+        return deposit_noalloc_impl<double>(s, scr, u, (const double *)kappa, kappa_uniform, (const double *)weight, N,
+                                            Ng, L, (double *)rho_out);
+    return deposit_noalloc_impl<float>(s, scr, u, (const float *)kappa, kappa_uniform, (const float *)weight, N, Ng, L,
+                                       (float *)rho_out);
 }
