@@ -112,9 +112,11 @@ def cv_inradius_pairs(u_np, cands):
             total += N * (N - 1) // 2
             continue
         r = 2.0 * math.asin(math.sqrt(s2))
+        # pairs j after i (circularly) within r: with r < pi each unordered pair is
+        # counted exactly once, from the particle it follows
         hi = np.searchsorted(ext, th + r, side="right")
         cnt = np.minimum(hi - np.arange(N) - 1, N - 1)
-        total += int(cnt.sum()) // 2 if r < math.pi else N * (N - 1) // 2
+        total += int(cnt.sum())
     return total
 
 

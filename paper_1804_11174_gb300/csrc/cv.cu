@@ -362,6 +362,188 @@ __global__ void __launch_bounds__(CV_T) cv_pairs_kernel(CvPairArgs A, CvCands cc
     }
 }
 
+// ---------------------------------------------------------------------------
+// Uniform widths, at most 64 candidates: persistent pair kernel.
+//
+// Work items are (row tile, split) pairs handed out by an atomic counter; each
+// item's FP64 sums go to the item's own slot, so the result does not depend on
+// which CTA ran which item.  Per column particle the kernel forms s^2 once and
+// then runs every active candidate with its exponent factor -2 kappa_c log2 e
+// read as a constant-bank operand.  The number of active candidates of a tile
+// pair, rounded up to a multiple of 4, selects one of 16 instantiations of the
+// column loop, so no per-column branching remains.  After each tile pair the
+// 64 per-thread FP32 sums are reduced across the warp by a transposing
+// butterfly (62 shuffles leave lane l with candidates l and l + 32), and added
+// to per-warp FP64 accumulators.
+// ---------------------------------------------------------------------------
+#define CVF_MAXC 64
+
+struct CvFast {
+    int n;             // active candidates (sorted ascending by width)
+    int nitems;        // work items = row tiles x splits
+    int splits;
+    float kk[CVF_MAXC];  // -2 log2(e) kappa_c
+    float k[CVF_MAXC];   // kappa_c
+};
+
+template <int NG>
+__device__ __forceinline__ void cvf_columns(const float2 *__restrict__ t, int ncol, float2 me, int self,
+                                            float (&acc)[CVF_MAXC], const CvFast &cf)
+{
+    if (self < 0) {
+#pragma unroll 2
+        for (int i = 0; i < ncol; ++i) {
+            const float2 o = t[i];
+            const float s = me.x * o.y - me.y * o.x;
+            const float s2 = s * s;
+#pragma unroll
+            for (int q = 0; q < 4 * NG; ++q) acc[q] += kde_ex2(s2 * cf.kk[q]);
+        }
+    } else {
+        for (int i = 0; i < ncol; ++i) {
+            if (i == self) continue;
+            const float2 o = t[i];
+            const float s = me.x * o.y - me.y * o.x;
+            const float s2 = s * s;
+#pragma unroll
+            for (int q = 0; q < 4 * NG; ++q) acc[q] += kde_ex2(s2 * cf.kk[q]);
+        }
+    }
+}
+
+__device__ __forceinline__ void cvf_dispatch(int ng, const float2 *t, int ncol, float2 me, int self,
+                                             float (&acc)[CVF_MAXC], const CvFast &cf)
+{
+    switch (ng) {
+#define CVF_CASE(G) \
+    case G: cvf_columns<G>(t, ncol, me, self, acc, cf); break;
+        CVF_CASE(1) CVF_CASE(2) CVF_CASE(3) CVF_CASE(4) CVF_CASE(5) CVF_CASE(6) CVF_CASE(7) CVF_CASE(8)
+        CVF_CASE(9) CVF_CASE(10) CVF_CASE(11) CVF_CASE(12) CVF_CASE(13) CVF_CASE(14) CVF_CASE(15) CVF_CASE(16)
+#undef CVF_CASE
+    default: break;
+    }
+}
+
+// butterfly over 32 values: afterwards lane l holds the warp sum of v[l]
+__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            float send = up ? v[i] : v[i + o];
+            float keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+__global__ void __launch_bounds__(CV_T, 2)
+    cv_pairs_fast_kernel(const float2 *__restrict__ sc, int64_t N, int NT, const uint2 *__restrict__ tile_u,
+                         int *counter, double *part, unsigned int *status, const __grid_constant__ CvFast cf)
+{
+    __shared__ __align__(128) float2 buf[2][CV_T];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double wacc[CV_WARPS][CVF_MAXC];
+    __shared__ int s_item, s_stop;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    unsigned phase[2] = {0u, 0u};
+    bool failed = false;
+    const float Kthr = cf.k[0];
+    for (;;) {
+        __syncthreads();  // the previous item's readers of s_item and wacc are done
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        for (int c = tid; c < CV_WARPS * CVF_MAXC; c += CV_T) (&wacc[0][0])[c] = 0.0;
+        __syncthreads();
+        const int item = s_item;
+        if (item >= cf.nitems) break;
+        const int a = item / cf.splits, sidx = item % cf.splits;
+        const int64_t j = (int64_t)a * CV_T + tid;
+        const bool rvalid = j < N;
+        const float2 me = sc[j];
+        const uint2 ta = tile_u[a];
+        float acc[CVF_MAXC];
+#pragma unroll
+        for (int q = 0; q < CVF_MAXC; ++q) acc[q] = 0.f;
+
+        Walk w{0, 0, 0};
+        int cnt = 0;
+        auto fetch = [&](int &b, int &d) -> bool {
+            while (walk_next(w, a, NT, tile_u, ta, Kthr, b, d)) {
+                if (!canonical_pair(a, b, NT)) continue;
+                if ((cnt++) % cf.splits == sidx) return true;
+            }
+            return false;
+        };
+        int b_cur = 0, d_cur = 0;
+        bool have = fetch(b_cur, d_cur);
+        int cur = 0;
+        if (have && tid == 0) tma_load_1d(buf[cur], sc + (size_t)b_cur * CV_T, CV_T * sizeof(float2), &bar[cur]);
+        while (have) {
+            int b_nxt = 0, d_nxt = 0;
+            const bool next = fetch(b_nxt, d_nxt);
+            if (next && tid == 0)
+                tma_load_1d(buf[cur ^ 1], sc + (size_t)b_nxt * CV_T, CV_T * sizeof(float2), &bar[cur ^ 1]);
+            const bool ok = mbar_wait(&bar[cur], phase[cur]);
+            phase[cur] ^= 1u;
+            if (tid == 0) s_stop = ok ? 0 : 1;
+            __syncthreads();
+            if (s_stop) {
+                if (next && !mbar_wait(&bar[cur ^ 1], phase[cur ^ 1]) && tid == 0)
+                    kde_flag(status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
+                failed = true;
+                break;
+            }
+            // active candidates of this tile pair (widths sorted ascending)
+            const float kr = reach_kappa(tile_gap(ta, tile_u[b_cur]));
+            int nact = 0;
+            while (nact < cf.n && cf.k[nact] <= kr) ++nact;
+            if (nact > 0) {
+                const int64_t col0 = (int64_t)b_cur * CV_T;
+                const int ncol = (int)(N - col0 < CV_T ? N - col0 : CV_T);
+                const bool diag = d_cur == 0;
+                cvf_dispatch((nact + 3) >> 2, buf[cur], ncol, me, diag ? tid : -1, acc, cf);
+                const float wgt = diag ? 1.0f : 2.0f;
+                const float m = rvalid ? wgt : 0.0f;
+                float lo[32], hi[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    lo[q] = acc[q] * m;
+                    hi[q] = acc[q + 32] * m;
+                    acc[q] = 0.f;
+                    acc[q + 32] = 0.f;
+                }
+                const float r0 = warp_transpose_sum32(lo, lane);
+                const float r1 = warp_transpose_sum32(hi, lane);
+                wacc[warp][lane] += (double)r0;
+                wacc[warp][lane + 32] += (double)r1;
+            }
+            __syncthreads();  // buffer `cur` is free again
+            cur ^= 1;
+            b_cur = b_nxt;
+            d_cur = d_nxt;
+            have = next;
+        }
+        if (failed) {
+            if (tid == 0) kde_flag(status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
+            break;
+        }
+        __syncthreads();
+        for (int c = tid; c < cf.n; c += CV_T) {
+            double sum = 0.0;
+            for (int ww = 0; ww < CV_WARPS; ++ww) sum += wacc[ww][c];
+            part[(size_t)item * cf.n + c] = sum;
+        }
+    }
+}
+
 // per-candidate sum of CTA partials in CTA order
 __global__ void cv_reduce_kernel(const double *part, int nblocks, int n, double *tot)
 {
@@ -478,6 +660,133 @@ __global__ void __launch_bounds__(CV_T) cv_loo_kernel(CvLooArgs A)
 }
 
 // ---------------------------------------------------------------------------
+// Leave-one-out sums at the selected width, uniform widths: one row tile per
+// CTA, column tiles of both directions staged by TMA (double-buffered), two
+// columns per step in packed f32x2 arithmetic.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk2(float a, float b)
+{
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f2x r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f2x mul2(f2x a, f2x b)
+{
+    f2x d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b)
+{
+    f2x d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c)
+{
+    f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__global__ void __launch_bounds__(CV_T) cv_loo_fast_kernel(const float2 *__restrict__ sc, int64_t N, int NT,
+                                                           const uint2 *__restrict__ tile_u,
+                                                           const uint32_t *__restrict__ perm, const int *argmin,
+                                                           CvCands cc, double xs, float *loo, unsigned int *status)
+{
+    __shared__ __align__(128) float2 buf[2][CV_T];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_stop;
+    const int tid = threadIdx.x;
+    const int a = blockIdx.x;
+    const int best = *argmin;
+    int cs = 0;
+    for (int c = 0; c < cc.n; ++c)
+        if (cc.orig[c] == best) cs = c;
+    const float kc = cc.k[cs];
+    const float kk = (float)(-2.0 * KDE_LOG2E) * kc;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)a * CV_T + tid;
+    const bool rvalid = i < N;
+    const float2 me = sc[i];
+    const uint2 ta = tile_u[a];
+    const f2x mx = pk2(me.x, me.x), my = pk2(-me.y, -me.y), k2 = pk2(kk, kk);
+    double sum = 0.0;
+    Walk w{0, 0, 0};
+    int b_cur = 0, d_cur = 0;
+    bool have = walk_next(w, a, NT, tile_u, ta, kc, b_cur, d_cur);
+    unsigned phase[2] = {0u, 0u};
+    int cur = 0;
+    if (have && tid == 0) tma_load_1d(buf[cur], sc + (size_t)b_cur * CV_T, CV_T * sizeof(float2), &bar[cur]);
+    bool failed = false;
+    while (have) {
+        int b_nxt = 0, d_nxt = 0;
+        const bool next = walk_next(w, a, NT, tile_u, ta, kc, b_nxt, d_nxt);
+        if (next && tid == 0)
+            tma_load_1d(buf[cur ^ 1], sc + (size_t)b_nxt * CV_T, CV_T * sizeof(float2), &bar[cur ^ 1]);
+        const bool ok = mbar_wait(&bar[cur], phase[cur]);
+        phase[cur] ^= 1u;
+        if (tid == 0) s_stop = ok ? 0 : 1;
+        __syncthreads();
+        if (s_stop) {
+            if (next && !mbar_wait(&bar[cur ^ 1], phase[cur ^ 1]) && tid == 0)
+                kde_flag(status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
+            failed = true;
+            break;
+        }
+        const int64_t col0 = (int64_t)b_cur * CV_T;
+        const int ncol = (int)(N - col0 < CV_T ? N - col0 : CV_T);
+        const float2 *t = buf[cur];
+        float tile_sum;
+        if (d_cur == 0 || ncol < CV_T) {
+            float acc = 0.f;
+            for (int q = 0; q < ncol; ++q) {
+                if (d_cur == 0 && q == tid) continue;
+                const float2 o = t[q];
+                const float s = me.x * o.y - me.y * o.x;
+                acc += kde_ex2(s * s * kk);
+            }
+            tile_sum = acc;
+        } else {
+            const float4 *t4 = (const float4 *)t;
+            f2x acc = pk2(0.f, 0.f);
+#pragma unroll 4
+            for (int q = 0; q < CV_T / 2; ++q) {
+                const float4 o = t4[q];  // columns 2q and 2q+1: (sin, cos, sin, cos)
+                const f2x sv = fma2(mx, pk2(o.y, o.w), mul2(my, pk2(o.x, o.z)));
+                const f2x x = mul2(mul2(sv, sv), k2);
+                float x0, x1;
+                upk2(x, x0, x1);
+                acc = add2(acc, pk2(kde_ex2(x0), kde_ex2(x1)));
+            }
+            float a0, a1;
+            upk2(acc, a0, a1);
+            tile_sum = a0 + a1;
+        }
+        sum += (double)tile_sum;
+        __syncthreads();
+        cur ^= 1;
+        b_cur = b_nxt;
+        d_cur = d_nxt;
+        have = next;
+    }
+    if (failed) {
+        if (tid == 0) kde_flag(status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
+        return;
+    }
+    if (!rvalid) return;
+    const double v = xs * kde_norm((double)kc) * sum / (double)(N - 1);
+    loo[perm ? perm[i] : i] = (float)v;
+}
+
+// ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64_t N, double L,
@@ -544,13 +853,38 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
     A.lnorm = lnorm;
     A.part = part;
     A.status = ctx->d_status;
-    {
-        KdeProfScope _ps(ctx, PROF_CV_PAIRS);
-        if (scale_mode) cv_pairs_kernel<true><<<nblocks, CV_T, 0, ctx->stream>>>(A, cc);
-        else cv_pairs_kernel<false><<<nblocks, CV_T, 0, ctx->stream>>>(A, cc);
+    int nparts = nblocks;
+    if (!scale_mode && n_cand <= CVF_MAXC) {
+        // persistent fast path: enough work items for an even finish
+        CvFast cf{};
+        cf.n = n_cand;
+        int ctas = 2 * ctx->sm_count;
+        cf.splits = 1;
+        while ((int64_t)NT * cf.splits < 8LL * ctas && cf.splits < NT) ++cf.splits;
+        cf.nitems = NT * cf.splits;
+        for (int c = 0; c < n_cand; ++c) {
+            cf.k[c] = cc.k[c];
+            cf.kk[c] = (float)(-2.0 * KDE_LOG2E) * cc.k[c];
+        }
+        part = (double *)kde_ws(ctx, WS_CV_PART, (size_t)cf.nitems * n_cand * 8 + 64);
+        if (!part) return KDE_ENOMEM;
+        int *counter = (int *)(part + (size_t)cf.nitems * n_cand);
+        KDE_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), ctx->stream), "cv counter memset");
+        {
+            KdeProfScope _ps(ctx, PROF_CV_PAIRS);
+            cv_pairs_fast_kernel<<<ctas, CV_T, 0, ctx->stream>>>(sc, N, NT, tile_u, counter, part, ctx->d_status, cf);
+        }
+        KDE_LAUNCHED(ctx, "cv_pairs_fast_kernel");
+        nparts = cf.nitems;
+    } else {
+        {
+            KdeProfScope _ps(ctx, PROF_CV_PAIRS);
+            if (scale_mode) cv_pairs_kernel<true><<<nblocks, CV_T, 0, ctx->stream>>>(A, cc);
+            else cv_pairs_kernel<false><<<nblocks, CV_T, 0, ctx->stream>>>(A, cc);
+        }
+        KDE_LAUNCHED(ctx, "cv_pairs_kernel");
     }
-    KDE_LAUNCHED(ctx, "cv_pairs_kernel");
-    cv_reduce_kernel<<<n_cand, 256, 0, ctx->stream>>>(part, nblocks, n_cand, tot);
+    cv_reduce_kernel<<<n_cand, 256, 0, ctx->stream>>>(part, nparts, n_cand, tot);
     KDE_LAUNCHED(ctx, "cv_reduce_kernel");
 
     // integral term on fine grids
@@ -577,7 +911,9 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
         {
             KdeProfScope _ps(ctx, PROF_CV_LOO);
             if (scale_mode) cv_loo_kernel<true><<<NT, CV_T, 0, ctx->stream>>>(B);
-            else cv_loo_kernel<false><<<NT, CV_T, 0, ctx->stream>>>(B);
+            else
+                cv_loo_fast_kernel<<<NT, CV_T, 0, ctx->stream>>>(sc, N, NT, tile_u, perm, argmin_dev, cc,
+                                                                 KDE_TWO_PI / L, loo, ctx->d_status);
         }
         KDE_LAUNCHED(ctx, "cv_loo_kernel");
     }
