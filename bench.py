@@ -201,7 +201,8 @@ def run_ours(args, rank, world, local_rank):
     total_steps = P * (args.warmup + args.steps) + P
     st = kp.PicState(u0_t.clone(), v0_t.clone(), L, Ng, dt, kappa=torch.ones(N, device=dev),
                      ids=torch.arange(N, dtype=torch.int32, device=dev), width_every=P, cand=cand,
-                     alpha=w["alpha"], kappa_min=w["kappa_min"], kappa_max=w["kappa_max"], max_steps=total_steps)
+                     alpha=w["alpha"], kappa_min=w["kappa_min"], kappa_max=w["kappa_max"], max_steps=total_steps,
+                     cv_spectral=args.cv == "spectral")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
 
     for _ in range(args.warmup):
@@ -232,7 +233,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     cv_ms, cv_n = ctx.profile_read("cv_pairs")
-    prof = {k: ctx.profile_read(k) for k in ("deposit", "gather", "sort", "poisson", "cv_grid", "cv_loo")}
+    prof = {k: ctx.profile_read(k) for k in ("deposit", "gather", "sort", "poisson", "cv_grid", "cv_loo",
+                                              "spectral")}
     _, launches = ctx.profile_read("all")
     ctx.profile_enable(False)
     clk = clocks.stop()
@@ -262,7 +264,8 @@ def run_ours(args, rank, world, local_rank):
         e2e_steps = max(1, min(args.steps, 3))
         st2 = kp.PicState(torch.empty(N, dtype=torch.int32, device=dev), torch.empty(N, device=dev), L, Ng, dt,
                           kappa=torch.empty(N, device=dev), width_every=P, cand=cand, alpha=w["alpha"],
-                          kappa_min=w["kappa_min"], kappa_max=w["kappa_max"], max_steps=P)
+                          kappa_min=w["kappa_min"], kappa_max=w["kappa_max"], max_steps=P,
+                          cv_spectral=args.cv == "spectral")
         torch.cuda.synchronize()
         e_ms = []
         for _ in range(e2e_steps):
@@ -290,6 +293,13 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
+    if args.cv == "spectral":
+        line = spectral_line(args, ctx, world, t_step, value, prof, launches, clk, e2e, wall, w, st)
+        print(json.dumps(line), flush=True)
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
     # ---- roofline of the dominant kernel (CV pair sums, bound by the exp2 unit) ----
     alg = [cv_inradius_pairs(u, cand) for u in cv_alg]
     alg_per_launch = float(np.mean(alg))
@@ -386,6 +396,27 @@ def run_cv_sweep(args, rank, world, local_rank):
     ctx.close()
 
 
+def spectral_line(args, ctx, world, t_step, value, prof, launches, clk, e2e, wall, w, st):
+    """Bench line for the Landau period with the width schedule in the exact Fourier form.
+    The dominant kernel is then the gather (+push); its roofline is taken against HBM:
+    algorithmic bytes per launch = 24 B read (u, v, kappa, norm... sorted copies) + 16 B written."""
+    N, Ng, P = w["N"], w["Ng"], w["period"]
+    g_ms, g_n = prof["gather"]
+    bytes_per_launch = N * (4 + 4 + 4 + 4 + 4) + N * (4 + 4 + 4 + 4)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") or 6768.8
+    ach = bytes_per_launch / (g_ms / g_n * 1e-3) / 1e9
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(w) + " [CV by the exact Fourier form]", "N": N, "Ng": Ng,
+                       "pic_steps_per_step": P, "l2": "flushed before every timed step (256 MB write)"},
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}, "wall_s": wall,
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "kernel": "gather_kernel", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "traffic": None, "avg_launch_ms": g_ms / g_n}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,6 +424,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep"])
+    ap.add_argument("--cv", default="pairs", choices=["pairs", "spectral"],
+                    help="CV evaluation in the width schedule: O(N^2) pair sums or the exact Fourier form")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

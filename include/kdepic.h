@@ -59,6 +59,7 @@ typedef int kde_status;
 #define KDE_F64 0x1u         /* real arrays are float64 and arithmetic is FP64 */
 #define KDE_POISSON_FD 0x2u  /* finite-difference Poisson (Sec. III.A) instead of spectral */
 #define KDE_CV_SCALE 0x4u    /* kde_cv: candidates scale per-particle widths kappa_rel */
+#define KDE_CV_SPECTRAL 0x8u /* kde_cv / pic_step: exact Fourier form of the CV (uniform widths) */
 
 /* Maximum grid size accepted by deposit / gather / Poisson / pic_step. */
 #define KDE_MAX_NG 4096
@@ -160,7 +161,15 @@ kde_status kde_gather(kde_ctx *ctx, const uint32_t *u, const void *kappa, double
  * accumulation; the integral term is an exact trapezoid sum on a grid fine
  * enough for the narrowest candidate; the final combination is FP64.  Pairs
  * whose kernel value is below 2^-24 of the peak may be skipped.  Synchronises.
- * Flags: KDE_CV_SCALE. */
+ * KDE_CV_SPECTRAL (uniform widths only) evaluates the same objective by the
+ * identity K(t) = (1/2pi) sum_m A_m e^{imt}, A_m = I_m/I_0: with the structure
+ * factor S_m = sum_j e^{i m theta_j} (exact integer phases, FP64 combination),
+ * the pair sum is (1/2pi)(n^2 + 2 sum A_m |S_m|^2) - n K(0) and the integral
+ * term (1/(2pi n^2))(n^2 + 2 sum A_m^2 |S_m|^2), modes cut where A_m < 1e-17;
+ * cost O(N sqrt(kappa_max)) instead of O(N^2) per candidate.  The
+ * leave-one-out densities come from the same series (FP64 sums); their relative
+ * accuracy degrades only for particles whose own kernel dominates their pilot
+ * density.  Flags: KDE_CV_SCALE, KDE_CV_SPECTRAL. */
 kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64_t N, double L,
                   const double *cand, int32_t n_cand, double *cv_out, int32_t *argmin_out,
                   float *loo_out, uint32_t flags);
@@ -198,7 +207,7 @@ typedef struct pic_state {
     double *energy;       /* device float64[steps] field energy per step (indexed by step), or NULL */
     double *kappa_star;   /* device float64[steps] CV width in force per step, or NULL */
     int64_t step;         /* step counter (in/out); step 0 gets a half velocity kick */
-    uint32_t flags;       /* KDE_F64, KDE_POISSON_FD; PIC_NO_BACKSTEP */
+    uint32_t flags;       /* KDE_F64, KDE_POISSON_FD, KDE_CV_SPECTRAL (width schedule); PIC_NO_BACKSTEP */
 } pic_state;
 
 #define PIC_NO_BACKSTEP 0x100u /* do not halve the first kick at step 0 */
@@ -229,7 +238,8 @@ kde_status kde_probe_fma(kde_ctx *ctx, int64_t iters, double *ms_out, int64_t *o
  * switches recording on or off.  kde_profile_read(ctx, kernel, &ms, &n)
  * synchronises and returns the summed device time and launch count of one
  * kernel: 0 CV pair sums, 1 deposit, 2 gather(+push), 3 sort scatter,
- * 4 Poisson, 5 CV integral-term deposit, 6 CV leave-one-out; kernel = -1
+ * 4 Poisson, 5 CV integral-term deposit, 6 CV leave-one-out, 7 spectral
+ * structure factor; kernel = -1
  * returns the number of all kernel launches in *n. */
 kde_status kde_profile_enable(kde_ctx *ctx, int on);
 kde_status kde_profile_read(kde_ctx *ctx, int kernel, double *total_ms, int64_t *launches);

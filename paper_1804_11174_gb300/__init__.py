@@ -20,13 +20,14 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Context", "PicState", "KdeError", "load_library", "LIB_PATH", "F64", "POISSON_FD", "CV_SCALE",
+__all__ = ["Context", "PicState", "KdeError", "load_library", "LIB_PATH", "F64", "POISSON_FD", "CV_SCALE", "CV_SPECTRAL",
            "PIC_NO_BACKSTEP", "MAX_NG"]
 
 LIB_PATH = _build.LIB
 F64 = 0x1
 POISSON_FD = 0x2
 CV_SCALE = 0x4
+CV_SPECTRAL = 0x8
 PIC_NO_BACKSTEP = 0x100
 MAX_NG = 4096
 
@@ -194,15 +195,16 @@ class Context:
                                                       _ptr(field), field.numel(), float(L), _ptr(out), flags))
         return out
 
-    def cv(self, u, L: float, cand, kappa_rel=None, loo=None, want_loo: bool = False):
-        """kde_cv: CV(kappa_c) (x units) for every candidate; returns (cv, argmin, loo)."""
+    def cv(self, u, L: float, cand, kappa_rel=None, loo=None, want_loo: bool = False, spectral: bool = False):
+        """kde_cv: CV(kappa_c) (x units) for every candidate; returns (cv, argmin, loo).
+        spectral=True selects the exact Fourier form (uniform widths)."""
         torch = _torch()
         cand = np.ascontiguousarray(cand, dtype=np.float64)
         cv = np.empty(cand.size, dtype=np.float64)
         am = ctypes.c_int32()
         if want_loo and loo is None:
             loo = self._new(u.numel(), torch.float32)
-        flags = CV_SCALE if kappa_rel is not None else 0
+        flags = (CV_SCALE if kappa_rel is not None else 0) | (CV_SPECTRAL if spectral else 0)
         self._check("kde_cv", self.lib.kde_cv(self.h, _ptr(u), _ptr(kappa_rel), u.numel(), float(L),
                                               cand.ctypes.data, cand.size, cv.ctypes.data, ctypes.addressof(am),
                                               _ptr(loo), flags))
@@ -226,7 +228,8 @@ class Context:
         state._sync_in()
         self._check("pic_step", self.lib.pic_step(self.h, ctypes.byref(state.c), int(n_steps)))
 
-    PROF = {"cv_pairs": 0, "deposit": 1, "gather": 2, "sort": 3, "poisson": 4, "cv_grid": 5, "cv_loo": 6}
+    PROF = {"cv_pairs": 0, "deposit": 1, "gather": 2, "sort": 3, "poisson": 4, "cv_grid": 5, "cv_loo": 6,
+            "spectral": 7}
 
     def profile_enable(self, on: bool = True):
         """kde_profile_enable: start (or stop) recording per-kernel device times."""
@@ -292,7 +295,7 @@ class PicState:
     def __init__(self, u, v, L: float, Ng: int, dt: float, kappa=None, kappa_uniform: float = 0.0, ids=None,
                  qm: float = -1.0, charge: float = -1.0, background: float = 1.0, width_every: int = 0,
                  cand=None, alpha: float = 0.5, kappa_min: float = 0.0, kappa_max: float = 1e6,
-                 max_steps: int = 0, fd: bool = False, backstep: bool = True):
+                 max_steps: int = 0, fd: bool = False, backstep: bool = True, cv_spectral: bool = False):
         torch = _torch()
         self.u, self.v, self.kappa, self.id = u, v, kappa, ids
         f64 = v.dtype == torch.float64
@@ -311,7 +314,8 @@ class PicState:
         c.n_cand = 0 if self.cand is None else self.cand.size
         c.alpha, c.kappa_min, c.kappa_max = float(alpha), float(kappa_min), float(kappa_max)
         c.step = 0
-        c.flags = (F64 if f64 else 0) | (POISSON_FD if fd else 0) | (0 if backstep else PIC_NO_BACKSTEP)
+        c.flags = ((F64 if f64 else 0) | (POISSON_FD if fd else 0) | (0 if backstep else PIC_NO_BACKSTEP)
+                   | (CV_SPECTRAL if cv_spectral else 0))
         self.c = c
 
     def _sync_in(self):

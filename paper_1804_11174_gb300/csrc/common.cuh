@@ -70,12 +70,15 @@ enum WsSlot {
     WS_PIC_E,
     WS_PIC_LOO,
     WS_PIC_KS,
+    WS_SP_PART,
+    WS_SP_S,
+    WS_SP_A,
     WS_NSLOTS
 };
 
 // kernels timed by the profiling hook (kde_profile_enable / kde_profile_read)
 enum KdeProfId { PROF_CV_PAIRS = 0, PROF_DEPOSIT, PROF_GATHER, PROF_SORT, PROF_POISSON, PROF_CV_GRID, PROF_CV_LOO,
-                 PROF_NIDS };
+                 PROF_SPECTRAL, PROF_NIDS };
 
 struct kde_ctx {
     int device = 0;
@@ -305,6 +308,10 @@ struct CandList {
 kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64_t N, double L,
                          const double *cand_host, int n_cand, bool scale_mode, double *cv_dev, int *argmin_dev,
                          float *loo, double *kstar_dev);
+
+// the same results by the exact Fourier form (uniform widths only)
+kde_status kde_cv_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *cand_host,
+                                  int n_cand, double *cv_dev, int *argmin_dev, float *loo, double *kstar_dev);
 
 // Silverman widths from leave-one-out densities; kstar from the device when
 // kstar_dev is not null.  Writes widths (and norms when norm_out is not null)

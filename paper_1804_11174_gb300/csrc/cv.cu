@@ -926,7 +926,11 @@ extern "C" kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa
 {
     if (!ctx) return KDE_EINVAL;
     const bool scale = (flags & KDE_CV_SCALE) != 0;
-    if (flags & ~KDE_CV_SCALE) return kde_fail(ctx, KDE_ENOTSUP, "kde_cv: unsupported flags 0x%x", flags);
+    const bool spectral = (flags & KDE_CV_SPECTRAL) != 0;
+    if (flags & ~(KDE_CV_SCALE | KDE_CV_SPECTRAL))
+        return kde_fail(ctx, KDE_ENOTSUP, "kde_cv: unsupported flags 0x%x", flags);
+    if (scale && spectral)
+        return kde_fail(ctx, KDE_ENOTSUP, "kde_cv: the spectral form is for uniform candidate widths");
     if (N < 2 || N > 0xFFFFFFFFll || !(L > 0) || !u || !cand || !cv_out || n_cand < 1 || n_cand > CV_MAXC)
         return kde_fail(ctx, KDE_EINVAL, "kde_cv: need 2 <= N < 2^32, L > 0, 1 <= n_cand <= %d, non-null arrays",
                         CV_MAXC);
@@ -938,8 +942,10 @@ extern "C" kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa
     double *cvd = (double *)kde_ws(ctx, WS_CV_OUT, (size_t)n_cand * 8 + 64);
     if (!cvd) return KDE_ENOMEM;
     int *amin = (int *)(cvd + n_cand);
-    KDE_TRY(kde_cv_device(ctx, u, scale ? kappa_rel : nullptr, N, L, cand, n_cand, scale, cvd, amin, loo_out,
-                          nullptr));
+    if (spectral) KDE_TRY(kde_cv_spectral_device(ctx, u, N, L, cand, n_cand, cvd, amin, loo_out, nullptr));
+    else
+        KDE_TRY(kde_cv_device(ctx, u, scale ? kappa_rel : nullptr, N, L, cand, n_cand, scale, cvd, amin, loo_out,
+                              nullptr));
     KDE_CUDA(ctx, cudaMemcpyAsync(cv_out, cvd, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, ctx->stream), "cv copy");
     int am = 0;
     KDE_CUDA(ctx, cudaMemcpyAsync(&am, amin, 4, cudaMemcpyDeviceToHost, ctx->stream), "argmin copy");

@@ -66,8 +66,11 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
         const int64_t step = st->step;
         const bool update = sched && step % st->width_every == 0;
         if (update) {
-            KDE_TRY(kde_cv_device(ctx, st->u, nullptr, N, L, st->cand, st->n_cand, false, cv_dev, amin_dev, loo,
-                                  ks_dev));
+            if (st->flags & KDE_CV_SPECTRAL)
+                KDE_TRY(kde_cv_spectral_device(ctx, st->u, N, L, st->cand, st->n_cand, cv_dev, amin_dev, loo, ks_dev));
+            else
+                KDE_TRY(kde_cv_device(ctx, st->u, nullptr, N, L, st->cand, st->n_cand, false, cv_dev, amin_dev, loo,
+                                      ks_dev));
             KDE_TRY(kde_adapt_device(ctx, loo, N, L, ks_dev, 0.0, st->alpha, st->kappa_min, st->kappa_max, st->kappa,
                                      norm_arr, sizeof(T) == 8));
             if (!fetch_ws()) return KDE_ENOMEM;
@@ -121,7 +124,7 @@ extern "C" kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps)
         !st->u || !st->v || st->step < 0)
         return kde_fail(ctx, KDE_EINVAL, "pic_step: need 1 <= N < 2^32, 1 <= Ng <= %d, L > 0, dt > 0, u and v",
                         KDE_MAX_NG);
-    if (st->flags & ~(KDE_F64 | KDE_POISSON_FD | PIC_NO_BACKSTEP))
+    if (st->flags & ~(KDE_F64 | KDE_POISSON_FD | KDE_CV_SPECTRAL | PIC_NO_BACKSTEP))
         return kde_fail(ctx, KDE_ENOTSUP, "pic_step: unsupported flags 0x%x", st->flags);
     if (st->kappa && !st->kappa_norm)
         return kde_fail(ctx, KDE_EINVAL, "pic_step: per-particle widths need the kappa_norm array");

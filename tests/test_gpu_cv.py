@@ -141,3 +141,44 @@ def test_adapt_widths(ctx, oracle):
     k = ctx.adapt_widths(to_dev(loo32), L, 300.0, 0.5, 10.0, 1e4).cpu().numpy()
     ref = oracle.adapt_widths(loo32.astype(np.float64), L, 300.0, 0.5, 10.0, 1e4)
     np.testing.assert_allclose(k, ref, rtol=2e-6)
+
+
+# ---------------------------------------------------------------------------
+# exact Fourier form of the CV (uniform widths)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [2000, 3001])
+def test_cv_spectral_against_dense(ctx, oracle, N):
+    L = 4 * math.pi
+    u, _ = I.landau_load(N, N, L, 0.05, 1.0)
+    x = I.from_fixed(u, L)
+    cand = I.log_candidates(1.0, 1e4, 16)
+    cv, am, loo = ctx.cv(to_dev_u(u), L, cand, want_loo=True, spectral=True)
+    ref = np.array([oracle.cv_dense(x, L, kappa_u=c)[0] for c in cand])
+    # an exact identity combined in FP64; the phases are FP32 sincospi of exact
+    # 32-bit turn fractions (~1e-7 per term), so 1e-8 of max |CV| bounds the error
+    check_curve(cv, am, ref, tol=1e-8)
+    _, _, _, loo_ref = oracle.cv_dense(x, L, kappa_u=cand[am], want_loo=True)
+    np.testing.assert_allclose(loo.cpu().numpy(), loo_ref, rtol=1e-5, atol=1e-7 * np.max(loo_ref))
+
+
+def test_cv_spectral_matches_pairs_and_sweep_size(ctx, oracle):
+    L = 2 * math.pi
+    u = I.cv_sweep_load(0, 1 << 18)
+    x = I.from_fixed(u, L)
+    cand = I.log_candidates(1.0, 1e4, 64)
+    ud = to_dev_u(u)
+    cs, ams, ls = ctx.cv(ud, L, cand, want_loo=True, spectral=True)
+    cp, amp, lp = ctx.cv(ud, L, cand, want_loo=True)
+    sel = np.arange(0, 64, 7)
+    ref = np.array([oracle.cv_fourier(x, L, cand[c])[0] for c in sel])
+    assert np.max(np.abs(cs[sel] - ref)) <= 1e-8 * np.max(np.abs(ref))
+    assert np.max(np.abs(cs - cp)) <= TOL * np.max(np.abs(cs))
+    assert ams == amp or abs(cs[amp] - cs[ams]) <= 10 * TOL * np.max(np.abs(cs))
+    idx = np.arange(0, 1 << 18, 97)
+    np.testing.assert_allclose(ls.cpu().numpy()[idx], lp.cpu().numpy()[idx], rtol=2e-5)
+
+
+def test_cv_spectral_rejects_scale_mode(ctx, kp):
+    u = to_dev_u(np.arange(100, dtype=np.uint32) * 40000)
+    with pytest.raises(kp.KdeError):
+        ctx.cv(u, 1.0, [1.0, 2.0], kappa_rel=to_dev(np.ones(100)), spectral=True)

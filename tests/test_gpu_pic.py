@@ -156,3 +156,18 @@ def test_pic_rejects_bad_state(ctx, kp):
     st = kp.PicState(u, v, 1.0, 64, 0.1, kappa_uniform=10.0, width_every=5, cand=[1.0, 10.0])
     with pytest.raises(kp.KdeError):  # the width schedule needs a kappa array
         ctx.pic_step(st, 1)
+
+
+def test_width_schedule_spectral_matches_pairs(ctx, kp):
+    # the width schedule by the exact Fourier form selects the same widths
+    L, Ng, dt, N = 4 * math.pi, 256, 0.1, 1 << 15
+    u, v = I.landau_load(12, N, L, 0.05, 1.0)
+    cand = I.log_candidates(1.0, 1e4, 64)
+    kw = dict(kappa=np.ones(N), width_every=10, cand=cand, alpha=0.5, kappa_min=1.0, kappa_max=1e5)
+    a = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 21, **kw)
+    b = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 21, cv_spectral=True, **kw)
+    ctx.pic_step(a, 21)
+    ctx.pic_step(b, 21)
+    ctx.sync()
+    np.testing.assert_array_equal(a.kappa_star.cpu().numpy(), b.kappa_star.cpu().numpy())
+    np.testing.assert_allclose(a.energy.cpu().numpy(), b.energy.cpu().numpy(), rtol=1e-3)
