@@ -316,6 +316,32 @@ def run_ours(args, rank, world, local_rank):
             "unit_def": "one exp2 per (unordered pair inside the candidate's truncation radius, candidate)",
             "avg_launch_ms": cv_launch_ms, "launches": cv_n}
 
+    # the same period with the width schedule in the exact Fourier form (same run, same state size)
+    variant = None
+    try:
+        st3 = kp.PicState(u0_t.clone(), v0_t.clone(), L, Ng, dt, kappa=torch.ones(N, device=dev),
+                          ids=torch.arange(N, dtype=torch.int32, device=dev), width_every=P, cand=cand,
+                          alpha=w["alpha"], kappa_min=w["kappa_min"], kappa_max=w["kappa_max"],
+                          max_steps=P * (args.warmup + args.steps), cv_spectral=True)
+        for _ in range(args.warmup):
+            ctx.pic_step(st3, P)
+        torch.cuda.synchronize()
+        v_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.pic_step(st3, P)
+            b.record()
+            b.synchronize()
+            v_ms.append(a.elapsed_time(b))
+        vt = float(np.mean(v_ms))
+        variant = {"cv": "exact Fourier form (kde_cv KDE_CV_SPECTRAL)", "ms_per_step": vt,
+                   "value": world * pairs_dg / (vt * 1e-3), "unit": UNIT}
+    except Exception as e:  # report, do not fail the main line
+        variant = {"error": str(e)}
+
     try:
         cpu_v, cpu_dt, cores, sample = oracle_sample(5, 1 << 12)
         cpu = {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
@@ -339,6 +365,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "variant_cv_spectral": variant,
     }
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -172,6 +172,38 @@ __device__ __forceinline__ float kde_ex2(float x)
 }
 __device__ __forceinline__ double kde_ex2(double x) { return exp2(x); }
 
+// packed FP32 pairs (f32x2: one instruction applies the operation to both lanes)
+typedef unsigned long long kde_f2;
+__device__ __forceinline__ kde_f2 kde_pk(float a, float b)
+{
+    kde_f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void kde_upk(kde_f2 r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ kde_f2 kde_mul2(kde_f2 a, kde_f2 b)
+{
+    kde_f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ kde_f2 kde_fma2(kde_f2 a, kde_f2 b, kde_f2 c)
+{
+    kde_f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// 2^(-x) for both lanes of a packed pair
+__device__ __forceinline__ kde_f2 kde_ex2neg2(kde_f2 x)
+{
+    float a, b;
+    kde_upk(x, a, b);
+    return kde_pk(kde_ex2(-a), kde_ex2(-b));
+}
+
 __device__ __forceinline__ void kde_flag(unsigned int *status, unsigned code, unsigned detail)
 {
     if (status && atomicCAS(status, 0u, code) == 0u) status[1] = detail;

@@ -215,6 +215,144 @@ __device__ void deposit_chunk_body(const DepSrc<T> &S, int64_t chunk, DepRec<T> 
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 chunk body with packed pair arithmetic: each lane owns two nodes (a warp
+// pass covers 64 consecutive nodes) and every particle record is staged
+// pre-duplicated -- (beta sin, beta sin, beta cos, beta cos) and (w n, w n) --
+// so one 128-bit and one 64-bit broadcast load feed the f32x2 multiply-adds of
+// both nodes.  Same node range, slicing and fixed-order combination as the
+// scalar body.
+// ---------------------------------------------------------------------------
+#define DEP2_PART 512
+
+__device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, float4 *rsc, float2 *rwn, float *part,
+                                      int *red)
+{
+    const int64_t i0 = chunk * DEP_CHUNK;
+    if (i0 >= S.N) return;
+    const int n = (int)(S.N - i0 < DEP_CHUNK ? S.N - i0 : DEP_CHUNK);
+    const int Ng = S.Ng;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int wloc = 0;
+    for (int t = tid; t < n; t += DEP_THREADS) {
+        const int64_t j = i0 + t;
+        const uint32_t uu = S.u[j];
+        float k = S.kappa ? S.kscale * S.kappa[j] : S.kappa_u;
+        if (!(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
+            kde_flag(S.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
+            k = (float)KDE_KAPPA_MAX;
+        }
+        float nm;
+        if (S.lnorm) nm = exp2f(S.lnorm[j]);
+        else if (S.norm) nm = S.norm[j];
+        else if (S.kappa) nm = (float)kde_norm((double)k);
+        else nm = S.norm_u;
+        const float wj = S.w ? S.w[j] : S.w_u;
+        float sh, ch;
+        kde_half_sincos(uu, sh, ch);
+        const float beta = sqrtf((float)(2.0 * KDE_LOG2E) * k);
+        rsc[t] = make_float4(beta * sh, beta * sh, beta * ch, beta * ch);
+        const float wn = wj * S.coef * nm;
+        rwn[t] = make_float2(wn, wn);
+        const int wn_ = window_nodes_f(k, Ng, (float)KDE_XCUT);
+        wloc = wn_ > wloc ? wn_ : wloc;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wloc = max(wloc, __shfl_xor_sync(0xffffffffu, wloc, o));
+    if (lane == 0) red[warp] = wloc;
+    __syncthreads();
+    int W = 0;
+#pragma unroll
+    for (int k = 0; k < DEP_WARPS; ++k) W = red[k] > W ? red[k] : W;
+    const int c_first = kde_cell(S.u[i0], Ng), c_last = kde_cell(S.u[i0 + n - 1], Ng);
+    int g_lo = c_first - W;
+    int R = c_last + W - g_lo + 1;
+    if (R >= Ng || c_last < c_first) {
+        g_lo = 0;
+        R = Ng;
+    }
+    const int ngroups = (R + 63) >> 6;
+    double bound = S.bound;
+    if (S.wmax_bits) bound = (double)S.N * (double)S.coef * S.norm_bound * (double)__uint_as_float(*S.wmax_bits);
+    const double scale = kde_acc_scale(bound);
+
+    auto node_pair = [&](int gi, int &ga, int &gb, kde_f2 &SS, kde_f2 &nCC, bool &va, bool &vb) {
+        const int ra = gi * 64 + lane, rb = ra + 32;
+        va = ra < R;
+        vb = rb < R;
+        ga = g_lo + ra;
+        ga = ga < 0 ? ga + Ng : (ga >= Ng ? ga - Ng : ga);
+        gb = g_lo + rb;
+        gb = gb < 0 ? gb + Ng : (gb >= Ng ? gb - Ng : gb);
+        float sa, ca, sb, cb;
+        node_sc(S, va ? ga : 0, sa, ca);
+        node_sc(S, vb ? gb : 0, sb, cb);
+        SS = kde_pk(sa, sb);
+        nCC = kde_pk(-ca, -cb);
+    };
+    auto sweep = [&](int p0, int p1, kde_f2 SS, kde_f2 nCC) -> kde_f2 {
+        kde_f2 acc = kde_pk(0.f, 0.f);
+#pragma unroll 4
+        for (int p = p0; p < p1; ++p) {
+            const float4 q = rsc[p];
+            const float2 w2 = rwn[p];
+            // s = S_g (beta cos_j) - C_g (beta sin_j) for both nodes
+            const kde_f2 sv = kde_fma2(SS, kde_pk(q.z, q.w), kde_mul2(nCC, kde_pk(q.x, q.y)));
+            acc = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), kde_pk(w2.x, w2.y), acc);
+        }
+        return acc;
+    };
+
+    if (ngroups >= DEP_WARPS) {
+        for (int gi = warp; gi < ngroups; gi += DEP_WARPS) {
+            int ga, gb;
+            bool va, vb;
+            kde_f2 SS, nCC;
+            node_pair(gi, ga, gb, SS, nCC, va, vb);
+            float aa, ab;
+            kde_upk(sweep(0, n, SS, nCC), aa, ab);
+            long long v;
+            if (va && (v = __double2ll_rn((double)aa * scale)) != 0)
+                atomicAdd((unsigned long long *)&S.acc[ga], (unsigned long long)v);
+            if (vb && (v = __double2ll_rn((double)ab * scale)) != 0)
+                atomicAdd((unsigned long long *)&S.acc[gb], (unsigned long long)v);
+        }
+        return;
+    }
+    const int slices = DEP_WARPS / ngroups;
+    const int gi = warp % ngroups, sl = warp / ngroups;
+    if (sl < slices) {
+        const int p0 = (int)((int64_t)n * sl / slices), p1 = (int)((int64_t)n * (sl + 1) / slices);
+        int ga, gb;
+        bool va, vb;
+        kde_f2 SS, nCC;
+        node_pair(gi, ga, gb, SS, nCC, va, vb);
+        float aa, ab;
+        kde_upk(sweep(p0, p1, SS, nCC), aa, ab);
+        part[sl * DEP2_PART + gi * 64 + lane] = aa;
+        part[sl * DEP2_PART + gi * 64 + 32 + lane] = ab;
+    }
+    __syncthreads();
+    for (int r = tid; r < ngroups * 64; r += DEP_THREADS) {
+        if (r >= R) continue;
+        float a = 0.f;
+        for (int k = 0; k < slices; ++k) a += part[k * DEP2_PART + r];
+        int g = g_lo + r;
+        g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
+        const long long v = __double2ll_rn((double)a * scale);
+        if (v) atomicAdd((unsigned long long *)&S.acc[g], (unsigned long long)v);
+    }
+}
+
+__global__ void __launch_bounds__(DEP_THREADS) deposit_chunk_x2_kernel(DepSrc<float> S)
+{
+    __shared__ float4 rsc[DEP_CHUNK];
+    __shared__ float2 rwn[DEP_CHUNK];
+    __shared__ float part[DEP_WARPS * DEP2_PART];
+    __shared__ int red[DEP_WARPS];
+    deposit_chunk_body_x2(S, blockIdx.x, rsc, rwn, part, red);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(DEP_THREADS) deposit_chunk_kernel(DepSrc<T> S)
 {
@@ -284,7 +422,8 @@ kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T
     unsigned grid = (unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK);
     {
         KdeProfScope _ps(ctx, PROF_DEPOSIT);
-    deposit_chunk_kernel<T><<<grid, DEP_THREADS, 0, ctx->stream>>>(S);
+        if constexpr (sizeof(T) == 4) deposit_chunk_x2_kernel<<<grid, DEP_THREADS, 0, ctx->stream>>>(S);
+        else deposit_chunk_kernel<T><<<grid, DEP_THREADS, 0, ctx->stream>>>(S);
     }
     KDE_LAUNCHED(ctx, "deposit_chunk_kernel");
     return KDE_OK;
@@ -329,8 +468,9 @@ __global__ void __launch_bounds__(DEP_THREADS)
     cv_grid_deposit_kernel(const uint32_t *u, int64_t N, const float *kappa_rel, const float *lnorm,
                            const unsigned int *krmax_bits, CandList cl, long long *acc, unsigned int *status)
 {
-    __shared__ DepRec<float> rec[DEP_CHUNK];
-    __shared__ float part[DEP_WARPS * 32 * DEP_WARPS];
+    __shared__ float4 rsc[DEP_CHUNK];
+    __shared__ float2 rwn[DEP_CHUNK];
+    __shared__ float part[DEP_WARPS * DEP2_PART];
     __shared__ int red[DEP_WARPS];
     const int c = blockIdx.y;
     DepSrc<float> S{};
@@ -362,7 +502,7 @@ __global__ void __launch_bounds__(DEP_THREADS)
         S.bound = kde_norm(kmax);
     }
     S.Ng = cv_grid_points(kmax);
-    deposit_chunk_body<float>(S, blockIdx.x, rec, part, red);
+    deposit_chunk_body_x2(S, blockIdx.x, rsc, rwn, part, red);
 }
 
 // FP64 trapezoid sum of fhat^2 on each candidate's grid: f2[c] = (2 pi / M) sum_g fhat_g^2

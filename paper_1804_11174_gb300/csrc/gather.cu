@@ -170,6 +170,151 @@ __global__ void __launch_bounds__(GAT_THREADS) gather_kernel(GatherArgs<T> A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 gather with packed pair arithmetic: each lane carries two particles (a
+// warp covers 64 consecutive sorted particles), and every node record is kept
+// pre-duplicated in shared memory -- (sin, sin, -cos, -cos) and (E, E) -- so
+// one 128-bit and one 64-bit broadcast load feed two particles' f32x2
+// multiply-adds.  The node loop runs as two contiguous segments (before and
+// after the wrap point), so it carries no per-node index arithmetic.
+// ---------------------------------------------------------------------------
+#define GAT2_WARPS 8
+
+__global__ void __launch_bounds__(GAT2_WARPS * 32) gather2_kernel(GatherArgs<float> A)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ng = A.Ng;
+    float4 *SC = (float4 *)sm;           // (S, S, -C, -C)
+    float2 *FF = (float2 *)(SC + Ng);    // (E, E)
+    for (int g = threadIdx.x; g < Ng; g += GAT2_WARPS * 32) {
+        float2 sc = A.nodes[g];
+        SC[g] = make_float4(sc.x, sc.x, -sc.y, -sc.y);
+        float f = A.field[g];
+        FF[g] = make_float2(f, f);
+    }
+    if (blockIdx.x == 0 && A.energy) {
+        __shared__ double red[GAT2_WARPS * 32];
+        double sum = 0.0;
+        for (int g = threadIdx.x; g < Ng; g += GAT2_WARPS * 32) sum += (double)A.field[g] * (double)A.field[g];
+        red[threadIdx.x] = sum;
+        __syncthreads();
+        for (int o = GAT2_WARPS * 16; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            A.energy[0] = 0.5 * red[0] * A.dx;
+            if (A.kstar_out) A.kstar_out[0] = A.kstar_in ? A.kstar_in[0] : (double)A.kappa_u;
+        }
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x * GAT2_WARPS + warp) * 64;
+    int64_t jj[2] = {base + lane, base + 32 + lane};
+    float bs[2], bc[2], nm[2], kap[2];
+    uint32_t uu[2];
+    bool valid[2];
+    int lo = 0x3fffffff, hi = -0x3fffffff;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t j = jj[h];
+        valid[h] = j < A.N;
+        uu[h] = valid[h] ? A.u[j] : 0u;
+        float k = A.kappa ? (valid[h] ? A.kappa[j] : 1.0f) : A.kappa_u;
+        if (valid[h] && !(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
+            kde_flag(A.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
+            k = (float)KDE_KAPPA_MAX;
+        }
+        kap[h] = k;
+        nm[h] = A.norm ? (valid[h] ? A.norm[j] : 0.f) : (A.kappa ? (float)kde_norm((double)k) : A.norm_u);
+        float sh, ch;
+        kde_half_sincos(uu[h], sh, ch);
+        const float beta = sqrtf((float)(2.0 * KDE_LOG2E) * k);
+        bs[h] = beta * sh;
+        bc[h] = beta * ch;
+        if (valid[h]) {
+            const int cell = kde_cell(uu[h], Ng);
+            const int W = window_nodes_g(k, Ng, (float)KDE_XCUT);
+            lo = min(lo, cell - W);
+            hi = max(hi, cell + W);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    int len = hi - lo + 1;
+    if (len >= Ng) {
+        lo = 0;
+        len = Ng;
+    }
+    if (len <= 0) return;  // whole warp past the end
+    int g0 = lo % Ng;
+    if (g0 < 0) g0 += Ng;
+    const kde_f2 bsv = kde_pk(bs[0], bs[1]), bcv = kde_pk(bc[0], bc[1]);
+    kde_f2 acc = kde_pk(0.f, 0.f);
+    const int e1 = g0 + len < Ng ? g0 + len : Ng;  // first segment [g0, e1), then [0, len - (e1 - g0))
+    const int e2 = len - (e1 - g0);
+#pragma unroll 2
+    for (int g = g0; g < e1; ++g) {
+        const float4 q = SC[g];
+        const float2 f = FF[g];
+        const kde_f2 sv = kde_fma2(kde_pk(q.x, q.y), bcv, kde_mul2(kde_pk(q.z, q.w), bsv));
+        acc = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), kde_pk(f.x, f.y), acc);
+    }
+#pragma unroll 2
+    for (int g = 0; g < e2; ++g) {
+        const float4 q = SC[g];
+        const float2 f = FF[g];
+        const kde_f2 sv = kde_fma2(kde_pk(q.x, q.y), bcv, kde_mul2(kde_pk(q.z, q.w), bsv));
+        acc = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), kde_pk(f.x, f.y), acc);
+    }
+    float ea[2];
+    kde_upk(acc, ea[0], ea[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!valid[h]) continue;
+        const int64_t j = jj[h];
+        const float Ei = ea[h] * nm[h] * A.coef;
+        if (A.u_out) {
+            const float v = A.v_in[j] + A.kick_qm_dt * Ei;
+            A.v_out[j] = v;
+            A.u_out[j] = advance_position(uu[h], v * A.dt_scale);
+            if (A.kappa_out) A.kappa_out[j] = kap[h];
+            if (A.norm_out) A.norm_out[j] = A.norm_in[j];
+            if (A.id_out) A.id_out[j] = A.id_in[j];
+        } else {
+            A.out[A.perm ? A.perm[j] : j] = Ei;
+        }
+    }
+}
+
+static kde_status launch_gather2(kde_ctx *ctx, GatherArgs<float> &A)
+{
+    const void *nodes = kde_node_table(ctx, A.Ng, false);
+    if (!nodes) return KDE_ENOMEM;
+    A.nodes = (const float2 *)nodes;
+    A.status = ctx->d_status;
+    const size_t smem = (size_t)A.Ng * (sizeof(float4) + sizeof(float2));
+    static bool attr = false;
+    if (!attr) {
+        KDE_CUDA(ctx, cudaFuncSetAttribute(gather2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           KDE_MAX_NG * (int)(sizeof(float4) + sizeof(float2))),
+                 "gather2 attribute");
+        attr = true;
+    }
+    unsigned grid = (unsigned)((A.N + GAT2_WARPS * 64 - 1) / (GAT2_WARPS * 64));
+    if (grid == 0) grid = 1;
+    {
+        KdeProfScope _ps(ctx, PROF_GATHER);
+        gather2_kernel<<<grid, GAT2_WARPS * 32, smem, ctx->stream>>>(A);
+    }
+    KDE_LAUNCHED(ctx, "gather2_kernel");
+    return KDE_OK;
+}
+
 template <typename T>
 static kde_status launch_gather(kde_ctx *ctx, GatherArgs<T> &A)
 {
@@ -227,7 +372,8 @@ kde_status kde_gather_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T 
         A.kstar_out = push->kstar_out;
         A.dx = push->dx;
     }
-    return launch_gather<T>(ctx, A);
+    if constexpr (sizeof(T) == 4) return launch_gather2(ctx, A);
+    else return launch_gather<T>(ctx, A);
 }
 
 template kde_status kde_gather_sorted<float>(kde_ctx *, const uint32_t *, const float *, float, const float *, float,

@@ -1,78 +1,96 @@
 // sort.cu -- stable counting sort of particles by bin (cell) index.
 //
-// Three passes, each warp owning a contiguous unit of SORT_UNIT particles:
-//   count   : warp-private shared histogram of its unit -> counts[unit][bin]
-//   scan    : per bin, exclusive prefix over units; then exclusive prefix of
-//             the bin totals -> bin starts
-//   scatter : the warp re-reads its unit in order, ranks equal keys within
-//             each 32-particle step with __match_any_sync, and writes every
-//             particle (position + payloads) to
-//             start[bin] + prefix[unit][bin] + running count + rank.
-// The order inside a bin is the input order (stable), so the result is
-// deterministic.
+// Each warp owns a contiguous unit of `unit` particles (a multiple of 32).
+//   count   : warp-private shared histogram of its unit -> counts[bin][unit]
+//             (bin-major, so that the destination order of the segments is the
+//             flat index bin * nunits + unit)
+//   scan    : exclusive scan of the flat counts array: tiles of 4096 scanned
+//             in place plus a one-block scan of the tile totals
+//   scatter : the warp loads its unit up front, then ranks equal keys in each
+//             32-particle step with __match_any_sync and writes every particle
+//             (position and payloads) to its segment start + running count +
+//             rank.
+// The order inside a bin is the input order (stable), so results are
+// deterministic.  Units are small enough to keep thousands of warps in flight.
 #include "common.cuh"
 
-#define SORT_UNIT 4096
-#define SORT_WARPS 4
+#define SORT_MAX_COUNTS (1 << 22)
+#define SCAN_TILE 4096
+#define SCAN_THREADS 256
 
 __device__ __forceinline__ int bin_of(uint32_t u, int nbins) { return (int)(((uint64_t)u * (uint64_t)nbins) >> 32); }
 
-__global__ void __launch_bounds__(SORT_WARPS * 32) sort_count_kernel(const uint32_t *u, int64_t N, int nbins,
-                                                                      int nunits, unsigned int *counts)
+__global__ void sort_count_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int unit, int nunits,
+                                  unsigned int *counts)
 {
     extern __shared__ unsigned int hist[];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int unit = blockIdx.x * SORT_WARPS + warp;
+    const int wpb = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int un = blockIdx.x * wpb + warp;
     unsigned int *h = hist + (size_t)warp * nbins;
     for (int b = lane; b < nbins; b += 32) h[b] = 0;
     __syncwarp();
-    if (unit < nunits) {
-        int64_t i0 = (int64_t)unit * SORT_UNIT, i1 = i0 + SORT_UNIT < N ? i0 + SORT_UNIT : N;
-        for (int64_t i = i0 + lane; i < i1; i += 32) atomicAdd(&h[bin_of(u[i], nbins)], 1u);
-        __syncwarp();
-        for (int b = lane; b < nbins; b += 32) counts[(size_t)unit * nbins + b] = h[b];
-    }
+    if (un >= nunits) return;
+    const int64_t i0 = (int64_t)un * unit, i1 = i0 + unit < N ? i0 + unit : N;
+    for (int64_t i = i0 + lane; i < i1; i += 32) atomicAdd(&h[bin_of(u[i], nbins)], 1u);
+    __syncwarp();
+    for (int b = lane; b < nbins; b += 32) counts[(size_t)b * nunits + un] = h[b];
 }
 
-// counts[unit][bin] -> exclusive prefix over units (in place); totals[bin]
-__global__ void sort_colscan_kernel(unsigned int *counts, int nbins, int nunits, unsigned int *totals)
+// exclusive scan of each SCAN_TILE-element tile in place; tile totals out
+__global__ void __launch_bounds__(SCAN_THREADS) sort_scan_tiles_kernel(unsigned int *a, int64_t n, unsigned int *tot)
 {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbins) return;
-    unsigned int run = 0;
-    for (int t = 0; t < nunits; ++t) {
-        unsigned int c = counts[(size_t)t * nbins + b];
-        counts[(size_t)t * nbins + b] = run;
-        run += c;
-    }
-    totals[b] = run;
-}
-
-// exclusive scan of totals[nbins] in one block (in place)
-__global__ void sort_binscan_kernel(unsigned int *totals, int nbins)
-{
-    __shared__ unsigned int part[1024];
-    int t = threadIdx.x, per = (nbins + blockDim.x - 1) / blockDim.x;
-    int b0 = t * per, b1 = b0 + per < nbins ? b0 + per : nbins;
+    __shared__ unsigned int wsum[SCAN_THREADS / 32];
+    const int per = SCAN_TILE / SCAN_THREADS;  // 16 consecutive elements per thread
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * per;
+    unsigned int v[SCAN_TILE / SCAN_THREADS];
     unsigned int s = 0;
-    for (int b = b0; b < b1; ++b) s += totals[b];
-    part[t] = s;
-    __syncthreads();
-    if (t == 0) {
-        unsigned int run = 0;
-        for (int k = 0; k < (int)blockDim.x; ++k) {
-            unsigned int c = part[k];
-            part[k] = run;
-            run += c;
-        }
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        v[k] = base + k < n ? a[base + k] : 0u;
+        s += v[k];
     }
-    __syncthreads();
-    unsigned int run = part[t];
-    for (int b = b0; b < b1; ++b) {
-        unsigned int c = totals[b];
-        totals[b] = run;
-        run += c;
+    // exclusive scan of the per-thread sums across the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
     }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    unsigned int woff = 0, total = 0;
+    for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+        if (w < warp) woff += wsum[w];
+        total += wsum[w];
+    }
+    unsigned int run = woff + inc - s;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        if (base + k < n) a[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = total;
+}
+
+// exclusive scan of the tile totals (at most 1024) in one block
+__global__ void sort_scan_totals_kernel(unsigned int *tot, int ntiles)
+{
+    __shared__ unsigned int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    unsigned int v = t < ntiles ? tot[t] : 0u;
+    unsigned int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned int x = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += x;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    unsigned int woff = 0;
+    for (int w = 0; w < warp; ++w) woff += wsum[w];
+    if (t < ntiles) tot[t] = woff + inc - v;
 }
 
 struct ScatterPl {
@@ -82,39 +100,51 @@ struct ScatterPl {
     int n;
 };
 
-__global__ void __launch_bounds__(SORT_WARPS * 32)
-    sort_scatter_kernel(const uint32_t *u, int64_t N, int nbins, int nunits, const unsigned int *prefix,
-                        const unsigned int *starts, uint32_t *u_out, ScatterPl pl, uint32_t *perm_out)
+#define SORT_MAXR 8  // 32-particle steps loaded ahead per chunk of the unit
+
+__global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int unit, int nunits,
+                                    const unsigned int *__restrict__ seg, const unsigned int *__restrict__ tiles,
+                                    uint32_t *u_out, ScatterPl pl, uint32_t *perm_out)
 {
     extern __shared__ unsigned int hist[];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int unit = blockIdx.x * SORT_WARPS + warp;
+    const int wpb = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int un = blockIdx.x * wpb + warp;
     unsigned int *h = hist + (size_t)warp * nbins;
-    if (unit >= nunits) return;
+    if (un >= nunits) return;
     for (int b = lane; b < nbins; b += 32) h[b] = 0;
     __syncwarp();
-    const unsigned int *pre = prefix + (size_t)unit * nbins;
-    unsigned int lt = (1u << lane) - 1u;
-    int64_t i0 = (int64_t)unit * SORT_UNIT, i1 = i0 + SORT_UNIT < N ? i0 + SORT_UNIT : N;
-    for (int64_t base = i0; base < i1; base += 32) {
-        int64_t i = base + lane;
-        bool valid = i < i1;
-        uint32_t uu = valid ? u[i] : 0u;
-        int key = valid ? bin_of(uu, nbins) : -1;
-        unsigned int peers = __match_any_sync(0xffffffffu, key);
-        unsigned int rank = __popc(peers & lt);
-        unsigned int before = valid ? h[key] : 0u;
-        __syncwarp();
-        if (valid && rank == 0) h[key] = before + __popc(peers);
-        __syncwarp();
-        if (valid) {
-            size_t dst = (size_t)starts[key] + pre[key] + before + rank;
-            u_out[dst] = uu;
-            for (int k = 0; k < pl.n; ++k) {
-                if (pl.elem[k] == 8) ((uint64_t *)pl.dst[k])[dst] = ((const uint64_t *)pl.src[k])[i];
-                else ((uint32_t *)pl.dst[k])[dst] = ((const uint32_t *)pl.src[k])[i];
+    const unsigned int lt = (1u << lane) - 1u;
+    const int64_t i0 = (int64_t)un * unit, i1 = i0 + unit < N ? i0 + unit : N;
+    for (int64_t c0 = i0; c0 < i1; c0 += 32 * SORT_MAXR) {
+        uint32_t uu[SORT_MAXR];
+#pragma unroll
+        for (int r = 0; r < SORT_MAXR; ++r) {
+            const int64_t i = c0 + r * 32 + lane;
+            uu[r] = i < i1 ? u[i] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < SORT_MAXR; ++r) {
+            const int64_t i = c0 + r * 32 + lane;
+            if (c0 + r * 32 >= i1) break;
+            const bool valid = i < i1;
+            const int key = valid ? bin_of(uu[r], nbins) : -1;
+            const unsigned int peers = __match_any_sync(0xffffffffu, key);
+            const unsigned int rank = __popc(peers & lt);
+            const unsigned int before = valid ? h[key] : 0u;
+            __syncwarp();
+            if (valid && rank == 0) h[key] = before + __popc(peers);
+            __syncwarp();
+            if (valid) {
+                const size_t flat = (size_t)key * nunits + un;
+                const size_t dst = (size_t)seg[flat] + tiles[flat / SCAN_TILE] + before + rank;
+                u_out[dst] = uu[r];
+                for (int k = 0; k < pl.n; ++k) {
+                    if (pl.elem[k] == 8) ((uint64_t *)pl.dst[k])[dst] = ((const uint64_t *)pl.src[k])[i];
+                    else ((uint32_t *)pl.dst[k])[dst] = ((const uint32_t *)pl.src[k])[i];
+                }
+                if (perm_out) perm_out[dst] = (uint32_t)i;
             }
-            if (perm_out) perm_out[dst] = (uint32_t)i;
         }
     }
 }
@@ -125,24 +155,34 @@ kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins
     if (N <= 0) return KDE_OK;
     if (nbins < 1 || nbins > 8192 || npl > 4 || N > 0xFFFFFFFFll)
         return kde_fail(ctx, KDE_EINVAL, "sort: unsupported sizes");
-    int nunits = (int)((N + SORT_UNIT - 1) / SORT_UNIT);
-    unsigned int *counts = (unsigned int *)kde_ws(ctx, WS_SORT_COUNTS, (size_t)nunits * nbins * 4);
-    unsigned int *starts = (unsigned int *)kde_ws(ctx, WS_SORT_STARTS, (size_t)nbins * 4);
-    if (!counts || !starts) return KDE_ENOMEM;
-    size_t smem = (size_t)SORT_WARPS * nbins * 4;
+    int unit = 256;
+    while ((int64_t)nbins * ((N + unit - 1) / unit) > SORT_MAX_COUNTS) unit *= 2;
+    const int nunits = (int)((N + unit - 1) / unit);
+    const int64_t ncounts = (int64_t)nbins * nunits;
+    const int ntiles = (int)((ncounts + SCAN_TILE - 1) / SCAN_TILE);
+    unsigned int *counts = (unsigned int *)kde_ws(ctx, WS_SORT_COUNTS, (size_t)ncounts * 4);
+    unsigned int *tiles = (unsigned int *)kde_ws(ctx, WS_SORT_STARTS, (size_t)ntiles * 4);
+    if (!counts || !tiles) return KDE_ENOMEM;
+    // warps per block: warp-private histograms must fit the shared-memory budget
+    int wpb = 8;
+    while (wpb > 1 && (size_t)wpb * nbins * 4 > 96 * 1024) wpb >>= 1;
+    const size_t smem = (size_t)wpb * nbins * 4;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(sort_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SORT_WARPS * 8192 * 4);
-        cudaFuncSetAttribute(sort_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SORT_WARPS * 8192 * 4);
+        KDE_CUDA(ctx, cudaFuncSetAttribute(sort_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
+                 "sort attribute");
+        KDE_CUDA(ctx,
+                 cudaFuncSetAttribute(sort_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
+                 "sort attribute");
         attr_set = true;
     }
-    int blocks = (nunits + SORT_WARPS - 1) / SORT_WARPS;
-    sort_count_kernel<<<blocks, SORT_WARPS * 32, smem, ctx->stream>>>(u, N, nbins, nunits, counts);
+    const int blocks = (nunits + wpb - 1) / wpb;
+    sort_count_kernel<<<blocks, wpb * 32, smem, ctx->stream>>>(u, N, nbins, unit, nunits, counts);
     KDE_LAUNCHED(ctx, "sort_count_kernel");
-    sort_colscan_kernel<<<(nbins + 127) / 128, 128, 0, ctx->stream>>>(counts, nbins, nunits, starts);
-    KDE_LAUNCHED(ctx, "sort_colscan_kernel");
-    sort_binscan_kernel<<<1, 1024, 0, ctx->stream>>>(starts, nbins);
-    KDE_LAUNCHED(ctx, "sort_binscan_kernel");
+    sort_scan_tiles_kernel<<<ntiles, SCAN_THREADS, 0, ctx->stream>>>(counts, ncounts, tiles);
+    KDE_LAUNCHED(ctx, "sort_scan_tiles_kernel");
+    sort_scan_totals_kernel<<<1, 1024, 0, ctx->stream>>>(tiles, ntiles);
+    KDE_LAUNCHED(ctx, "sort_scan_totals_kernel");
     ScatterPl sp{};
     sp.n = npl;
     for (int k = 0; k < npl; ++k) {
@@ -152,8 +192,8 @@ kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins
     }
     {
         KdeProfScope _ps(ctx, PROF_SORT);
-    sort_scatter_kernel<<<blocks, SORT_WARPS * 32, smem, ctx->stream>>>(u, N, nbins, nunits, counts, starts, u_out,
-                                                                         sp, perm_out);
+        sort_scatter_kernel<<<blocks, wpb * 32, smem, ctx->stream>>>(u, N, nbins, unit, nunits, counts, tiles, u_out,
+                                                                     sp, perm_out);
     }
     KDE_LAUNCHED(ctx, "sort_scatter_kernel");
     return KDE_OK;
