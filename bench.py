@@ -444,13 +444,101 @@ def spectral_line(args, ctx, world, t_step, value, prof, launches, clk, e2e, wal
                          "frac": ach / hbm, "traffic": None, "avg_launch_ms": g_ms / g_n}}
 
 
+def serve_requests(R, seed=0, nmax_log2=20, cv_nmax_log2=16):
+    """Bounded sample of the serving stream: kinds cycle deposit / gather / CV (16 scale
+    factors on kappa_i) / 10-step PIC; N = floor(2^(12 + (nmax-12) U)) (CV requests capped at
+    2^cv_nmax); Ng log-uniform integer in [64, 4096]; kappa_i log-uniform in [5, 5e3];
+    Maxwellian v_th = 1; uniform positions.  Requests are slices of one shared host pool."""
+    import kde_inputs as I
+    pool = 1 << nmax_log2
+    u = (I.splitmix64(seed, I.STREAM_X, pool) >> np.uint64(32)).astype(np.uint32)
+    kap = I.log_uniform(seed, I.STREAM_KAPPA, pool, 5.0, 5e3).astype(np.float32)
+    v = I.maxwellian(seed, pool, 1.0).astype(np.float32)
+    U = I.uniforms(seed, I.STREAM_REQ, 3 * R)
+    scales = 10.0 ** ((np.arange(16) - 8) / 8.0)
+    reqs = []
+    for q in range(R):
+        kind = 1 + q % 4
+        top = cv_nmax_log2 if kind == 3 else nmax_log2
+        N = int(2 ** (12 + (top - 12) * U[3 * q]))
+        Ng = int(round(64 * 64 ** U[3 * q + 1]))
+        off = int(U[3 * q + 2] * (pool - N))
+        r = dict(kind=kind, N=N, Ng=Ng, u=u[off:off + N], kappa=kap[off:off + N])
+        if kind == 2:
+            r["field"] = np.sin(2 * math.pi * np.arange(Ng) / Ng).astype(np.float32)
+        if kind == 3:
+            r["cand"] = scales
+        if kind == 4:
+            r["v"] = v[off:off + N]
+        reqs.append(r)
+    return reqs
+
+
+def serve_stream(kp, reqs, n_slots, arrivals):
+    """Submit each request at its arrival time (seconds from start) and return latencies (ms)
+    and the makespan (s)."""
+    srv = kp.Server(0, n_slots=n_slots, hbm_budget_bytes=100 << 30)
+    L = 4 * math.pi
+    tickets = []
+    t0 = time.perf_counter()
+    for r, ta in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        out = np.empty(r["Ng"] if r["kind"] == 1 else r["N"], np.float32) if r["kind"] in (1, 2, 4) else None
+        out64 = np.empty(16 if r["kind"] == 3 else 10) if r["kind"] in (3, 4) else None
+        tickets.append(srv.submit(r["kind"], r["u"], L, Ng=r["Ng"], kappa=r["kappa"], v=r.get("v"),
+                                  field=r.get("field"), cand=r.get("cand"), n_steps=10 if r["kind"] == 4 else 0,
+                                  dt=0.1, out=out, out64=out64))
+    lat = np.array([srv.wait(t)[0] for t in tickets])
+    span = time.perf_counter() - t0
+    srv.close()
+    return lat, span
+
+
+def run_serve(args, rank, world, local_rank):
+    import kde_inputs as I
+    import paper_1804_11174_gb300 as kp
+    from paper_1804_11174_gb300 import _build
+    _build.build()
+    if rank != 0:
+        return
+    R = args.requests
+    reqs = serve_requests(R)
+    warm = serve_requests(16, seed=99)
+    serve_stream(kp, warm, 8, np.zeros(len(warm)))
+    # saturated runs (everything submitted at t = 0): throughput of each server
+    lat_p0, span_p = serve_stream(kp, reqs, 1, np.zeros(R))
+    lat_b0, span_b = serve_stream(kp, reqs, args.slots, np.zeros(R))
+    mu_plain = R / span_p
+    # the same Poisson stream at 0.9 x the plain throughput for both servers
+    gaps = -np.log(1.0 - I.uniforms(7, 7, R)) / (0.9 * mu_plain)
+    arr = np.cumsum(gaps) - gaps[0]
+    lat_p, _ = serve_stream(kp, reqs, 1, arr)
+    lat_b, _ = serve_stream(kp, reqs, args.slots, arr)
+    pct = lambda a, q: float(np.percentile(a, q))
+    line = {"metric": METRIC, "value": R / span_b, "unit": "requests/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * span_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: %d requests (deposit/gather/CV/10-step PIC), N log-uniform in "
+                                   "[2^12, 2^20] (CV capped at 2^16), Ng in [64, 4096], kappa_i in [5, 5e3], "
+                                   "HBM budget 100 GB, %d slots" % (R, args.slots)},
+            "saturated": {"batched_rps": R / span_b, "plain_rps": mu_plain},
+            "poisson_0.9x_plain": {"rate_rps": 0.9 * mu_plain,
+                                   "batched": {"p50_ms": pct(lat_b, 50), "p99_ms": pct(lat_b, 99)},
+                                   "plain": {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99)}}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep"])
+    ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep", "serve"])
+    ap.add_argument("--requests", type=int, default=1000, help="serving: requests in the sample")
+    ap.add_argument("--slots", type=int, default=8, help="serving: slots of the batched server")
     ap.add_argument("--cv", default="pairs", choices=["pairs", "spectral"],
                     help="CV evaluation in the width schedule: O(N^2) pair sums or the exact Fourier form")
     args = ap.parse_args()
@@ -461,6 +549,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "cv_sweep":
         run_cv_sweep(args, rank, world, local_rank)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

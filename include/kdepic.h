@@ -232,6 +232,58 @@ kde_status kde_damping_rate(const double *energy, int64_t n, double dt, double *
 kde_status kde_probe_exp2(kde_ctx *ctx, int64_t iters, double *ms_out, int64_t *ops_out);
 kde_status kde_probe_fma(kde_ctx *ctx, int64_t iters, double *ms_out, int64_t *ops_out);
 
+/* ---------------------------------------------------------------------------
+ * Request server (continuous batching).  Not a passage of the paper: it serves
+ * the operations above -- deposit, gather, CV and short PIC runs -- to many
+ * concurrent requests.  n_slots slots each own a context and a CUDA stream and
+ * run on their own host thread; submitted requests wait in one FIFO queue and
+ * the head request starts as soon as a slot is idle and its device footprint
+ * (inputs, outputs, workspace; see the implementation) fits in what is left of
+ * hbm_budget_bytes.  Requests that arrive while others run therefore start as
+ * slots and memory free up, and their kernels overlap on the device.  All
+ * request buffers are HOST memory owned by the caller and must stay valid until
+ * kde_server_wait returns for that ticket.  Every result is bitwise the same
+ * whether the request ran alone or beside others.
+ * ------------------------------------------------------------------------- */
+typedef struct kde_server kde_server;
+
+#define KDE_REQ_DEPOSIT 1 /* out: float32[Ng] density (kde_deposit) */
+#define KDE_REQ_GATHER 2  /* field: float32[Ng]; out: float32[N] (kde_gather) */
+#define KDE_REQ_CV 3      /* cand: float64[n_cand]; out64: float64[n_cand] CV; out_argmin */
+#define KDE_REQ_PIC 4     /* v: float32[N]; n_steps, dt; out64: float64[n_steps] field energy;
+                             out: float32[N] final velocities or NULL */
+
+typedef struct kde_request {
+    int32_t kind;            /* KDE_REQ_* */
+    int64_t N;               /* particles */
+    int32_t Ng;              /* grid nodes (1..KDE_MAX_NG) */
+    double L;                /* domain length */
+    const uint32_t *u;       /* HOST positions [N] */
+    const float *kappa;      /* HOST per-particle widths [N] (CV: kappa_rel), or NULL */
+    double kappa_uniform;    /* width when kappa == NULL (CV: candidates are widths) */
+    const float *v;          /* HOST velocities [N] (PIC) */
+    const float *field;      /* HOST field [Ng] (GATHER) */
+    const double *cand;      /* HOST candidates (CV) */
+    int32_t n_cand;
+    int32_t n_steps;         /* PIC steps */
+    double dt;               /* PIC time step */
+    float *out;              /* HOST float32 output (see kinds) */
+    double *out64;           /* HOST float64 output (see kinds) */
+    int32_t *out_argmin;     /* HOST (CV), or NULL */
+    uint32_t flags;          /* extra kde_cv flags for CV requests (KDE_CV_SPECTRAL) */
+} kde_request;
+
+/* Start a server with n_slots (1..64) slots on `device` under an HBM budget. */
+kde_status kde_server_create(kde_server **out, int device, int32_t n_slots, int64_t hbm_budget_bytes);
+/* Queue a request (validated here; KDE_EINVAL for bad fields or a footprint
+ * larger than the whole budget); *ticket identifies it. */
+kde_status kde_server_submit(kde_server *srv, const kde_request *req, int64_t *ticket);
+/* Wait for a ticket; returns the request's status and the times (ms) from
+ * submission and from admission to completion.  Each ticket is waited once. */
+kde_status kde_server_wait(kde_server *srv, int64_t ticket, double *latency_ms, double *service_ms);
+/* Finish the queued requests, stop the slots and release everything. */
+kde_status kde_server_destroy(kde_server *srv);
+
 /* Measurement support: while enabled, the library records CUDA events on its
  * stream around the launches of selected kernels and counts every kernel it
  * launches.  kde_profile_enable(ctx, on) synchronises, clears the record and

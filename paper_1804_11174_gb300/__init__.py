@@ -20,7 +20,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Context", "PicState", "KdeError", "load_library", "LIB_PATH", "F64", "POISSON_FD", "CV_SCALE", "CV_SPECTRAL",
+__all__ = ["Context", "PicState", "Server", "KdeError", "load_library", "LIB_PATH", "F64", "POISSON_FD", "CV_SCALE", "CV_SPECTRAL",
            "PIC_NO_BACKSTEP", "MAX_NG"]
 
 LIB_PATH = _build.LIB
@@ -57,6 +57,16 @@ class _PicState(ctypes.Structure):
     ]
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [
+        ("kind", _I32), ("N", _I64), ("Ng", _I32), ("L", _D), ("u", _P), ("kappa", _P), ("kappa_uniform", _D),
+        ("v", _P), ("field", _P), ("cand", _P), ("n_cand", _I32), ("n_steps", _I32), ("dt", _D), ("out", _P),
+        ("out64", _P), ("out_argmin", _P), ("flags", _U32),
+    ]
+
+
+REQ_DEPOSIT, REQ_GATHER, REQ_CV, REQ_PIC = 1, 2, 3, 4
+
 _lib = None
 
 
@@ -90,6 +100,10 @@ def load_library(path: str | None = None):
         "kde_probe_fma": (S, [_P, _I64, _P, _P]),
         "kde_profile_enable": (S, [_P, ctypes.c_int]),
         "kde_deposit_noalloc": (S, [_P, _P, _P, _D, _P, _I64, _I32, _D, _P, _U32]),
+        "kde_server_create": (S, [ctypes.POINTER(_P), ctypes.c_int, _I32, _I64]),
+        "kde_server_submit": (S, [_P, ctypes.POINTER(_Request), ctypes.POINTER(_I64)]),
+        "kde_server_wait": (S, [_P, _I64, _P, _P]),
+        "kde_server_destroy": (S, [_P]),
         "kde_profile_read": (S, [_P, ctypes.c_int, _P, _P]),
     }
     for name, (res, args) in sigs.items():
@@ -330,3 +344,81 @@ class PicState:
     @property
     def step(self) -> int:
         return self.c.step
+
+
+class Server:
+    """kde_server_*: continuous-batching request server over host numpy buffers.
+
+    submit() copies nothing on the host: it keeps references to the numpy arrays until
+    wait() returns for the ticket (the library reads and writes them from its slots)."""
+
+    def __init__(self, device: int = 0, n_slots: int = 4, hbm_budget_bytes: int = 100 << 30):
+        self.lib = load_library()
+        h = _P()
+        rc = self.lib.kde_server_create(ctypes.byref(h), int(device), int(n_slots), int(hbm_budget_bytes))
+        if rc != 0:
+            raise KdeError("kde_server_create", rc, "cannot start the server")
+        self.h = h
+        self.keep = {}
+
+    def submit(self, kind, u, L, Ng=1, kappa=None, kappa_uniform=0.0, v=None, field=None, cand=None, n_steps=0,
+               dt=0.0, out=None, out64=None, flags=0):
+        u = np.ascontiguousarray(u, dtype=np.uint32)
+        arrs = [u]
+        r = _Request()
+        r.kind, r.N, r.Ng, r.L = int(kind), u.size, int(Ng), float(L)
+        r.u = u.ctypes.data
+
+        def f32(a):
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            arrs.append(a)
+            return a
+
+        if kappa is not None:
+            r.kappa = f32(kappa).ctypes.data
+        r.kappa_uniform = float(kappa_uniform)
+        if v is not None:
+            r.v = f32(v).ctypes.data
+        if field is not None:
+            r.field = f32(field).ctypes.data
+        if cand is not None:
+            c = np.ascontiguousarray(cand, dtype=np.float64)
+            arrs.append(c)
+            r.cand, r.n_cand = c.ctypes.data, c.size
+        r.n_steps, r.dt = int(n_steps), float(dt)
+        am = np.zeros(1, dtype=np.int32)
+        arrs.append(am)
+        r.out_argmin = am.ctypes.data
+        if out is not None:
+            r.out = out.ctypes.data
+            arrs.append(out)
+        if out64 is not None:
+            r.out64 = out64.ctypes.data
+            arrs.append(out64)
+        r.flags = int(flags)
+        t = _I64()
+        rc = self.lib.kde_server_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if rc != 0:
+            raise KdeError("kde_server_submit", rc, "invalid request")
+        self.keep[t.value] = (arrs, am)
+        return t.value
+
+    def wait(self, ticket):
+        lat = ctypes.c_double()
+        svc = ctypes.c_double()
+        rc = self.lib.kde_server_wait(self.h, int(ticket), ctypes.addressof(lat), ctypes.addressof(svc))
+        arrs, am = self.keep.pop(ticket)
+        if rc != 0:
+            raise KdeError("kde_server_wait", rc, "request failed")
+        return lat.value, svc.value, int(am[0])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.kde_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
