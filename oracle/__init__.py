@@ -66,6 +66,14 @@ def _load():
                                     _P, _I, _D, _D, _D, _I, _I, _P, _P]),
                 "or_damping_rate": (_I, [_P, _I, _D, _P, _P, _P]),
                 "or_kde_at": (None, [_P, _P, _D, _P, _I64, _D, _P, _I64, _P]),
+                "or_ad_statistic": (_D, [_P, _I64]),
+                "or_ad_cdf_of_position": (_D, [_D, _D]),
+                "or_ad_cdf": (_D, [_D, _I64]),
+                "or_ad_pvalue": (_D, [_D, _I64]),
+                "or_ad_log_pvalue": (_D, [_D, _I64]),
+                "or_ad_schedule_step": (_I, [_D, _D, _P]),
+                "or_pic_run_ad": (_I, [_P, _P, _P, _I64, _I, _D, _D, _D, _D, _D, _I, _I, _P, _I, _D, _D,
+                                       _I, _I64, _P, _P, _P, _P, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -250,3 +258,66 @@ def damping_rate(W, dt: float):
     if rc != 0:
         raise ValueError("fewer than two energy maxima")
     return g.value, p1.value, p2.value
+
+
+def ad_statistic(F) -> float:
+    """Anderson-Darling A^2 of CDF values F(X_i) in (0, 1) against the uniform (Sec. II.D)."""
+    F = _f64(F)
+    return _load().or_ad_statistic(_ptr(F), F.size)
+
+
+def ad_cdf_of_codes(u):
+    """The uniform CDF as the test sees 32-bit position codes: (u + 1/2) / 2^32."""
+    return (np.asarray(u, dtype=np.uint32).astype(np.float64) + 0.5) / 4294967296.0
+
+
+def ad_cdf_of_position(x: float, L: float) -> float:
+    return _load().or_ad_cdf_of_position(float(x), float(L))
+
+
+def ad_cdf(z: float, n: int) -> float:
+    """P(A^2 <= z) for n uniform samples (Marsaglia & Marsaglia 2004)."""
+    return _load().or_ad_cdf(float(z), int(n))
+
+
+def ad_pvalue(a2: float, n: int) -> float:
+    """p-value of A^2 for n samples (Marsaglia up to A^2 = 7, the limiting tail beyond)."""
+    return _load().or_ad_pvalue(float(a2), int(n))
+
+
+def ad_log_pvalue(a2: float, n: int) -> float:
+    return _load().or_ad_log_pvalue(float(a2), int(n))
+
+
+def ad_schedule_step(lp: float, threshold: float, lp_th: float):
+    """One step of the Sec. II.D update rule on ln p-values; lp_th >= 0 means "start".
+    Returns (optimise, new lp_th)."""
+    s = ctypes.c_double(lp_th)
+    r = _load().or_ad_schedule_step(float(lp), float(threshold), ctypes.addressof(s))
+    return bool(r), s.value
+
+
+def pic_run_ad(x, v, L: float, Ng: int, dt: float, nsteps: int, kappa_u: float, cands,
+               threshold: float = 0.01, rate: float = 0.05, qm: float = -1.0, charge: float = -1.0,
+               background: float = 1.0, fd: bool = False, backstep: bool = True, step0: int = 0,
+               lp_th: float = 0.0, h_target: float = 0.0):
+    """Electrostatic PIC run (Sec. III.A) whose uniform width follows the Anderson-Darling
+    update algorithm of Sec. II.D; returns dict with x, v, the state (kappa, p_th, h_target)
+    and per-step energy, kappa, ln p-value and optimisation flags."""
+    x = _f64(x).copy()
+    v = _f64(v).copy()
+    cand = _f64(cands)
+    k = ctypes.c_double(kappa_u)
+    pth = ctypes.c_double(lp_th)
+    ht = ctypes.c_double(h_target)
+    W = np.empty(nsteps, dtype=np.float64)
+    ks = np.empty(nsteps, dtype=np.float64)
+    pv = np.empty(nsteps, dtype=np.float64)
+    cvf = np.empty(nsteps, dtype=np.int32)
+    _load().or_pic_run_ad(_ptr(x), _ptr(v), ctypes.addressof(k), x.size, int(Ng), float(L), float(dt),
+                          float(qm), float(charge), float(background), int(fd), int(nsteps), _ptr(cand),
+                          cand.size, float(threshold), float(rate), int(backstep), int(step0),
+                          ctypes.addressof(pth), ctypes.addressof(ht), _ptr(W), _ptr(ks), _ptr(pv),
+                          _ptr(cvf))
+    return {"x": x, "v": v, "kappa_u": k.value, "lp_th": pth.value, "h_target": ht.value, "energy": W,
+            "kappa": ks, "log_pvalue": pv, "optimised": cvf.astype(bool)}

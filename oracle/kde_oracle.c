@@ -468,6 +468,171 @@ int or_pic_run(double *x, double *v, double *kappa, int per_particle, double kap
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Sec. II.D: Anderson-Darling test of the positions against the uniform     */
+/* distribution on the domain.  F[i] = F(X_i) are the values of the uniform */
+/* CDF at the samples, in (0, 1).  With F_(1) <= ... <= F_(n) sorted:         */
+/*   A^2 = -n - (1/n) sum_{i=1}^{n} (2i - 1) [ln F_(i) + ln(1 - F_(n+1-i))]   */
+/* (Anderson & Darling 1954).  The sort is a library qsort; the sum runs in  */
+/* index order.                                                              */
+/* ------------------------------------------------------------------------ */
+static int or_cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+double or_ad_statistic(const double *F, int64_t n)
+{
+    double *s = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    memcpy(s, F, sizeof(double) * (size_t)n);
+    qsort(s, (size_t)n, sizeof(double), or_cmp_double);
+    double sum = 0.0;
+    for (int64_t i = 1; i <= n; ++i) sum += (2.0 * i - 1.0) * (log(s[i - 1]) + log(1.0 - s[n - i]));
+    free(s);
+    return -(double)n - sum / (double)n;
+}
+
+/* The uniform CDF at a position as the test sees it: at the resolution of the */
+/* 32-bit position code, at the centre of the code's cell,                     */
+/* F = (floor(x / L * 2^32) + 1/2) / 2^32, which lies strictly inside (0, 1).  */
+double or_ad_cdf_of_position(double x, double L)
+{
+    double q = floor(x / L * 4294967296.0);
+    if (q < 0.0) q = 0.0;
+    if (q > 4294967295.0) q = 4294967295.0;
+    return (q + 0.5) / 4294967296.0;
+}
+
+/* P(A^2 <= z) for n samples from the hypothesised distribution, following   */
+/* Marsaglia & Marsaglia, "Evaluating the Anderson-Darling distribution",     */
+/* J. Stat. Softw. 9(2), 2004: the limiting distribution by their two fitted  */
+/* expressions (below and above z = 2), plus their finite-n correction, which */
+/* is a function of n and of the limiting value.                             */
+static double or_ad_limit(double z)
+{
+    if (z <= 0.0) return 0.0;
+    if (z < 2.0)
+        return exp(-1.2337141 / z) / sqrt(z) *
+               (2.00012 + (0.247105 - (0.0649821 - (0.0347962 - (0.011672 - 0.00168691 * z) * z) * z) * z) * z);
+    return exp(-exp(1.0776 - (2.30695 - (0.43424 - (0.082433 - (0.008056 - 0.0003146 * z) * z) * z) * z) * z));
+}
+
+static double or_ad_finite_n(int64_t n_, double x)
+{
+    const double n = (double)n_;
+    if (x > 0.8)
+        return (-130.2137 + (745.2337 - (1705.091 - (1950.646 - (1116.360 - 255.7844 * x) * x) * x) * x) * x) / n;
+    const double c = 0.01265 + 0.1757 / n;
+    if (x < c) {
+        double t = x / c;
+        t = sqrt(t) * (1.0 - t) * (49.0 * t - 102.0);
+        return t * (0.0037 / (n * n) + 0.00078 / n + 0.00006) / n;
+    }
+    double t = (x - c) / (0.8 - c);
+    t = -0.00022633 + (6.54034 - (14.6538 - (14.458 - (8.259 - 1.91864 * t) * t) * t) * t) * t;
+    return t * (0.04213 + 0.01365 / n) / n;
+}
+
+double or_ad_cdf(double z, int64_t n)
+{
+    const double x = or_ad_limit(z);
+    double p = x + or_ad_finite_n(n, x);
+    if (p < 0.0) p = 0.0;
+    if (p > 1.0) p = 1.0;
+    return p;
+}
+
+/* Natural log of the p-value of the test: the probability, under the uniform */
+/* hypothesis, of an A^2 at least this large.  Up to A^2 = 7 it is           */
+/* 1 - P(A^2 <= z) from the expressions above.  Beyond, where those fitted    */
+/* expressions stop resolving the tail (they reach 1 to double precision), it */
+/* follows the large-z behaviour of the limiting distribution: A^2 is a sum   */
+/* of chi^2_1 variables weighted 1/(j(j+1)); the j = 1 term dominates the     */
+/* tail, so P(A^2 > z) ~ C z^{-1/2} e^{-z}.  The constant is taken from the   */
+/* value at z = 7, so the p-value is continuous and keeps decreasing, and the */
+/* log form does not underflow for the huge statistics of strongly clustered  */
+/* samples.                                                                   */
+#define OR_AD_ZJOIN 7.0
+double or_ad_log_pvalue(double a2, int64_t n)
+{
+    if (a2 <= OR_AD_ZJOIN) return log(1.0 - or_ad_cdf(a2, n));
+    return log(1.0 - or_ad_cdf(OR_AD_ZJOIN, n)) + 0.5 * log(OR_AD_ZJOIN / a2) + (OR_AD_ZJOIN - a2);
+}
+
+double or_ad_pvalue(double a2, int64_t n) { return exp(or_ad_log_pvalue(a2, n)); }
+
+/* Sec. II.D update rule for one step, written on logs of p-values.  State:  */
+/* lp_th = ln p_th (a value >= 0 means "no step yet": it starts at            */
+/* ln(2 threshold)).  Returns 1 when the width is to be re-optimised at this  */
+/* step (the caller then minimises CV and takes the new target), else 0:     */
+/*   p > 2 threshold            -> p_th = 2 threshold                         */
+/*   else if p < p_th / 2       -> optimise, p_th = p                         */
+int or_ad_schedule_step(double lp, double threshold, double *lp_th)
+{
+    const double l2t = log(2.0 * threshold);
+    if (*lp_th >= 0.0) *lp_th = l2t;
+    if (lp > l2t) {
+        *lp_th = l2t;
+        return 0;
+    }
+    if (lp < *lp_th - log(2.0)) {
+        *lp_th = lp;
+        return 1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. III.A PIC cycle with the width-update algorithm of Sec. II.D on a    */
+/* uniform width.  Every step, before the deposit: the AD p-value of the      */
+/* positions, the update rule above; on an optimisation step the uniform CV   */
+/* over `cand` (Fourier form) gives the target width.  Widths are smoothed in */
+/* h = kappa^{-1/2}: h = rate h_target + (1 - rate) h.  Until the first       */
+/* optimisation the caller's width kappa_u is used; the first optimisation    */
+/* sets h = h_target (there is no earlier optimum to smooth from).           */
+/* State (in/out): *lp_th (>= 0 on entry = start), *h_target (0 = no          */
+/* optimisation yet), *kappa_u.  Outputs per step (optional): W_out,          */
+/* kappa_out (width in force), lp_out (ln p-value), cv_out (1 on optimisation)*/
+/* ------------------------------------------------------------------------ */
+int or_pic_run_ad(double *x, double *v, double *kappa_u, int64_t N, int Ng, double L, double dt, double qm,
+                  double charge, double background, int poisson_fd, int nsteps, const double *cand, int n_cand,
+                  double threshold, double rate, int backstep, int64_t step0, double *lp_th, double *h_target,
+                  double *W_out, double *kappa_out, double *lp_out, int *cv_out)
+{
+    double *rho = (double *)malloc(sizeof(double) * (size_t)Ng);
+    double *E = (double *)malloc(sizeof(double) * (size_t)Ng);
+    double *Ei = (double *)malloc(sizeof(double) * (size_t)N);
+    double *F = (double *)malloc(sizeof(double) * (size_t)N);
+    double *cv = (double *)malloc(sizeof(double) * (size_t)(n_cand > 0 ? n_cand : 1));
+    double h = 1.0 / sqrt(*kappa_u);
+    for (int n = 0; n < nsteps; ++n) {
+        for (int64_t i = 0; i < N; ++i) F[i] = or_ad_cdf_of_position(x[i], L);
+        const double lp = or_ad_log_pvalue(or_ad_statistic(F, N), N);
+        const int opt = or_ad_schedule_step(lp, threshold, lp_th);
+        if (opt) {
+            for (int c = 0; c < n_cand; ++c) cv[c] = or_cv_fourier(x, N, L, cand[c], NULL, NULL, NULL);
+            const double ht = 1.0 / sqrt(cand[or_argmin(cv, n_cand)]);
+            if (!(*h_target > 0.0)) h = ht;
+            *h_target = ht;
+        }
+        if (*h_target > 0.0) h = rate * *h_target + (1.0 - rate) * h;
+        *kappa_u = 1.0 / (h * h);
+        if (lp_out) lp_out[n] = lp;
+        if (cv_out) cv_out[n] = opt;
+        if (kappa_out) kappa_out[n] = *kappa_u;
+        or_deposit(x, NULL, *kappa_u, NULL, N, Ng, L, rho);
+        for (int g = 0; g < Ng; ++g) rho[g] = background + charge * rho[g];
+        if (poisson_fd) or_poisson_fd(rho, Ng, L, E);
+        else or_poisson_spectral(rho, Ng, L, E);
+        if (W_out) W_out[n] = or_field_energy(E, Ng, L);
+        or_gather(x, NULL, *kappa_u, N, E, Ng, L, Ei);
+        or_push(x, v, Ei, N, L, dt, qm, (step0 + n == 0 && backstep) ? 0.5 : 1.0);
+    }
+    free(rho); free(E); free(Ei); free(F); free(cv);
+    return 0;
+}
+
 /* Sec. III.B: damping rate from the field energy.  The slope of ln W through
  * the first two strict local maxima after t = 0 (steps n >= 1) is the energy
  * decay rate; the amplitude rate gamma is half of it.  Returns 0 and sets
