@@ -183,6 +183,18 @@ kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64
 kde_status kde_adapt_widths(kde_ctx *ctx, const float *loo, int64_t N, double L, double kappa_star,
                             double alpha, double kappa_min, double kappa_max, float *kappa_out);
 
+/* Anderson-Darling test of the positions against the uniform distribution on
+ * the domain (Sec. II.D, where it decides when the width is re-optimised).
+ * u: device uint32[N] position codes in any order (not modified); each sample
+ * is taken at its code cell's centre, F_i = (u_i + 1/2) / 2^32.  N >= KDE_AD_MIN_N.
+ * a2_out: the statistic A^2 = -n - (1/n) sum_i (2i - 1)[ln F_(i) + ln(1 - F_(n+1-i))];
+ * log_p_out: natural log of the p-value -- Marsaglia & Marsaglia (2004) for
+ * A^2 <= 7 (finite-n corrected), the limiting tail C (A^2)^{-1/2} e^{-A^2}
+ * beyond.  Both HOST, either may be NULL.  Synchronises.  The sum runs in
+ * FP64 with FP32 in-bin logarithms: |error of A^2| <= about 2e-11 N. */
+#define KDE_AD_MIN_N 8
+kde_status kde_ad_test(kde_ctx *ctx, const uint32_t *u, int64_t N, double *a2_out, double *log_p_out);
+
 /* State of one electrostatic PIC run (Sec. III.A).  The caller owns all arrays.
  * pic_step reorders particles (u, v, kappa and id move together) by cell. */
 typedef struct pic_state {
@@ -208,15 +220,32 @@ typedef struct pic_state {
     double *kappa_star;   /* device float64[steps] CV width in force per step, or NULL */
     int64_t step;         /* step counter (in/out); step 0 gets a half velocity kick */
     uint32_t flags;       /* KDE_F64, KDE_POISSON_FD, KDE_CV_SPECTRAL (width schedule); PIC_NO_BACKSTEP */
+    /* Width-update algorithm of Sec. II.D on the uniform width (kappa == NULL;
+     * replaces width_every).  Every step, before the deposit: ln p of the
+     * Anderson-Darling test of the positions; if p > 2 ad_threshold then
+     * p_th = 2 ad_threshold, else if p < p_th / 2 the CV over cand picks a
+     * target width and p_th = p; then h = adjust_rate h_target +
+     * (1 - adjust_rate) h with h = kappa_uniform^{-1/2}.  The caller's
+     * kappa_uniform holds until the first optimisation, which sets h = h_target.
+     * Reads the p-value on the host: one synchronisation per step. */
+    int32_t width_ad;     /* != 0: use this schedule */
+    double ad_threshold;  /* significance threshold (the paper uses 0.01) */
+    double adjust_rate;   /* smoothing rate (the paper uses 0.05) */
+    double ad_log_pth;    /* state, in/out: ln p_th; >= 0 means not started */
+    double h_target;      /* state, in/out: target h of the last optimisation; 0 = none yet */
+    int64_t n_opt;        /* state, in/out: optimisations so far */
+    double *ad_log_p;     /* device float64[steps] ln p-value per step (indexed by step), or NULL */
 } pic_state;
 
 #define PIC_NO_BACKSTEP 0x100u /* do not halve the first kick at step 0 */
 
 /* Advance the run by n_steps leap-frog steps.  Each step: (width update when
- * width_every > 0 and step % width_every == 0), counting sort by cell,
- * deposit, Poisson, field energy, gather, push.  At step 0 the velocity kick
- * is halved (v^{1/2} = v^0 + (q/m) E^0 dt / 2) unless PIC_NO_BACKSTEP.
- * Stream-ordered; no host synchronisation. */
+ * width_every > 0 and step % width_every == 0, or the Sec. II.D schedule when
+ * width_ad != 0), counting sort by cell, deposit, Poisson, field energy,
+ * gather, push.  At step 0 the velocity kick is halved
+ * (v^{1/2} = v^0 + (q/m) E^0 dt / 2) unless PIC_NO_BACKSTEP.
+ * Stream-ordered; no host synchronisation except the width_ad schedule's one
+ * read of the p-value (and of the CV argmin on optimisation steps) per step. */
 kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps);
 
 /* Damping rate (Sec. III.B) from a field-energy history on the HOST: half the
@@ -291,7 +320,7 @@ kde_status kde_server_destroy(kde_server *srv);
  * synchronises and returns the summed device time and launch count of one
  * kernel: 0 CV pair sums, 1 deposit, 2 gather(+push), 3 sort scatter,
  * 4 Poisson, 5 CV integral-term deposit, 6 CV leave-one-out, 7 spectral
- * structure factor; kernel = -1
+ * structure factor, 8 Anderson-Darling terms; kernel = -1
  * returns the number of all kernel launches in *n. */
 kde_status kde_profile_enable(kde_ctx *ctx, int on);
 kde_status kde_profile_read(kde_ctx *ctx, int kernel, double *total_ms, int64_t *launches);

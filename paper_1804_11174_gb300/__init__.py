@@ -54,6 +54,8 @@ class _PicState(ctypes.Structure):
         ("width_every", _I32), ("cand", _P), ("n_cand", _I32),
         ("alpha", _D), ("kappa_min", _D), ("kappa_max", _D),
         ("energy", _P), ("kappa_star", _P), ("step", _I64), ("flags", _U32),
+        ("width_ad", _I32), ("ad_threshold", _D), ("adjust_rate", _D), ("ad_log_pth", _D), ("h_target", _D),
+        ("n_opt", _I64), ("ad_log_p", _P),
     ]
 
 
@@ -93,6 +95,7 @@ def load_library(path: str | None = None):
         "kde_poisson": (S, [_P, _P, _I32, _D, _D, _D, _P, _P, _U32]),
         "kde_gather": (S, [_P, _P, _P, _D, _I64, _P, _I32, _D, _P, _U32]),
         "kde_cv": (S, [_P, _P, _P, _I64, _D, _P, _I32, _P, _P, _P, _U32]),
+        "kde_ad_test": (S, [_P, _P, _I64, _P, _P]),
         "kde_adapt_widths": (S, [_P, _P, _I64, _D, _D, _D, _D, _D, _P]),
         "pic_step": (S, [_P, ctypes.POINTER(_PicState), _I32]),
         "kde_damping_rate": (S, [_P, _I64, _D, _P]),
@@ -224,6 +227,15 @@ class Context:
                                               _ptr(loo), flags))
         return cv, am.value, loo
 
+    def ad_test(self, u):
+        """Anderson-Darling test of the positions against the uniform distribution (Sec. II.D):
+        returns (A^2, ln p)."""
+        a2 = ctypes.c_double()
+        lp = ctypes.c_double()
+        self._check("kde_ad_test", self.lib.kde_ad_test(self.h, _ptr(u), u.numel(), ctypes.addressof(a2),
+                                                        ctypes.addressof(lp)))
+        return a2.value, lp.value
+
     def adapt_widths(self, loo, L: float, kappa_star: float, alpha: float = 0.5, kappa_min: float = 0.0,
                      kappa_max: float = 1e6, out=None):
         """kde_adapt_widths: Silverman particle-wise widths from leave-one-out densities."""
@@ -243,7 +255,7 @@ class Context:
         self._check("pic_step", self.lib.pic_step(self.h, ctypes.byref(state.c), int(n_steps)))
 
     PROF = {"cv_pairs": 0, "deposit": 1, "gather": 2, "sort": 3, "poisson": 4, "cv_grid": 5, "cv_loo": 6,
-            "spectral": 7}
+            "spectral": 7, "ad": 8}
 
     def profile_enable(self, on: bool = True):
         """kde_profile_enable: start (or stop) recording per-kernel device times."""
@@ -309,7 +321,8 @@ class PicState:
     def __init__(self, u, v, L: float, Ng: int, dt: float, kappa=None, kappa_uniform: float = 0.0, ids=None,
                  qm: float = -1.0, charge: float = -1.0, background: float = 1.0, width_every: int = 0,
                  cand=None, alpha: float = 0.5, kappa_min: float = 0.0, kappa_max: float = 1e6,
-                 max_steps: int = 0, fd: bool = False, backstep: bool = True, cv_spectral: bool = False):
+                 max_steps: int = 0, fd: bool = False, backstep: bool = True, cv_spectral: bool = False,
+                 width_ad: bool = False, ad_threshold: float = 0.01, adjust_rate: float = 0.05):
         torch = _torch()
         self.u, self.v, self.kappa, self.id = u, v, kappa, ids
         f64 = v.dtype == torch.float64
@@ -318,6 +331,7 @@ class PicState:
         dev = u.device
         self.energy = torch.zeros(max(max_steps, 1), dtype=torch.float64, device=dev)
         self.kappa_star = torch.zeros(max(max_steps, 1), dtype=torch.float64, device=dev)
+        self.ad_log_p = torch.zeros(max(max_steps, 1), dtype=torch.float64, device=dev)
         self.max_steps = max_steps
         c = _PicState()
         c.N = u.numel()
@@ -330,6 +344,9 @@ class PicState:
         c.step = 0
         c.flags = ((F64 if f64 else 0) | (POISSON_FD if fd else 0) | (0 if backstep else PIC_NO_BACKSTEP)
                    | (CV_SPECTRAL if cv_spectral else 0))
+        c.width_ad = int(bool(width_ad))
+        c.ad_threshold, c.adjust_rate = float(ad_threshold), float(adjust_rate)
+        c.ad_log_pth, c.h_target, c.n_opt = 0.0, 0.0, 0
         self.c = c
 
     def _sync_in(self):
@@ -340,6 +357,7 @@ class PicState:
         ok = self.max_steps > 0
         c.energy = _ptr(self.energy) if ok else None
         c.kappa_star = _ptr(self.kappa_star) if ok else None
+        c.ad_log_p = _ptr(self.ad_log_p) if ok else None
 
     @property
     def step(self) -> int:

@@ -73,12 +73,16 @@ enum WsSlot {
     WS_SP_PART,
     WS_SP_S,
     WS_SP_A,
+    WS_AD_Z,
+    WS_AD_T,
+    WS_AD_PART,
+    WS_AD_OUT,
     WS_NSLOTS
 };
 
 // kernels timed by the profiling hook (kde_profile_enable / kde_profile_read)
 enum KdeProfId { PROF_CV_PAIRS = 0, PROF_DEPOSIT, PROF_GATHER, PROF_SORT, PROF_POISSON, PROF_CV_GRID, PROF_CV_LOO,
-                 PROF_SPECTRAL, PROF_NIDS };
+                 PROF_SPECTRAL, PROF_AD, PROF_NIDS };
 
 struct kde_ctx {
     int device = 0;
@@ -97,6 +101,8 @@ struct kde_ctx {
     std::map<std::pair<int, int>, void *> node_tab;
     // cached Green's functions keyed by (Ng, L bits, fd, precision)
     std::map<std::tuple<int, uint64_t, int, int>, void *> green_tab;
+    // Anderson-Darling per-bin logarithms (one table per context)
+    void *ad_tab = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -281,6 +287,9 @@ struct SortPayload {
 };
 kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, uint32_t *u_out,
                            const SortPayload *pl, int npl, uint32_t *perm_out);
+// ascending sort of N 32-bit codes (LSD radix, four stable 8-bit passes);
+// tmp: N-element scratch; u may alias neither out nor tmp
+kde_status kde_radix_sort_u32(kde_ctx *ctx, const uint32_t *u, int64_t N, uint32_t *out, uint32_t *tmp);
 
 // deposit of cell-sorted particles into int64 accumulators acc[Ng] (zeroed
 // here).  Particle j contributes w_j * coef * norm_j * exp(-2 kappa_j sin^2(..)).
@@ -340,6 +349,11 @@ struct CandList {
 kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64_t N, double L,
                          const double *cand_host, int n_cand, bool scale_mode, double *cv_dev, int *argmin_dev,
                          float *loo, double *kstar_dev);
+
+// Anderson-Darling test (Sec. II.D) of positions u (any order) against the
+// uniform distribution: out_dev[0] = A^2, out_dev[1] = ln p; ln p also to
+// *lp_slot when not null.  Stream-ordered.
+kde_status kde_ad_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double *out_dev, double *lp_slot);
 
 // the same results by the exact Fourier form (uniform widths only)
 kde_status kde_cv_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *cand_host,

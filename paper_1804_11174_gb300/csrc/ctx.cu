@@ -172,6 +172,7 @@ extern "C" kde_status kde_destroy(kde_ctx *ctx)
         if (ctx->ws[i]) cudaFree(ctx->ws[i]);
     for (auto &kv : ctx->node_tab) cudaFree(kv.second);
     for (auto &kv : ctx->green_tab) cudaFree(kv.second);
+    if (ctx->ad_tab) cudaFree(ctx->ad_tab);
     if (ctx->d_status) cudaFree(ctx->d_status);
     for (auto &p : ctx->prof) {
         cudaEventDestroy(p.second.first);

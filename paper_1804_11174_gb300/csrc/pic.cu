@@ -1,8 +1,11 @@
 // pic.cu -- the electrostatic PIC cycle of Sec. III.A on the device.
 //
-// Per step (all stream-ordered, no host synchronisation):
+// Per step (stream-ordered; no host synchronisation except in the AD schedule):
 //   [width update: CV over the uniform candidates, kappa* = argmin on the
 //    device, leave-one-out pilot densities, Silverman widths + norms]
+//   [or the Sec. II.D schedule on the uniform width: Anderson-Darling p-value
+//    read on the host, the update rule, CV on optimisation steps, smoothing
+//    of h = kappa^{-1/2}]
 //   counting sort by cell (positions, velocities, widths, norms, labels)
 //   deposit -> int64 grid accumulators
 //   Poisson solve straight from the accumulators (mean removed in FP64)
@@ -29,7 +32,8 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
     const int Ng = st->Ng;
     const double L = st->L;
     const bool per = st->kappa != nullptr;
-    const bool sched = st->width_every > 0 && st->n_cand > 0;
+    const bool adsched = st->width_ad != 0;
+    const bool sched = !adsched && st->width_every > 0 && st->n_cand > 0;
     const bool fd = (st->flags & KDE_POISSON_FD) != 0;
     T *norm_arr = (T *)st->kappa_norm;
 
@@ -51,9 +55,13 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
     T *E = (T *)kde_ws(ctx, WS_GRID0, (size_t)Ng * sizeof(T));
     float *loo = sched ? (float *)kde_ws(ctx, WS_PIC_LOO, (size_t)N * 4) : nullptr;
     double *ks_dev = sched ? (double *)kde_ws(ctx, WS_PIC_KS, 64) : nullptr;
-    double *cv_dev = sched ? (double *)kde_ws(ctx, WS_CV_OUT, (size_t)st->n_cand * 8 + 64) : nullptr;
-    if (!acc || !E || (sched && (!loo || !ks_dev || !cv_dev))) return KDE_ENOMEM;
-    int *amin_dev = sched ? (int *)(cv_dev + st->n_cand) : nullptr;
+    double *cv_dev = (sched || adsched) ? (double *)kde_ws(ctx, WS_CV_OUT, (size_t)st->n_cand * 8 + 64) : nullptr;
+    double *ad_out = adsched ? (double *)kde_ws(ctx, WS_AD_OUT, 16) : nullptr;
+    if (!acc || !E || (sched && (!loo || !ks_dev || !cv_dev)) || (adsched && (!cv_dev || !ad_out)))
+        return KDE_ENOMEM;
+    int *amin_dev = (sched || adsched) ? (int *)(cv_dev + st->n_cand) : nullptr;
+    // the AD schedule smooths h = kappa^{-1/2}, carried across the steps of this call
+    double h_ad = adsched ? 1.0 / sqrt(st->kappa_uniform) : 0.0;
 
     if (per) {
         norm_from_kappa_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>((const T *)st->kappa, N,
@@ -74,6 +82,39 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
             KDE_TRY(kde_adapt_device(ctx, loo, N, L, ks_dev, 0.0, st->alpha, st->kappa_min, st->kappa_max, st->kappa,
                                      norm_arr, sizeof(T) == 8));
             if (!fetch_ws()) return KDE_ENOMEM;
+        }
+        if (adsched) {
+            KDE_TRY(kde_ad_device(ctx, st->u, N, ad_out, st->ad_log_p ? st->ad_log_p + step : nullptr));
+            double ad_h[2];
+            KDE_CUDA(ctx, cudaMemcpyAsync(ad_h, ad_out, 16, cudaMemcpyDeviceToHost, ctx->stream), "AD result copy");
+            KDE_TRY(kde_sync(ctx));
+            const double lp = ad_h[1], l2t = log(2.0 * st->ad_threshold);
+            if (st->ad_log_pth >= 0.0) st->ad_log_pth = l2t;
+            bool opt = false;
+            if (lp > l2t) {
+                st->ad_log_pth = l2t;
+            } else if (lp < st->ad_log_pth - log(2.0)) {
+                st->ad_log_pth = lp;
+                opt = true;
+            }
+            if (opt) {
+                if (st->flags & KDE_CV_SPECTRAL)
+                    KDE_TRY(kde_cv_spectral_device(ctx, st->u, N, L, st->cand, st->n_cand, cv_dev, amin_dev, nullptr,
+                                                   nullptr));
+                else
+                    KDE_TRY(kde_cv_device(ctx, st->u, nullptr, N, L, st->cand, st->n_cand, false, cv_dev, amin_dev,
+                                          nullptr, nullptr));
+                int am = 0;
+                KDE_CUDA(ctx, cudaMemcpyAsync(&am, amin_dev, 4, cudaMemcpyDeviceToHost, ctx->stream), "argmin copy");
+                KDE_TRY(kde_sync(ctx));
+                const double ht = 1.0 / sqrt(st->cand[am]);
+                if (!(st->h_target > 0.0)) h_ad = ht;
+                st->h_target = ht;
+                ++st->n_opt;
+                if (!fetch_ws()) return KDE_ENOMEM;
+            }
+            if (st->h_target > 0.0) h_ad = st->adjust_rate * st->h_target + (1.0 - st->adjust_rate) * h_ad;
+            st->kappa_uniform = 1.0 / (h_ad * h_ad);
         }
         SortPayload pl[4];
         int npl = 0;
@@ -126,11 +167,22 @@ extern "C" kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps)
                         KDE_MAX_NG);
     if (st->flags & ~(KDE_F64 | KDE_POISSON_FD | KDE_CV_SPECTRAL | PIC_NO_BACKSTEP))
         return kde_fail(ctx, KDE_ENOTSUP, "pic_step: unsupported flags 0x%x", st->flags);
+    if (st->width_ad) {
+        if (st->kappa || !st->cand || st->n_cand < 1 || st->n_cand > 256 || st->N < KDE_AD_MIN_N ||
+            !(st->ad_threshold > 0 && st->ad_threshold < 0.5) || !(st->adjust_rate > 0 && st->adjust_rate <= 1))
+            return kde_fail(ctx, KDE_EINVAL,
+                            "pic_step: the Anderson-Darling schedule needs a uniform width (kappa == NULL), 1..256 "
+                            "host candidates, N >= %d, 0 < ad_threshold < 0.5 and 0 < adjust_rate <= 1",
+                            KDE_AD_MIN_N);
+        for (int c = 0; c < st->n_cand; ++c)
+            if (!(st->cand[c] > 0 && st->cand[c] <= KDE_KAPPA_MAX))
+                return kde_fail(ctx, KDE_EINVAL, "pic_step: candidate %d outside (0, 1e6]", c);
+    }
     if (st->kappa && !st->kappa_norm)
         return kde_fail(ctx, KDE_EINVAL, "pic_step: per-particle widths need the kappa_norm array");
     if (!st->kappa && !(st->kappa_uniform > 0 && st->kappa_uniform <= KDE_KAPPA_MAX))
         return kde_fail(ctx, KDE_EINVAL, "pic_step: kappa_uniform must be in (0, 1e6]");
-    if (st->width_every > 0 && st->n_cand > 0) {
+    if (!st->width_ad && st->width_every > 0 && st->n_cand > 0) {
         if (!st->kappa || !st->cand || st->n_cand > 256 || st->N < 2 || !(st->alpha >= 0) ||
             !(st->kappa_min <= st->kappa_max))
             return kde_fail(ctx, KDE_EINVAL,

@@ -12,6 +12,9 @@
 //             rank.
 // The order inside a bin is the input order (stable), so results are
 // deterministic.  Units are small enough to keep thousands of warps in flight.
+//
+// The same kernels in digit mode (key = a bit field of the code) give an LSD
+// radix sort of the full 32-bit codes: four stable passes of 8-bit digits.
 #include "common.cuh"
 
 #define SORT_MAX_COUNTS (1 << 22)
@@ -20,8 +23,18 @@
 
 __device__ __forceinline__ int bin_of(uint32_t u, int nbins) { return (int)(((uint64_t)u * (uint64_t)nbins) >> 32); }
 
-__global__ void sort_count_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int unit, int nunits,
-                                  unsigned int *counts)
+// sort key: the bin floor(u nbins / 2^32), or in digit mode the bit field
+// (u >> shift) mod nbins (nbins a power of two)
+template <bool DIGIT>
+__device__ __forceinline__ int sort_key(uint32_t u, int nbins, int shift)
+{
+    if (DIGIT) return (int)((u >> shift) & (uint32_t)(nbins - 1));
+    return bin_of(u, nbins);
+}
+
+template <bool DIGIT>
+__global__ void sort_count_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int shift, int unit,
+                                  int nunits, unsigned int *counts)
 {
     extern __shared__ unsigned int hist[];
     const int wpb = blockDim.x >> 5;
@@ -32,7 +45,7 @@ __global__ void sort_count_kernel(const uint32_t *__restrict__ u, int64_t N, int
     __syncwarp();
     if (un >= nunits) return;
     const int64_t i0 = (int64_t)un * unit, i1 = i0 + unit < N ? i0 + unit : N;
-    for (int64_t i = i0 + lane; i < i1; i += 32) atomicAdd(&h[bin_of(u[i], nbins)], 1u);
+    for (int64_t i = i0 + lane; i < i1; i += 32) atomicAdd(&h[sort_key<DIGIT>(u[i], nbins, shift)], 1u);
     __syncwarp();
     for (int b = lane; b < nbins; b += 32) counts[(size_t)b * nunits + un] = h[b];
 }
@@ -102,9 +115,11 @@ struct ScatterPl {
 
 #define SORT_MAXR 8  // 32-particle steps loaded ahead per chunk of the unit
 
-__global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int unit, int nunits,
-                                    const unsigned int *__restrict__ seg, const unsigned int *__restrict__ tiles,
-                                    uint32_t *u_out, ScatterPl pl, uint32_t *perm_out)
+template <bool DIGIT>
+__global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int shift, int unit,
+                                    int nunits, const unsigned int *__restrict__ seg,
+                                    const unsigned int *__restrict__ tiles, uint32_t *u_out, ScatterPl pl,
+                                    uint32_t *perm_out)
 {
     extern __shared__ unsigned int hist[];
     const int wpb = blockDim.x >> 5;
@@ -128,7 +143,7 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
             const int64_t i = c0 + r * 32 + lane;
             if (c0 + r * 32 >= i1) break;
             const bool valid = i < i1;
-            const int key = valid ? bin_of(uu[r], nbins) : -1;
+            const int key = valid ? sort_key<DIGIT>(uu[r], nbins, shift) : -1;
             const unsigned int peers = __match_any_sync(0xffffffffu, key);
             const unsigned int rank = __popc(peers & lt);
             const unsigned int before = valid ? h[key] : 0u;
@@ -149,12 +164,10 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
     }
 }
 
-kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, uint32_t *u_out,
-                           const SortPayload *pl, int npl, uint32_t *perm_out)
+template <bool DIGIT>
+static kde_status sort_pass(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, int shift, uint32_t *u_out,
+                            const SortPayload *pl, int npl, uint32_t *perm_out)
 {
-    if (N <= 0) return KDE_OK;
-    if (nbins < 1 || nbins > 8192 || npl > 4 || N > 0xFFFFFFFFll)
-        return kde_fail(ctx, KDE_EINVAL, "sort: unsupported sizes");
     int unit = 256;
     while ((int64_t)nbins * ((N + unit - 1) / unit) > SORT_MAX_COUNTS) unit *= 2;
     const int nunits = (int)((N + unit - 1) / unit);
@@ -169,15 +182,17 @@ kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins
     const size_t smem = (size_t)wpb * nbins * 4;
     static bool attr_set = false;
     if (!attr_set) {
-        KDE_CUDA(ctx, cudaFuncSetAttribute(sort_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
+        KDE_CUDA(ctx,
+                 cudaFuncSetAttribute(sort_count_kernel<DIGIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
                  "sort attribute");
         KDE_CUDA(ctx,
-                 cudaFuncSetAttribute(sort_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
+                 cudaFuncSetAttribute(sort_scatter_kernel<DIGIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      96 * 1024),
                  "sort attribute");
         attr_set = true;
     }
     const int blocks = (nunits + wpb - 1) / wpb;
-    sort_count_kernel<<<blocks, wpb * 32, smem, ctx->stream>>>(u, N, nbins, unit, nunits, counts);
+    sort_count_kernel<DIGIT><<<blocks, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nunits, counts);
     KDE_LAUNCHED(ctx, "sort_count_kernel");
     sort_scan_tiles_kernel<<<ntiles, SCAN_THREADS, 0, ctx->stream>>>(counts, ncounts, tiles);
     KDE_LAUNCHED(ctx, "sort_scan_tiles_kernel");
@@ -192,9 +207,32 @@ kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins
     }
     {
         KdeProfScope _ps(ctx, PROF_SORT);
-        sort_scatter_kernel<<<blocks, wpb * 32, smem, ctx->stream>>>(u, N, nbins, unit, nunits, counts, tiles, u_out,
-                                                                     sp, perm_out);
+        sort_scatter_kernel<DIGIT><<<blocks, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nunits, counts,
+                                                                            tiles, u_out, sp, perm_out);
     }
     KDE_LAUNCHED(ctx, "sort_scatter_kernel");
+    return KDE_OK;
+}
+
+kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, uint32_t *u_out,
+                           const SortPayload *pl, int npl, uint32_t *perm_out)
+{
+    if (N <= 0) return KDE_OK;
+    if (nbins < 1 || nbins > 8192 || npl > 4 || N > 0xFFFFFFFFll)
+        return kde_fail(ctx, KDE_EINVAL, "sort: unsupported sizes");
+    return sort_pass<false>(ctx, u, N, nbins, 0, u_out, pl, npl, perm_out);
+}
+
+kde_status kde_radix_sort_u32(kde_ctx *ctx, const uint32_t *u, int64_t N, uint32_t *out, uint32_t *tmp)
+{
+    if (N <= 0) return KDE_OK;
+    if (N > 0xFFFFFFFFll) return kde_fail(ctx, KDE_EINVAL, "radix sort: at most 2^32 - 1 keys");
+    // LSD: digits 0..3 of 8 bits, u -> tmp -> out -> tmp -> out
+    const uint32_t *src = u;
+    uint32_t *dst[4] = {tmp, out, tmp, out};
+    for (int d = 0; d < 4; ++d) {
+        KDE_TRY(sort_pass<true>(ctx, src, N, 256, 8 * d, dst[d], nullptr, 0, nullptr));
+        src = dst[d];
+    }
     return KDE_OK;
 }

@@ -91,12 +91,21 @@ def _landau_run(ctx, kp, oracle, N, steps):
     cand = I.log_candidates(1.0, 1e4, 64)
     st = make_state(kp, u, v32, L, Ng, dt, steps, kappa=np.ones(N), width_every=50, cand=cand, alpha=0.5,
                     kappa_min=1.0, kappa_max=1e5)
-    ctx.pic_step(st, steps)
+    ctx.pic_step(st, 50)
+    ctx.sync()
+    u50 = st.u.cpu().numpy().view(np.uint32).copy()
+    ctx.pic_step(st, steps - 50)
     ctx.sync()
     r = oracle.pic_run(I.from_fixed(u, L), v32, L, Ng, dt, steps, kappa=np.ones(N), width_every=50, cands=cand,
                        alpha=0.5, kmin=1.0, kmax=1e5)
     ks = st.kappa_star.cpu().numpy()
-    assert ks[0] == r["kstar"][0] and ks[50] == r["kstar"][50]
+    assert ks[0] == r["kstar"][0]
+    # After 50 steps the FP32 run and the FP64 oracle hold slightly different positions, so
+    # the second width is checked on the GPU's own positions: the oracle's CV curve there
+    # must have its minimum at the GPU's choice, unless the two are a near-tie.
+    cv = oracle.cv_curve(I.from_fixed(u50, L), L, cand, fourier=True)
+    best, mine = oracle.argmin(cv), int(np.flatnonzero(cand == ks[50])[0])
+    assert mine == best or cv[mine] - cv[best] <= 2e-5 * np.abs(cv).max(), (mine, best)
     g_gpu = kp.damping_rate(st.energy.cpu().numpy(), dt)
     g_or = oracle.damping_rate(r["energy"], dt)[0]
     assert abs(g_gpu - g_or) <= 1e-3, (g_gpu, g_or)
