@@ -31,8 +31,8 @@
 #define AD_BITS 16                    // table bins: the top 16 bits of the code
 #define AD_NBINS (1 << AD_BITS)
 #define AD_EDGE 256                   // bins at each end taken in FP64 per sample
-#define AD_THREADS 256
-#define AD_PER 8                      // consecutive sorted samples per thread
+#define AD_THREADS 128
+#define AD_PER 16                     // consecutive sorted samples per thread
 #define AD_TILE (AD_THREADS * AD_PER)  // samples per block
 #define AD_ZJOIN 7.0
 
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(AD_THREADS)
     long long sa = 0, sb = 0, sad = 0, sbd = 0;
     AdBin tb{};
     auto flush = [&]() { big += (double)sa * tb.lnF + (double)sad * tb.r1 + (double)sb * tb.ln1mF - (double)sbd * tb.r2; };
-#pragma unroll
+#pragma unroll 4
     for (int q = 0; q < AD_PER; ++q) {
         const int64_t i = i0 + q;
         if (i >= N) break;
@@ -91,16 +91,15 @@ __global__ void __launch_bounds__(AD_THREADS)
             tb = tab[b];
         }
         const long long wa = 2 * (i + 1) - 1, wb = 2 * N + 1 - 2 * (i + 1);
-        const double Fi = ((double)y + 0.5) * (1.0 / 4294967296.0);
         if (b < AD_EDGE) {
-            big += (double)wa * log(Fi);
+            big += (double)wa * log(((double)y + 0.5) * (1.0 / 4294967296.0));
         } else {
             sa += wa;
             sad += wa * d;
             small = fmaf((float)wa, ad_log1p_rem((float)d * tb.r1f), small);
         }
         if (b >= AD_NBINS - AD_EDGE) {
-            big += (double)wb * log1p(-Fi);
+            big += (double)wb * log1p(-((double)y + 0.5) * (1.0 / 4294967296.0));
         } else {
             sb += wb;
             sbd += wb * d;
