@@ -73,6 +73,10 @@ enum WsSlot {
     WS_SP_PART,
     WS_SP_S,
     WS_SP_A,
+    WS_SP_ASEL,
+    WS_SP_AS,
+    WS_SP_SEL,
+    WS_SP_MLIM,
     WS_AD_Z,
     WS_AD_T,
     WS_AD_PART,
@@ -354,6 +358,12 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
 // uniform distribution: out_dev[0] = A^2, out_dev[1] = ln p; ln p also to
 // *lp_slot when not null.  Stream-ordered.
 kde_status kde_ad_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double *out_dev, double *lp_slot);
+
+// leave-one-out densities at the width cand[*argmin_dev] (caller's order) by the
+// exact Fourier form: the same values as the pair-sum pass, O(N M(kappa*)) work
+kde_status kde_loo_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *cand_host,
+                                   int n_cand, const int *argmin_dev, float *loo);
+int kde_spec_modes(double kappa);  // Fourier modes the exact form keeps for a width
 
 // the same results by the exact Fourier form (uniform widths only)
 kde_status kde_cv_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *cand_host,

@@ -893,6 +893,20 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
     cv_combine_kernel<<<1, 32, 0, ctx->stream>>>(f2, tot, cc, cl, N, L, cv_dev, argmin_dev, kstar_dev);
     KDE_LAUNCHED(ctx, "cv_combine_kernel");
 
+    // Leave-one-out densities at kappa* (uniform widths): the pair sums cost about
+    // N^2 frac(kappa*) exponentials (frac = share of the circle inside the truncation
+    // radius), the exact Fourier form about 4 N M(kappa*) exponential-equivalents.
+    // The choice is made for the widest candidate and the narrowest: where the Fourier
+    // form is cheaper at the largest candidate it is cheaper at every candidate.
+    if (loo && !scale_mode) {
+        const double kmx = cl.k[n_cand - 1];
+        const double s2 = KDE_XCUT * KDE_LN2 / (2.0 * kmx);
+        const double frac = s2 >= 1.0 ? 1.0 : 2.0 * asin(sqrt(s2)) / KDE_PI;
+        if (4.0 * kde_spec_modes(kmx) < (double)N * frac) {
+            KDE_TRY(kde_loo_spectral_device(ctx, u, N, L, cand_host, n_cand, argmin_dev, loo));
+            return KDE_OK;
+        }
+    }
     if (loo) {
         CvLooArgs B{};
         B.sc = sc;

@@ -47,17 +47,20 @@ __device__ void spec_ratios(double kappa, int M, double *A)
     for (int m = 1; m <= M; ++m) A[m] *= A[m - 1];
 }
 
-// structure factor partials: block (chunk, mode block); thread = one mode
+// structure factor partials: block (chunk, mode block); thread = one mode.  The
+// partials are laid out with stride M; modes above *mlim (when given) are skipped.
 __global__ void __launch_bounds__(SP_THREADS)
-    spec_sf_kernel(const uint32_t *__restrict__ u, int64_t N, int64_t chunk, int M, double2 *part)
+    spec_sf_kernel(const uint32_t *__restrict__ u, int64_t N, int64_t chunk, int M, const int *mlim, double2 *part)
 {
     extern __shared__ uint32_t us[];
+    const int Me = mlim ? min(M, *mlim) : M;
+    if (1 + (int)blockIdx.y * SP_THREADS > Me) return;  // the whole mode block is above the limit
     const int64_t j0 = (int64_t)blockIdx.x * chunk;
     const int n = (int)(N - j0 < chunk ? N - j0 : chunk);
     for (int k = threadIdx.x; k < n; k += SP_THREADS) us[k] = u[j0 + k];
     __syncthreads();
     const int m = 1 + blockIdx.y * SP_THREADS + threadIdx.x;
-    if (m > M) return;
+    if (m > Me) return;
     double cr = 0.0, ci = 0.0;
     for (int k0 = 0; k0 < n; k0 += SP_SUB) {
         const int k1 = k0 + SP_SUB < n ? k0 + SP_SUB : n;
@@ -76,11 +79,11 @@ __global__ void __launch_bounds__(SP_THREADS)
     part[(size_t)blockIdx.x * M + (m - 1)] = make_double2(cr, ci);
 }
 
-// S_m = sum over chunks in chunk order
-__global__ void spec_reduce_kernel(const double2 *part, int nchunks, int M, double2 *S)
+// S_m = sum over chunks in chunk order (modes up to *mlim when given)
+__global__ void spec_reduce_kernel(const double2 *part, int nchunks, int M, const int *mlim, double2 *S)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= M) return;
+    if (m >= (mlim ? min(M, *mlim) : M)) return;
     double sr = 0.0, si = 0.0;
     for (int c = 0; c < nchunks; ++c) {
         double2 p = part[(size_t)c * M + m];
@@ -90,76 +93,193 @@ __global__ void spec_reduce_kernel(const double2 *part, int nchunks, int M, doub
     S[m] = make_double2(sr, si);
 }
 
-// per candidate (caller's order): Bessel ratios, the three mode sums and CV (x
-// units); then argmin (smallest index on ties) and the selected width
-__global__ void spec_cv_kernel(const double2 *S, CandList cl, int64_t N, double L, int Astride, double *Atab,
-                               double *cv_out, int *argmin, double *kstar)
+// one CTA per candidate (caller's order): Bessel ratios (sequential recurrence,
+// one thread), then the three mode sums over the block and CV (x units)
+__global__ void __launch_bounds__(SP_THREADS)
+    spec_cv_kernel(const double2 *S, CandList cl, int64_t N, double L, int Astride, double *Atab, double *cv_out)
 {
-    const int c = threadIdx.x;
+    __shared__ double r0[SP_THREADS], r1[SP_THREADS], r2[SP_THREADS];
+    const int c = blockIdx.x;
     const double n = (double)N;
-    if (c < cl.n) {
-        const double kappa = cl.k[c];
-        const int M = spec_modes(kappa);
-        double *A = Atab + (size_t)c * Astride;
-        spec_ratios(kappa, M, A);
-        double sA = 0.0, sAS = 0.0, sA2S = 0.0;
-        for (int m = 1; m <= M; ++m) {
-            const double2 s = S[m - 1];
-            const double p = s.x * s.x + s.y * s.y;
-            sA += A[m];
-            sAS += A[m] * p;
-            sA2S += A[m] * A[m] * p;
-        }
-        const double f2 = (n * n + 2.0 * sA2S) / (KDE_TWO_PI * n * n);
-        const double pairs = (n * n + 2.0 * sAS - n - 2.0 * n * sA) / KDE_TWO_PI;
-        cv_out[c] = (KDE_TWO_PI / L) * (f2 - 2.0 * pairs / (n * (n - 1.0)));
-    }
+    const double kappa = cl.k[c];
+    const int M = spec_modes(kappa);
+    double *A = Atab + (size_t)c * Astride;
+    if (threadIdx.x == 0) spec_ratios(kappa, M, A);
     __syncthreads();
+    double sA = 0.0, sAS = 0.0, sA2S = 0.0;
+    for (int m = 1 + threadIdx.x; m <= M; m += SP_THREADS) {
+        const double2 s = S[m - 1];
+        const double p = s.x * s.x + s.y * s.y;
+        const double a = A[m];
+        sA += a;
+        sAS += a * p;
+        sA2S += a * a * p;
+    }
+    r0[threadIdx.x] = sA;
+    r1[threadIdx.x] = sAS;
+    r2[threadIdx.x] = sA2S;
+    __syncthreads();
+    for (int o = SP_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            r0[threadIdx.x] += r0[threadIdx.x + o];
+            r1[threadIdx.x] += r1[threadIdx.x + o];
+            r2[threadIdx.x] += r2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        int best = 0;
-        for (int q = 1; q < cl.n; ++q)
-            if (cv_out[q] < cv_out[best]) best = q;
-        *argmin = best;
-        if (kstar) *kstar = cl.k[best];
+        const double f2 = (n * n + 2.0 * r2[0]) / (KDE_TWO_PI * n * n);
+        const double pairs = (n * n + 2.0 * r1[0] - n - 2.0 * n * r0[0]) / KDE_TWO_PI;
+        cv_out[c] = (KDE_TWO_PI / L) * (f2 - 2.0 * pairs / (n * (n - 1.0)));
     }
 }
 
-// leave-one-out density at the selected width for every particle (input order)
-__global__ void __launch_bounds__(SP_THREADS)
-    spec_loo_kernel(const uint32_t *__restrict__ u, int64_t N, const double2 *S, CandList cl, int Astride,
-                    const double *Atab, const int *argmin, double xs, float *loo)
+// argmin (smallest index on ties) and the selected width
+__global__ void spec_argmin_kernel(const double *cv, CandList cl, int *argmin, double *kstar)
 {
-    __shared__ double sA[512];
-    __shared__ double2 sS[512];
-    const int c = *argmin;
-    const double kappa = cl.k[c];
+    int best = 0;
+    for (int q = 1; q < cl.n; ++q)
+        if (cv[q] < cv[best]) best = q;
+    *argmin = best;
+    if (kstar) *kstar = cl.k[best];
+}
+
+// the selected width kappa* = cand[*argmin]: its mode count, Bessel ratios A[0..M]
+// and normalisation 1 / (2 pi I0e(kappa*)), for the leave-one-out pass
+struct SpecSel {
+    int M;
+    double norm;
+};
+__global__ void spec_select_kernel(CandList cl, const int *argmin, SpecSel *sel, double *A)
+{
+    const double kappa = cl.k[*argmin];
     const int M = spec_modes(kappa);
-    const double *A = Atab + (size_t)c * Astride;
+    spec_ratios(kappa, M, A);
+    sel->M = M;
+    sel->norm = kde_norm(kappa);
+}
+
+// A_m S_m in FP32 for the leave-one-out sums
+__global__ void spec_as_kernel(const double2 *S, const double *A, const SpecSel *sel, float2 *AS)
+{
+    const int m = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > sel->M) return;
+    const double2 s = S[m - 1];
+    AS[m - 1] = make_float2((float)(A[m] * s.x), (float)(A[m] * s.y));
+}
+
+// leave-one-out density at the selected width for every particle (input order):
+// sum_j K(theta_i - theta_j) = (1/2pi)(n + 2 sum_m Re(e^{i m theta_i} conj(A_m S_m))),
+// minus the particle's own K(0).  Exact integer phases, FP32 terms with compensated
+// (Kahan) summation over the modes; the combination in FP64 once per particle.
+#define SP_LOO_CH 1024
+__global__ void __launch_bounds__(SP_THREADS)
+    spec_loo_kernel(const uint32_t *__restrict__ u, int64_t N, const float2 *__restrict__ AS,
+                    const SpecSel *__restrict__ sel, double xs, float *loo)
+{
+    __shared__ float2 sAS[SP_LOO_CH];
+    const int M = sel->M;
     const int64_t i = (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
     const uint32_t ui = i < N ? u[i] : 0u;
-    double acc = 0.0;
-    for (int m0 = 1; m0 <= M; m0 += 512) {
-        const int cnt = M - m0 + 1 < 512 ? M - m0 + 1 : 512;
+    float acc = 0.f, comp = 0.f;
+    for (int m0 = 1; m0 <= M; m0 += SP_LOO_CH) {
+        const int cnt = M - m0 + 1 < SP_LOO_CH ? M - m0 + 1 : SP_LOO_CH;
         __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += SP_THREADS) {
-            sA[k] = A[m0 + k];
-            sS[k] = S[m0 + k - 1];
-        }
+        for (int k = threadIdx.x; k < cnt; k += SP_THREADS) sAS[k] = AS[m0 - 1 + k];
         __syncthreads();
+#pragma unroll 4
         for (int k = 0; k < cnt; ++k) {
             const uint32_t ph = (uint32_t)(m0 + k) * ui;
             float s, co;
             sincospif((float)(int32_t)ph * (1.0f / 2147483648.0f), &s, &co);
-            const double2 q = sS[k];
-            // Re(e^{i m theta_i} conj(S_m)) = cos * Sr + sin * Si
-            acc += sA[k] * ((double)co * q.x + (double)s * q.y);
+            const float2 q = sAS[k];
+            // Re(e^{i m theta_i} conj(A_m S_m)) = cos * Re + sin * Im, added with compensation
+            const float y = fmaf(co, q.x, s * q.y) - comp;
+            const float t = acc + y;
+            comp = (t - acc) - y;
+            acc = t;
         }
     }
     if (i >= N) return;
     const double n = (double)N;
-    const double all = (n + 2.0 * acc) / KDE_TWO_PI;
-    loo[i] = (float)(xs * (all - kde_norm(kappa)) / (n - 1.0));
+    const double all = (n + 2.0 * ((double)acc - (double)comp)) / KDE_TWO_PI;
+    loo[i] = (float)(xs * (all - sel->norm) / (n - 1.0));
 }
+
+// leave-one-out densities at cand[*argmin] from the structure factor S (modes
+// 1..M(kappa*) present)
+static kde_status spec_loo_from_S(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double2 *S,
+                                  const CandList &cl, int Mmax, const int *argmin_dev, float *loo)
+{
+    double *Asel = (double *)kde_ws(ctx, WS_SP_ASEL, (size_t)(Mmax + 1) * 8 + 64);
+    float2 *AS = (float2 *)kde_ws(ctx, WS_SP_AS, (size_t)Mmax * sizeof(float2) + 64);
+    SpecSel *sel = (SpecSel *)kde_ws(ctx, WS_SP_SEL, sizeof(SpecSel));
+    if (!Asel || !AS || !sel) return KDE_ENOMEM;
+    spec_select_kernel<<<1, 1, 0, ctx->stream>>>(cl, argmin_dev, sel, Asel);
+    KDE_LAUNCHED(ctx, "spec_select_kernel");
+    spec_as_kernel<<<(Mmax + 255) / 256, 256, 0, ctx->stream>>>(S, Asel, sel, AS);
+    KDE_LAUNCHED(ctx, "spec_as_kernel");
+    {
+        KdeProfScope _ps(ctx, PROF_CV_LOO);
+        spec_loo_kernel<<<(unsigned)((N + SP_THREADS - 1) / SP_THREADS), SP_THREADS, 0, ctx->stream>>>(
+            u, N, AS, sel, KDE_TWO_PI / L, loo);
+    }
+    KDE_LAUNCHED(ctx, "spec_loo_kernel");
+    return KDE_OK;
+}
+
+// structure factor for modes 1..M (or up to *mlim) into S
+static kde_status spec_structure(kde_ctx *ctx, const uint32_t *u, int64_t N, int M, const int *mlim, double2 **S_out)
+{
+    int64_t chunk = 4096;
+    while ((N + chunk - 1) / chunk > 256 && chunk < SP_MAXCHUNK) chunk *= 2;
+    const int nchunks = (int)((N + chunk - 1) / chunk);
+    double2 *part = (double2 *)kde_ws(ctx, WS_SP_PART, (size_t)nchunks * M * sizeof(double2));
+    double2 *S = (double2 *)kde_ws(ctx, WS_SP_S, (size_t)M * sizeof(double2));
+    if (!part || !S) return KDE_ENOMEM;
+    static bool attr = false;
+    if (!attr) {
+        KDE_CUDA(ctx, cudaFuncSetAttribute(spec_sf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           SP_MAXCHUNK * 4),
+                 "spec_sf_kernel attribute");
+        attr = true;
+    }
+    {
+        KdeProfScope _ps(ctx, PROF_SPECTRAL);
+        dim3 grid((unsigned)nchunks, (unsigned)((M + SP_THREADS - 1) / SP_THREADS));
+        spec_sf_kernel<<<grid, SP_THREADS, (size_t)chunk * 4, ctx->stream>>>(u, N, chunk, M, mlim, part);
+    }
+    KDE_LAUNCHED(ctx, "spec_sf_kernel");
+    spec_reduce_kernel<<<(M + 255) / 256, 256, 0, ctx->stream>>>(part, nchunks, M, mlim, S);
+    KDE_LAUNCHED(ctx, "spec_reduce_kernel");
+    *S_out = S;
+    return KDE_OK;
+}
+
+// selected width's mode count, for the structure factor of the leave-one-out pass
+__global__ void spec_mlim_kernel(CandList cl, const int *argmin, int *mlim) { *mlim = spec_modes(cl.k[*argmin]); }
+
+kde_status kde_loo_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *cand_host,
+                                   int n_cand, const int *argmin_dev, float *loo)
+{
+    CandList cl{};
+    cl.n = n_cand;
+    double kmax = 0.0;
+    for (int c = 0; c < n_cand; ++c) {
+        cl.k[c] = cand_host[c];
+        kmax = cand_host[c] > kmax ? cand_host[c] : kmax;
+    }
+    const int Mmax = spec_modes(kmax);
+    int *mlim = (int *)kde_ws(ctx, WS_SP_MLIM, 64);
+    if (!mlim) return KDE_ENOMEM;
+    spec_mlim_kernel<<<1, 1, 0, ctx->stream>>>(cl, argmin_dev, mlim);
+    KDE_LAUNCHED(ctx, "spec_mlim_kernel");
+    double2 *S = nullptr;
+    KDE_TRY(spec_structure(ctx, u, N, Mmax, mlim, &S));
+    return spec_loo_from_S(ctx, u, N, L, S, cl, Mmax, argmin_dev, loo);
+}
+
+int kde_spec_modes(double kappa) { return spec_modes(kappa); }
 
 kde_status kde_cv_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *cand_host,
                                   int n_cand, double *cv_dev, int *argmin_dev, float *loo, double *kstar_dev)
@@ -173,36 +293,15 @@ kde_status kde_cv_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, do
         kmax = cand_host[c] > kmax ? cand_host[c] : kmax;
     }
     const int M = spec_modes(kmax);
-    int64_t chunk = 4096;
-    while ((N + chunk - 1) / chunk > 256 && chunk < SP_MAXCHUNK) chunk *= 2;
-    const int nchunks = (int)((N + chunk - 1) / chunk);
     const int Astride = M + 1;
-    double2 *part = (double2 *)kde_ws(ctx, WS_SP_PART, (size_t)nchunks * M * sizeof(double2));
-    double2 *S = (double2 *)kde_ws(ctx, WS_SP_S, (size_t)M * sizeof(double2));
     double *Atab = (double *)kde_ws(ctx, WS_SP_A, (size_t)n_cand * Astride * 8 + 64 * 1024 * 8);
-    if (!part || !S || !Atab) return KDE_ENOMEM;
-    static bool attr = false;
-    if (!attr) {
-        KDE_CUDA(ctx, cudaFuncSetAttribute(spec_sf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SP_MAXCHUNK * 4),
-                 "spec_sf_kernel attribute");
-        attr = true;
-    }
-    const size_t smem = (size_t)chunk * 4;
-    {
-        KdeProfScope _ps(ctx, PROF_SPECTRAL);
-        dim3 grid((unsigned)nchunks, (unsigned)((M + SP_THREADS - 1) / SP_THREADS));
-        spec_sf_kernel<<<grid, SP_THREADS, smem, ctx->stream>>>(u, N, chunk, M, part);
-    }
-    KDE_LAUNCHED(ctx, "spec_sf_kernel");
-    spec_reduce_kernel<<<(M + 255) / 256, 256, 0, ctx->stream>>>(part, nchunks, M, S);
-    KDE_LAUNCHED(ctx, "spec_reduce_kernel");
-    spec_cv_kernel<<<1, 256, 0, ctx->stream>>>(S, cl, N, L, Astride, Atab, cv_dev, argmin_dev, kstar_dev);
+    if (!Atab) return KDE_ENOMEM;
+    double2 *S = nullptr;
+    KDE_TRY(spec_structure(ctx, u, N, M, nullptr, &S));
+    spec_cv_kernel<<<n_cand, SP_THREADS, 0, ctx->stream>>>(S, cl, N, L, Astride, Atab, cv_dev);
     KDE_LAUNCHED(ctx, "spec_cv_kernel");
-    if (loo) {
-        spec_loo_kernel<<<(unsigned)((N + SP_THREADS - 1) / SP_THREADS), SP_THREADS, 0, ctx->stream>>>(
-            u, N, S, cl, Astride, Atab, argmin_dev, KDE_TWO_PI / L, loo);
-        KDE_LAUNCHED(ctx, "spec_loo_kernel");
-    }
+    spec_argmin_kernel<<<1, 1, 0, ctx->stream>>>(cv_dev, cl, argmin_dev, kstar_dev);
+    KDE_LAUNCHED(ctx, "spec_argmin_kernel");
+    if (loo) KDE_TRY(spec_loo_from_S(ctx, u, N, L, S, cl, M, argmin_dev, loo));
     return KDE_OK;
 }
