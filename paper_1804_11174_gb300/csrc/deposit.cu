@@ -319,9 +319,11 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
         }
         return;
     }
-    const int slices = DEP_WARPS / ngroups;
+    // every warp works: warp w takes node group w mod ngroups and one of that group's
+    // particle slices (the groups' slice counts differ by at most one)
     const int gi = warp % ngroups, sl = warp / ngroups;
-    if (sl < slices) {
+    const int slices = (DEP_WARPS - gi + ngroups - 1) / ngroups;
+    {
         const int p0 = (int)((int64_t)n * sl / slices), p1 = (int)((int64_t)n * (sl + 1) / slices);
         int ga, gb;
         bool va, vb;
@@ -335,8 +337,9 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
     __syncthreads();
     for (int r = tid; r < ngroups * 64; r += DEP_THREADS) {
         if (r >= R) continue;
+        const int gr = r >> 6, sr = (DEP_WARPS - gr + ngroups - 1) / ngroups;
         float a = 0.f;
-        for (int k = 0; k < slices; ++k) a += part[k * DEP2_PART + r];
+        for (int k = 0; k < sr; ++k) a += part[k * DEP2_PART + r];
         int g = g_lo + r;
         g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
         const long long v = __double2ll_rn((double)a * scale);
