@@ -588,13 +588,104 @@ def run_serve(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args, rank, world, local_rank):
+    """Ensemble workload: R independent Landau realisations (seeds 0..R-1, alpha = 0.05,
+    v_th = 1, dt = 0.1), N log-uniform in [2^14, 2^20], Ng cycling {128, 256, 512, 1024}, one
+    uniform width per realisation chosen at t = 0 by the exact Fourier form of the CV over 16
+    candidates in [1, 1e3].  One step = one replay of the captured graph over all
+    realisations; compared with the plain form (pic_step per realisation, one after another,
+    on one stream).  value = deposit+gather definition pairs (2 sum_r N_r Ng_r) per second."""
+    import torch
+
+    import kde_inputs as I
+    import paper_1804_11174_gb300 as kp
+    from paper_1804_11174_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = "cuda:%d" % local_rank
+    R = args.realisations
+    L = 4 * math.pi
+    Ns, Ngs = I.ensemble_sizes(R)
+    us, vs = [], []
+    for r in range(R):
+        q = I.uniforms(r, I.STREAM_X, int(Ns[r]))
+        us.append(I.to_fixed(I.inverse_cdf_cosine(q, L, 0.05), L))
+        vs.append(I.maxwellian(r, int(Ns[r]), 1.0).astype(np.float32))
+    ctx = kp.Context(local_rank)
+    cand = I.log_candidates(1.0, 1e3, 16)
+    kap = []
+    for r in range(R):
+        _, am, _ = ctx.cv(torch.from_numpy(us[r].view(np.int32)).to(dev), L, cand, spectral=True)
+        kap.append(float(cand[am]))
+    u = torch.from_numpy(np.concatenate(us).view(np.int32)).to(dev)
+    v = torch.from_numpy(np.concatenate(vs)).to(dev)
+    ens = kp.Ensemble(ctx, Ns, Ngs, kap, L, 0.1, u, v)
+    mise = ens.mise(0.05, 1).cpu().numpy()
+    steps = args.steps * 10
+    en = torch.zeros(R * steps, dtype=torch.float64, device=dev)
+    ens.run(max(args.warmup, 1), None, use_graph=True)
+    ens.run(steps, en, use_graph=True)  # captures the step for this (energy, steps) pair
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush.zero_()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    ens.run(steps, en, use_graph=True)
+    b.record()
+    b.synchronize()
+    t_graph = a.elapsed_time(b) / steps
+    clk = clocks.stop()
+    flush.zero_()
+    a.record()
+    ens.run(steps, en, use_graph=False)
+    b.record()
+    b.synchronize()
+    t_launch = a.elapsed_time(b) / steps
+    # plain form: one realisation after another through pic_step (a bounded sample)
+    sample = min(R, 32)
+    sts = [kp.PicState(torch.from_numpy(us[r].view(np.int32)).to(dev), torch.from_numpy(vs[r]).to(dev), L,
+                       int(Ngs[r]), 0.1, kappa_uniform=kap[r]) for r in range(sample)]
+    for s_ in sts:
+        ctx.pic_step(s_, 1)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(3):
+        for s_ in sts:
+            ctx.pic_step(s_, 1)
+    b.record()
+    b.synchronize()
+    frac = float(np.sum(Ns[:sample])) / float(np.sum(Ns))
+    t_plain = a.elapsed_time(b) / 3 / frac
+    Ntot = float(np.sum(Ns))
+    pairs = 2.0 * float(np.sum(Ns * Ngs))
+    line = {"metric": METRIC, "value": pairs / (t_graph * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": t_graph, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ensemble of %d Landau realisations, N log-uniform in [2^14, 2^20] (total %d), "
+                                   "Ng in {128,256,512,1024}, one CUDA graph per step" % (R, int(Ntot)),
+                       "l2": "inputs larger than L2 (%.0f MB of particle state)" % (Ntot * 8 / 1e6)},
+            "particle_steps_per_s": Ntot / (t_graph * 1e-3),
+            "ms_per_step_graph": t_graph, "ms_per_step_launches": t_launch,
+            "ms_per_step_plain_per_realisation": t_plain,
+            "mise_t0": {"mean": float(np.mean(mise)), "min": float(np.min(mise)), "max": float(np.max(mise))},
+            "kappa_star": {"min": float(np.min(kap)), "max": float(np.max(kap))}, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ens.close()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep", "serve"])
+    ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep", "serve", "ensemble"])
+    ap.add_argument("--realisations", type=int, default=256, help="ensemble: realisations")
     ap.add_argument("--requests", type=int, default=1000, help="serving: requests in the sample")
     ap.add_argument("--slots", type=int, default=8, help="serving: slots of the batched server")
     ap.add_argument("--cv", default="pairs", choices=["pairs", "spectral"],
@@ -609,6 +700,8 @@ def main():
         run_cv_sweep(args, rank, world, local_rank)
     elif args.workload == "serve":
         run_serve(args, rank, world, local_rank)
+    elif args.workload == "ensemble":
+        run_ensemble(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

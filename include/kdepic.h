@@ -254,6 +254,41 @@ kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps);
  * two maxima exist. */
 kde_status kde_damping_rate(const double *energy, int64_t n, double dt, double *gamma_out);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles: R independent realisations of the PIC cycle of pic_step (uniform
+ * width per realisation, q/m = -1, charge -1, background 1, spectral Poisson,
+ * FP32) advanced together, as the ensemble statistics of Sec. III (MISE of the
+ * density, damping rates over many loads) need.  The realisations' particles
+ * are concatenated in the caller's device arrays u (uint32 codes) and v
+ * (float32), realisation r occupying N[r] consecutive slots in order.  The
+ * realisations are dealt to up to 16 lanes, each with its own context and
+ * stream, so that they run concurrently; kde_ensemble_run can capture one step
+ * of the whole ensemble into a CUDA graph and replay it once per step.  Each
+ * realisation's results are bitwise those of pic_step on the same state.  The
+ * arrays are reordered by cell within each realisation.  Not a passage of the
+ * paper: the paper runs its ensembles one after another.
+ * ------------------------------------------------------------------------- */
+typedef struct kde_ensemble kde_ensemble;
+
+/* N, Ng, kappa: HOST arrays of R entries (1 <= N[r] < 2^32, 1 <= Ng[r] <=
+ * KDE_MAX_NG, 0 < kappa[r] <= 1e6); u, v: device arrays of sum(N) entries,
+ * owned by the caller and kept by the ensemble until kde_ensemble_destroy. */
+kde_status kde_ensemble_create(kde_ctx *ctx, kde_ensemble **out, int32_t R, const int64_t *N, const int32_t *Ng,
+                               const double *kappa, double L, double dt, uint32_t *u, float *v);
+/* New uniform widths (HOST, R entries); a captured step is captured again. */
+kde_status kde_ensemble_set_widths(kde_ensemble *ens, const double *kappa);
+/* Integrated squared error of each realisation's deposited density against
+ * 1 + alpha cos(2 pi mode x / L) at the current positions (one sample of the
+ * MISE of Sec. II.B): mise (device float64[R]) = dx sum_g (rho_g - truth_g)^2. */
+kde_status kde_ensemble_mise(kde_ensemble *ens, double alpha, int32_t mode, double *mise);
+/* Advance every realisation by n_steps leap-frog steps (the first step of the
+ * ensemble's life gets pic_step's half kick).  energy: device float64[R * n_steps],
+ * energy[r * n_steps + k] = field energy of realisation r at step k of this call,
+ * or NULL.  use_graph != 0 replays one captured step (captured once per
+ * (energy, n_steps) pair).  Stream-ordered after and before the context's stream. */
+kde_status kde_ensemble_run(kde_ensemble *ens, int32_t n_steps, double *energy, int32_t use_graph);
+kde_status kde_ensemble_destroy(kde_ensemble *ens);
+
 /* Measurement support: throughput probes used to derive the roofline of the
  * pair kernels (not part of the method).  Each launches a dependency-free
  * stream of `iters` operations per thread on all SMs and writes the elapsed

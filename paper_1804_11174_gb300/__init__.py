@@ -20,7 +20,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Context", "PicState", "Server", "KdeError", "load_library", "LIB_PATH", "F64", "POISSON_FD", "CV_SCALE", "CV_SPECTRAL",
+__all__ = ["Context", "PicState", "Server", "Ensemble", "KdeError", "load_library", "LIB_PATH", "F64", "POISSON_FD", "CV_SCALE", "CV_SPECTRAL",
            "PIC_NO_BACKSTEP", "MAX_NG"]
 
 LIB_PATH = _build.LIB
@@ -96,6 +96,11 @@ def load_library(path: str | None = None):
         "kde_gather": (S, [_P, _P, _P, _D, _I64, _P, _I32, _D, _P, _U32]),
         "kde_cv": (S, [_P, _P, _P, _I64, _D, _P, _I32, _P, _P, _P, _U32]),
         "kde_ad_test": (S, [_P, _P, _I64, _P, _P]),
+        "kde_ensemble_create": (S, [_P, ctypes.POINTER(_P), _I32, _P, _P, _P, _D, _D, _P, _P]),
+        "kde_ensemble_set_widths": (S, [_P, _P]),
+        "kde_ensemble_mise": (S, [_P, _D, _I32, _P]),
+        "kde_ensemble_run": (S, [_P, _I32, _P, _I32]),
+        "kde_ensemble_destroy": (S, [_P]),
         "kde_adapt_widths": (S, [_P, _P, _I64, _D, _D, _D, _D, _D, _P]),
         "pic_step": (S, [_P, ctypes.POINTER(_PicState), _I32]),
         "kde_damping_rate": (S, [_P, _I64, _D, _P]),
@@ -362,6 +367,57 @@ class PicState:
     @property
     def step(self) -> int:
         return self.c.step
+
+
+class Ensemble:
+    """kde_ensemble_*: R independent PIC realisations in concatenated device arrays.
+
+    u (int32 view of the uint32 codes) and v (float32) are CUDA tensors of sum(N) entries,
+    realisation r in N[r] consecutive slots; the ensemble keeps references to them."""
+
+    def __init__(self, ctx: "Context", N, Ng, kappa, L: float, dt: float, u, v):
+        self.ctx = ctx
+        self.N = np.ascontiguousarray(N, dtype=np.int64)
+        self.Ng = np.ascontiguousarray(Ng, dtype=np.int32)
+        k = np.ascontiguousarray(kappa, dtype=np.float64)
+        self.u, self.v = u, v
+        h = _P()
+        ctx._check("kde_ensemble_create", ctx.lib.kde_ensemble_create(
+            ctx.h, ctypes.byref(h), self.N.size, self.N.ctypes.data, self.Ng.ctypes.data, k.ctypes.data,
+            float(L), float(dt), _ptr(u), _ptr(v)))
+        self.h = h
+
+    @property
+    def R(self):
+        return self.N.size
+
+    def set_widths(self, kappa):
+        k = np.ascontiguousarray(kappa, dtype=np.float64)
+        self.ctx._check("kde_ensemble_set_widths", self.ctx.lib.kde_ensemble_set_widths(self.h, k.ctypes.data))
+
+    def mise(self, alpha: float, mode: int = 1):
+        torch = _torch()
+        out = torch.empty(self.R, dtype=torch.float64, device=self.u.device)
+        self.ctx._check("kde_ensemble_mise", self.ctx.lib.kde_ensemble_mise(self.h, float(alpha), int(mode),
+                                                                             _ptr(out)))
+        return out
+
+    def run(self, n_steps: int, energy=None, use_graph: bool = True):
+        if energy is not None and energy.numel() < self.R * int(n_steps):
+            raise KdeError("kde_ensemble_run", 1, "energy must hold R * n_steps values")
+        self.ctx._check("kde_ensemble_run", self.ctx.lib.kde_ensemble_run(self.h, int(n_steps), _ptr(energy),
+                                                                           int(use_graph)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.kde_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
