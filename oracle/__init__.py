@@ -67,6 +67,10 @@ def _load():
                 "or_damping_rate": (_I, [_P, _I, _D, _P, _P, _P]),
                 "or_kde_at": (None, [_P, _P, _D, _P, _I64, _D, _P, _I64, _P]),
                 "or_ad_statistic": (_D, [_P, _I64]),
+                "or_bspline": (_D, [_I, _D]),
+                "or_deposit_bspline": (None, [_P, _I64, _I, _D, _I, _D, _P]),
+                "or_gather_bspline": (None, [_P, _I64, _I, _D, _P, _I, _D, _P]),
+                "or_cv_cic": (_D, [_P, _I64, _D, _D]),
                 "or_ad_cdf_of_position": (_D, [_D, _D]),
                 "or_ad_cdf": (_D, [_D, _I64]),
                 "or_ad_pvalue": (_D, [_D, _I64]),
@@ -321,3 +325,32 @@ def pic_run_ad(x, v, L: float, Ng: int, dt: float, nsteps: int, kappa_u: float, 
                           _ptr(cvf))
     return {"x": x, "v": v, "kappa_u": k.value, "lp_th": pth.value, "h_target": ht.value, "energy": W,
             "kappa": ks, "log_pvalue": pv, "optimised": cvf.astype(bool)}
+
+
+def bspline(p: int, t) -> np.ndarray:
+    """Centred cardinal B-spline of degree p (Cox-de Boor recursion), support |t| < (p+1)/2."""
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    f = _load().or_bspline
+    return np.array([f(int(p), float(v)) for v in t])
+
+
+def deposit_bspline(x, Ng: int, L: float, order: int, h: float) -> np.ndarray:
+    """Standard-PIC deposit with the B-spline shape of degree `order` and width h (x units)."""
+    x = _f64(x)
+    rho = np.empty(Ng, dtype=np.float64)
+    _load().or_deposit_bspline(_ptr(x), x.size, int(order), float(h), int(Ng), float(L), _ptr(rho))
+    return rho
+
+
+def gather_bspline(x, E, L: float, order: int, h: float) -> np.ndarray:
+    x = _f64(x)
+    E = _f64(E)
+    out = np.empty(x.size, dtype=np.float64)
+    _load().or_gather_bspline(_ptr(x), x.size, int(order), float(h), _ptr(E), E.size, float(L), _ptr(out))
+    return out
+
+
+def cv_cic(x, L: float, h: float) -> float:
+    """CV of the first-order (CIC) shape of width h (x units)."""
+    x = _f64(x)
+    return _load().or_cv_cic(_ptr(x), x.size, float(L), float(h))

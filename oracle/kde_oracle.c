@@ -633,6 +633,89 @@ int or_pic_run_ad(double *x, double *v, double *kappa_u, int64_t N, int Ng, doub
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Standard-PIC shapes for the comparison of Sec. IV (Fig. compare_high_order):*/
+/* the centred cardinal B-spline of degree p, B_p(t) = N_{p+1}(t + (p+1)/2),  */
+/* with the uniform B-spline of order m on the knots 0..m given by the         */
+/* Cox-de Boor recursion N_1 = 1 on [0, 1),                                    */
+/* N_m(x) = (x N_{m-1}(x) + (m - x) N_{m-1}(x - 1)) / (m - 1).                */
+/* A shape of width h is S(x) = (1/h) B_p(x/h), support (p + 1) h; h = dx is   */
+/* the standard PIC shape ("width (order + 1) dx").                            */
+/* ------------------------------------------------------------------------ */
+static double or_nspline(int m, double x)
+{
+    if (x < 0.0 || x >= (double)m) return 0.0;
+    if (m == 1) return 1.0;
+    return (x * or_nspline(m - 1, x) + ((double)m - x) * or_nspline(m - 1, x - 1.0)) / (double)(m - 1);
+}
+
+double or_bspline(int p, double t) { return or_nspline(p + 1, t + 0.5 * (double)(p + 1)); }
+
+/* shortest periodic signed separation a - b on a circle of length L */
+static double or_periodic(double a, double b, double L)
+{
+    double d = fmod(a - b, L);
+    if (d >= 0.5 * L) d -= L;
+    if (d < -0.5 * L) d += L;
+    return d;
+}
+
+/* deposit with the shape at the nodes: rho_g = sum_i w_i S(x_g - x_i), w_i = L/N, */
+/* periodic ((p + 1) h < L keeps one image in reach)                               */
+void or_deposit_bspline(const double *x, int64_t N, int p, double h, int Ng, double L, double *rho)
+{
+#pragma omp parallel for schedule(static)
+    for (int g = 0; g < Ng; ++g) {
+        const double xg = L * (double)g / (double)Ng;
+        double acc = 0.0;
+        for (int64_t i = 0; i < N; ++i) acc += (L / (double)N) / h * or_bspline(p, or_periodic(xg, x[i], L) / h);
+        rho[g] = acc;
+    }
+}
+
+/* field interpolation with the same shape: E_i = sum_g E_g (dx / h) B_p((x_g - x_i)/h) */
+void or_gather_bspline(const double *x, int64_t N, int p, double h, const double *E, int Ng, double L, double *out)
+{
+    const double dx = L / (double)Ng;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int g = 0; g < Ng; ++g)
+            acc += E[g] * (dx / h) * or_bspline(p, or_periodic(L * (double)g / (double)Ng, x[i], L) / h);
+        out[i] = acc;
+    }
+}
+
+/* Eq. (cv_def) for the first-order (CIC) shape of width h, in x units:          */
+/* int fhat^2 = (1/n^2) sum_{i,j} (S * S)(x_i - x_j) with S * S = (1/h) B_3(./h)   */
+/* (the convolution of two degree-1 B-splines is the cubic one), minus          */
+/* 2/(n(n-1)) sum_{i != j} S(x_i - x_j).  Dense over all pairs; 2h < L/2.         */
+double or_cv_cic(const double *x, int64_t N, double L, double h)
+{
+    double *row3 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *row1 = (double *)malloc(sizeof(double) * (size_t)N);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < N; ++i) {
+        double a3 = 0.0, a1 = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            const double t = or_periodic(x[i], x[j], L) / h;
+            a3 += or_bspline(3, t) / h;
+            if (j != i) a1 += or_bspline(1, t) / h;
+        }
+        row3[i] = a3;
+        row1[i] = a1;
+    }
+    double s3 = 0.0, s1 = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        s3 += row3[i];
+        s1 += row1[i];
+    }
+    free(row3);
+    free(row1);
+    const double n = (double)N;
+    return s3 / (n * n) - 2.0 * s1 / (n * (n - 1.0));
+}
+
 /* Sec. III.B: damping rate from the field energy.  The slope of ln W through
  * the first two strict local maxima after t = 0 (steps n >= 1) is the energy
  * decay rate; the amplitude rate gamma is half of it.  Returns 0 and sets
