@@ -183,6 +183,29 @@ kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64
 kde_status kde_adapt_widths(kde_ctx *ctx, const float *loo, int64_t N, double L, double kappa_star,
                             double alpha, double kappa_min, double kappa_max, float *kappa_out);
 
+/* Standard-PIC particle shapes, for the comparison of Sec. IV (Fig.
+ * compare_high_order: shape order, kernel width and the KDE method).  The shape of
+ * degree `order` (1 = CIC, 2, 3 or 5) and width h (x units) is the centred
+ * cardinal B-spline S(x) = (1/h) B_order(x/h), support (order + 1) h; h = dx = L/Ng
+ * is the standard PIC shape.  Not the paper's method: its baselines.
+ * kde_deposit_bspline: rho_out[g] = sum_i (L/N) S(x_g - x_i) (periodic, point values
+ *   at the nodes, x units); FP32 out, summed exactly in int64 fixed point, so the
+ *   result does not depend on the particle order.  u: device uint32[N], any order.
+ * kde_gather_bspline: out[i] = sum_g field[g] (dx/h) B_order((x_g - x_i)/h).
+ * Both need order in {1, 2, 3, 5}, 0 < (order + 1) h < L, Ng <= KDE_MAX_NG. */
+kde_status kde_deposit_bspline(kde_ctx *ctx, const uint32_t *u, int64_t N, int32_t order, double h, int32_t Ng,
+                               double L, float *rho_out);
+kde_status kde_gather_bspline(kde_ctx *ctx, const uint32_t *u, int64_t N, int32_t order, double h,
+                              const float *field, int32_t Ng, double L, float *out);
+/* Eq. (cv_def) for the first-order (CIC) shape over candidate widths h_c (HOST
+ * float64[n_cand], 0 < h_c < L/4, n_cand <= 64), in x units:
+ *   CV(h) = (1/n^2) sum_{i,j} (1/h) B_3((x_i - x_j)/h) - 2/(n(n-1)) sum_{i != j} (1/h) B_1((x_i - x_j)/h)
+ * (B_1 * B_1 = B_3 gives the integral term exactly).  cv_out: HOST float64[n_cand];
+ * argmin_out: smallest index on ties.  Pair sums in FP32 per tile, FP64 above.
+ * Synchronises. */
+kde_status kde_cv_cic(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *h_cand, int32_t n_cand,
+                      double *cv_out, int32_t *argmin_out);
+
 /* Anderson-Darling test of the positions against the uniform distribution on
  * the domain (Sec. II.D, where it decides when the width is re-optimised).
  * u: device uint32[N] position codes in any order (not modified); each sample

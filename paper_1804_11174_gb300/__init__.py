@@ -96,6 +96,9 @@ def load_library(path: str | None = None):
         "kde_gather": (S, [_P, _P, _P, _D, _I64, _P, _I32, _D, _P, _U32]),
         "kde_cv": (S, [_P, _P, _P, _I64, _D, _P, _I32, _P, _P, _P, _U32]),
         "kde_ad_test": (S, [_P, _P, _I64, _P, _P]),
+        "kde_deposit_bspline": (S, [_P, _P, _I64, _I32, _D, _I32, _D, _P]),
+        "kde_gather_bspline": (S, [_P, _P, _I64, _I32, _D, _P, _I32, _D, _P]),
+        "kde_cv_cic": (S, [_P, _P, _I64, _D, _P, _I32, _P, _P]),
         "kde_ensemble_create": (S, [_P, ctypes.POINTER(_P), _I32, _P, _P, _P, _D, _D, _P, _P]),
         "kde_ensemble_set_widths": (S, [_P, _P]),
         "kde_ensemble_mise": (S, [_P, _D, _I32, _P]),
@@ -231,6 +234,33 @@ class Context:
                                               cand.ctypes.data, cand.size, cv.ctypes.data, ctypes.addressof(am),
                                               _ptr(loo), flags))
         return cv, am.value, loo
+
+    def deposit_bspline(self, u, Ng: int, L: float, order: int, h: float, out=None):
+        """kde_deposit_bspline: standard-PIC shape of degree `order` and width h (x units)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(int(Ng), dtype=torch.float32, device=u.device)
+        self._check("kde_deposit_bspline", self.lib.kde_deposit_bspline(self.h, _ptr(u), u.numel(), int(order),
+                                                                        float(h), int(Ng), float(L), _ptr(out)))
+        return out
+
+    def gather_bspline(self, u, field, L: float, order: int, h: float, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(u.numel(), dtype=torch.float32, device=u.device)
+        self._check("kde_gather_bspline", self.lib.kde_gather_bspline(self.h, _ptr(u), u.numel(), int(order),
+                                                                      float(h), _ptr(field), field.numel(), float(L),
+                                                                      _ptr(out)))
+        return out
+
+    def cv_cic(self, u, L: float, h_cand):
+        """kde_cv_cic: CV of the CIC shape's width over candidates h (x units); returns (cv, argmin)."""
+        h = np.ascontiguousarray(h_cand, dtype=np.float64)
+        cv = np.empty(h.size, dtype=np.float64)
+        am = ctypes.c_int32()
+        self._check("kde_cv_cic", self.lib.kde_cv_cic(self.h, _ptr(u), u.numel(), float(L), h.ctypes.data, h.size,
+                                                      cv.ctypes.data, ctypes.addressof(am)))
+        return cv, am.value
 
     def ad_test(self, u):
         """Anderson-Darling test of the positions against the uniform distribution (Sec. II.D):

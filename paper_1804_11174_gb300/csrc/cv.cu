@@ -1064,3 +1064,196 @@ extern "C" kde_status kde_adapt_widths(kde_ctx *ctx, const float *loo, int64_t N
     return kde_adapt_device(ctx, loo, N, L, nullptr, kappa_star, alpha, kappa_min, kappa_max, kappa_out, nullptr,
                             false);
 }
+
+// ---------------------------------------------------------------------------
+// CV of the first-order (CIC) shape's width (Sec. IV, Fig. compare_high_order f):
+// S_h(x) = (1/h) B_1(x/h), and int fhat^2 = (1/n^2) sum_{i,j} (1/h) B_3((x_i - x_j)/h)
+// since B_1 * B_1 = B_3.  Both sums have compact support (|d| < h and < 2h), so
+// the bin-sorted tiles are walked only while their gap is below 2 h_max; pair
+// distances come from exact integer code differences.  Unordered tile pairs,
+// FP32 sums per tile, FP64 per CTA, a fixed reduction order.
+// ---------------------------------------------------------------------------
+#define CIC_MAXC 64
+#define CIC_G 8
+
+struct CicCands {
+    int n;
+    float inv_h[CIC_MAXC];  // 1 / h_c in position-code units
+};
+
+// the tile walk of walk_next with an integer gap threshold (codes)
+__device__ __forceinline__ bool walk_next_gap(Walk &w, int a, int NT, const uint2 *tile_u, uint2 ta, uint32_t reach,
+                                              int &b, int &d)
+{
+    for (;;) {
+        if (w.phase == 0) {
+            if (w.k >= NT) {
+                w.phase = 2;
+                return false;
+            }
+            const int bb = (a + w.k) % NT;
+            if (w.k == 0 || tile_gap(ta, tile_u[bb]) <= reach) {
+                b = bb;
+                d = w.k;
+                w.F = w.k;
+                ++w.k;
+                return true;
+            }
+            w.phase = 1;
+            w.k = 1;
+        } else if (w.phase == 1) {
+            if (w.k >= NT - w.F) {
+                w.phase = 2;
+                return false;
+            }
+            const int bb = ((a - w.k) % NT + NT) % NT;
+            if (tile_gap(ta, tile_u[bb]) <= reach) {
+                b = bb;
+                d = -w.k;
+                ++w.k;
+                return true;
+            }
+            w.phase = 2;
+            return false;
+        } else {
+            return false;
+        }
+    }
+}
+
+// per row tile: sums over ordered pairs i != j of B_1(d / h_c) and B_3(d / h_c)
+// (part[a][c] and part[a][n + c])
+__global__ void __launch_bounds__(CV_T)
+    cv_cic_kernel(const uint32_t *__restrict__ us, int64_t N, int NT, const uint2 *__restrict__ tile_u, uint32_t reach,
+                  CicCands cc, double *part)
+{
+    __shared__ uint32_t cu[CV_T];
+    __shared__ double wacc[CV_WARPS][2 * CIC_MAXC];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int a = blockIdx.x;
+    const int64_t i = (int64_t)a * CV_T + tid;
+    const bool rvalid = i < N;
+    const uint32_t ui = rvalid ? us[i] : 0u;
+    for (int c = tid; c < CV_WARPS * 2 * CIC_MAXC; c += CV_T) (&wacc[0][0])[c] = 0.0;
+    const uint2 ta = tile_u[a];
+    Walk w{0, 0, 0};
+    int b = 0, d = 0;
+    while (walk_next_gap(w, a, NT, tile_u, ta, reach, b, d)) {
+        if (!canonical_pair(a, b, NT)) continue;
+        const int64_t col0 = (int64_t)b * CV_T;
+        const int ncol = (int)(N - col0 < CV_T ? N - col0 : CV_T);
+        __syncthreads();  // the previous tile's readers are done
+        if (tid < ncol) cu[tid] = us[col0 + tid];
+        __syncthreads();
+        const bool diag = d == 0;
+        const float wgt = diag ? 1.0f : 2.0f;
+        for (int cg = 0; cg < cc.n; cg += CIC_G) {
+            float s1[CIC_G], s3[CIC_G];
+#pragma unroll
+            for (int k = 0; k < CIC_G; ++k) s1[k] = s3[k] = 0.f;
+            for (int q = 0; q < ncol; ++q) {
+                if (diag && q == tid) continue;
+                const uint32_t dd = cu[q] - ui;
+                const float dist = (float)(dd < 0x80000000u ? dd : 0u - dd);
+#pragma unroll
+                for (int k = 0; k < CIC_G; ++k) {
+                    const float t = dist * cc.inv_h[cg + k < cc.n ? cg + k : cc.n - 1];
+                    const float b1 = fmaxf(0.f, 1.f - t), b2 = fmaxf(0.f, 2.f - t);
+                    s1[k] += b1;
+                    s3[k] += (b2 * b2 * b2 - 4.f * b1 * b1 * b1) * (1.f / 6.f);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < CIC_G; ++k) {
+                float v1 = rvalid ? s1[k] : 0.f, v3 = rvalid ? s3[k] : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                    v3 += __shfl_xor_sync(0xffffffffu, v3, o);
+                }
+                if (lane == 0 && cg + k < cc.n) {
+                    wacc[warp][cg + k] += (double)wgt * (double)v1;
+                    wacc[warp][cc.n + cg + k] += (double)wgt * (double)v3;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < 2 * cc.n; c += CV_T) {
+        double s = 0.0;
+        for (int ww = 0; ww < CV_WARPS; ++ww) s += wacc[ww][c];
+        part[(size_t)a * 2 * cc.n + c] = s;
+    }
+}
+
+// CV_c = (n B_3(0) + S3_c) / (n^2 h_c) - 2 S1_c / (n (n - 1) h_c), x units; argmin
+// (smallest index on ties)
+__global__ void cic_combine_kernel(const double *tot, int n_cand, int64_t N, CandList hl, double *cv, int *argmin)
+{
+    if (threadIdx.x != 0) return;
+    const double n = (double)N;
+    for (int c = 0; c < n_cand; ++c) {
+        const double h = hl.k[c];
+        cv[c] = (n * (2.0 / 3.0) + tot[n_cand + c]) / (n * n * h) - 2.0 * tot[c] / (n * (n - 1.0) * h);
+    }
+    int best = 0;
+    for (int c = 1; c < n_cand; ++c)
+        if (cv[c] < cv[best]) best = c;
+    *argmin = best;
+}
+
+extern "C" kde_status kde_cv_cic(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *h_cand,
+                                 int32_t n_cand, double *cv_out, int32_t *argmin_out)
+{
+    if (!ctx) return KDE_EINVAL;
+    if (N < 2 || N > 0xFFFFFFFFll || !u || !(L > 0) || !h_cand || n_cand < 1 || n_cand > CIC_MAXC || !cv_out)
+        return kde_fail(ctx, KDE_EINVAL, "kde_cv_cic: need 2 <= N < 2^32, L > 0, 1 <= n_cand <= %d, non-null arrays",
+                        CIC_MAXC);
+    double hmax = 0.0;
+    CicCands cc{};
+    CandList hl{};
+    cc.n = hl.n = n_cand;
+    for (int c = 0; c < n_cand; ++c) {
+        if (!(h_cand[c] > 0 && 4.0 * h_cand[c] < L))
+            return kde_fail(ctx, KDE_EINVAL, "kde_cv_cic: candidate %d needs 0 < h < L/4", c);
+        hmax = h_cand[c] > hmax ? h_cand[c] : hmax;
+        cc.inv_h[c] = (float)(L / 4294967296.0 / h_cand[c]);
+        hl.k[c] = h_cand[c];
+    }
+    cudaSetDevice(ctx->device);
+    int nbins = 64;
+    while (nbins < 4096 && (int64_t)nbins * 16 < N) nbins <<= 1;
+    const int NT = (int)((N + CV_T - 1) / CV_T);
+    const int64_t Np = (int64_t)NT * CV_T;
+    uint32_t *us = (uint32_t *)kde_ws(ctx, WS_SORT_U, (size_t)Np * 4);
+    float2 *sc = (float2 *)kde_ws(ctx, WS_CV_SC, (size_t)Np * sizeof(float2));
+    uint2 *tile_u = (uint2 *)kde_ws(ctx, WS_CV_TILE, (size_t)NT * sizeof(uint2) + (size_t)NT * 4 + 64);
+    double *part = (double *)kde_ws(ctx, WS_CV_PART, (size_t)NT * 2 * n_cand * 8);
+    double *tot = (double *)kde_ws(ctx, WS_CV_TOT, (size_t)2 * n_cand * 8);
+    double *cvd = (double *)kde_ws(ctx, WS_CV_OUT, (size_t)n_cand * 8 + 64);
+    if (!us || !sc || !tile_u || !part || !tot || !cvd) return KDE_ENOMEM;
+    int *amin = (int *)(cvd + n_cand);
+    KDE_TRY(kde_sort_by_bin(ctx, u, N, nbins, us, nullptr, 0, nullptr));
+    int bin_shift = 32;
+    for (int nb = nbins; nb > 1; nb >>= 1) --bin_shift;
+    cv_prep_kernel<<<NT, CV_T, 0, ctx->stream>>>(us, nullptr, N, bin_shift, sc, tile_u, nullptr, nullptr, nullptr,
+                                                  CandList{}, nullptr, ctx->d_status);
+    KDE_LAUNCHED(ctx, "cv_prep_kernel");
+    const double reach_d = 2.0 * hmax / L * 4294967296.0;  // B_3 support in codes
+    const uint32_t reach = reach_d >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)ceil(reach_d);
+    {
+        KdeProfScope _ps(ctx, PROF_CV_PAIRS);
+        cv_cic_kernel<<<NT, CV_T, 0, ctx->stream>>>(us, N, NT, tile_u, reach, cc, part);
+    }
+    KDE_LAUNCHED(ctx, "cv_cic_kernel");
+    cv_reduce_kernel<<<2 * n_cand, 256, 0, ctx->stream>>>(part, NT, 2 * n_cand, tot);
+    KDE_LAUNCHED(ctx, "cv_reduce_kernel");
+    cic_combine_kernel<<<1, 32, 0, ctx->stream>>>(tot, n_cand, N, hl, cvd, amin);
+    KDE_LAUNCHED(ctx, "cic_combine_kernel");
+    KDE_CUDA(ctx, cudaMemcpyAsync(cv_out, cvd, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, ctx->stream), "cv copy");
+    int am = 0;
+    KDE_CUDA(ctx, cudaMemcpyAsync(&am, amin, 4, cudaMemcpyDeviceToHost, ctx->stream), "argmin copy");
+    KDE_TRY(kde_sync(ctx));
+    if (argmin_out) *argmin_out = am;
+    return KDE_OK;
+}
