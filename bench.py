@@ -678,14 +678,90 @@ def run_ensemble(args, rank, world, local_rank):
     ctx.close()
 
 
+def run_shapes(args, rank, world, local_rank):
+    """Shape comparison of Sec. IV (Fig. compare_high_order) on the GPU: the density
+    1 + 0.02 cos x on [0, 2 pi), N = 2^19 random particles, Ng = 512; MISE (probability-density
+    units, averaged over independent loads) and time per estimate for (a-d) B-spline shapes of
+    degree 1, 2, 3, 5 at width dx, (e) von Mises with sigma = 2 dx, (f) CIC with the CV width,
+    (g) von Mises with the CV width, (h) von Mises with Silverman widths around it."""
+    import torch
+
+    import kde_inputs as I
+    import paper_1804_11174_gb300 as kp
+    from paper_1804_11174_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = "cuda:%d" % local_rank
+    L, Ng, N, alpha = 2 * math.pi, 512, 1 << 19, 0.02
+    R = args.loads
+    dx = L / Ng
+    truth = 1.0 + alpha * np.cos(2 * math.pi * np.arange(Ng) / Ng)
+    ctx = kp.Context(local_rank)
+    kap_cand = I.log_candidates(1.0, 1e4, 64)
+    h_cand = dx * 2.0 ** (np.arange(28) / 4.0)  # dx .. 104 dx (the CV needs 4 h < L)
+    kap_e = 1.0 / (2 * dx) ** 2  # sigma = 2 dx (theta = x on [0, 2 pi))
+
+    def est(method, du):
+        if method.startswith("bspline"):
+            return ctx.deposit_bspline(du, Ng, L, int(method[-1]), dx), None
+        if method == "vm_2dx":
+            return ctx.deposit(du, Ng, L, kappa_uniform=kap_e), kap_e
+        if method == "cic_cv":
+            cv, am = ctx.cv_cic(du, L, h_cand)
+            return ctx.deposit_bspline(du, Ng, L, 1, float(h_cand[am])), float(h_cand[am])
+        _, am, loo = ctx.cv(du, L, kap_cand, spectral=True, want_loo=(method == "vm_adaptive"))
+        ks = float(kap_cand[am])
+        if method == "vm_cv":
+            return ctx.deposit(du, Ng, L, kappa_uniform=ks), ks
+        kap = ctx.adapt_widths(loo, L, ks, 0.5, 1.0, 1e6)
+        return ctx.deposit(du, Ng, L, kappa=kap), ks
+
+    methods = ["bspline1", "bspline2", "bspline3", "bspline5", "vm_2dx", "cic_cv", "vm_cv", "vm_adaptive"]
+    paper = {"bspline1": 2.28031e-3, "bspline2": 1.90144e-3, "bspline3": 1.14667e-3, "bspline5": 0.74505e-3,
+             "vm_2dx": 0.43698e-3, "cic_cv": 0.17233e-3, "vm_cv": 0.15423e-3, "vm_adaptive": 0.13063e-3}
+    loads = [torch.from_numpy(I.to_fixed(I.random_positions(r, N, L, alpha), L).view(np.int32)).to(dev)
+             for r in range(R)]
+    for m in methods:  # warm-up (tables, workspace)
+        est(m, loads[0])
+    torch.cuda.synchronize()
+    table = {}
+    for m in methods:
+        mise, widths, ms = [], [], []
+        for du in loads:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rho, w = est(m, du)
+            torch.cuda.synchronize()
+            ms.append(1e3 * (time.perf_counter() - t0))
+            d = rho.double().cpu().numpy() - truth
+            mise.append(float(np.sum(d * d) * dx) / L ** 2)  # density -> probability density: / L
+            widths.append(w)
+        table[m] = {"mise_pdf": float(np.mean(mise)), "mise_sd": float(np.std(mise, ddof=1)),
+                    "ms_per_estimate": float(np.median(ms)), "paper_mise": paper[m],
+                    "width": None if widths[0] is None else float(np.median(widths))}
+    t_cic = table["bspline1"]["ms_per_estimate"]
+    line = {"metric": METRIC, "value": N * Ng / (t_cic * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": R,
+            "warmup": 1, "ms_per_step": t_cic, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "shape comparison: 1 + 0.02 cos x on [0, 2pi), N = 2^19 random, Ng = 512, "
+                                   "%d independent loads" % R},
+            "mise": table,
+            "note": "MISE in probability-density units (density / 2pi), averaged over the loads; width = kappa "
+                    "(von Mises) or h (CIC, x units); paper_mise is the paper's single-run value, context only"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep", "serve", "ensemble"])
+    ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep", "serve", "ensemble", "shapes"])
     ap.add_argument("--realisations", type=int, default=256, help="ensemble: realisations")
+    ap.add_argument("--loads", type=int, default=8, help="shapes: independent particle loads")
     ap.add_argument("--requests", type=int, default=1000, help="serving: requests in the sample")
     ap.add_argument("--slots", type=int, default=8, help="serving: slots of the batched server")
     ap.add_argument("--cv", default="pairs", choices=["pairs", "spectral"],
@@ -702,6 +778,8 @@ def main():
         run_serve(args, rank, world, local_rank)
     elif args.workload == "ensemble":
         run_ensemble(args, rank, world, local_rank)
+    elif args.workload == "shapes":
+        run_shapes(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
