@@ -71,6 +71,7 @@ def _load():
                 "or_deposit_bspline": (None, [_P, _I64, _I, _D, _I, _D, _P]),
                 "or_gather_bspline": (None, [_P, _I64, _I, _D, _P, _I, _D, _P]),
                 "or_cv_cic": (_D, [_P, _I64, _D, _D]),
+                "or_pic_run_bspline": (_I, [_P, _P, _I64, _I, _D, _I, _D, _D, _D, _D, _D, _I, _I, _P]),
                 "or_ad_cdf_of_position": (_D, [_D, _D]),
                 "or_ad_cdf": (_D, [_D, _I64]),
                 "or_ad_pvalue": (_D, [_D, _I64]),
@@ -354,3 +355,16 @@ def cv_cic(x, L: float, h: float) -> float:
     """CV of the first-order (CIC) shape of width h (x units)."""
     x = _f64(x)
     return _load().or_cv_cic(_ptr(x), x.size, float(L), float(h))
+
+
+def pic_run_bspline(x, v, L: float, Ng: int, dt: float, nsteps: int, order: int = 1, h: float = 0.0,
+                    qm: float = -1.0, charge: float = -1.0, background: float = 1.0, backstep: bool = True):
+    """Standard PIC run with the B-spline shape of degree `order` and width h (0: dx); spectral
+    Poisson; returns dict with x, v and the field energy W[n]."""
+    x = _f64(x).copy()
+    v = _f64(v).copy()
+    h = h if h > 0 else L / Ng
+    W = np.empty(nsteps, dtype=np.float64)
+    _load().or_pic_run_bspline(_ptr(x), _ptr(v), x.size, int(order), float(h), int(Ng), float(L), float(dt),
+                               float(qm), float(charge), float(background), int(nsteps), int(backstep), _ptr(W))
+    return {"x": x, "v": v, "energy": W}

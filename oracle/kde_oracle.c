@@ -716,6 +716,27 @@ double or_cv_cic(const double *x, int64_t N, double L, double h)
     return s3 / (n * n) - 2.0 * s1 / (n * (n - 1.0));
 }
 
+/* Standard PIC cycle (the baseline of Sec. III.B's ensemble comparison): the  */
+/* step of or_pic_run with the B-spline shape of degree p and width h in place  */
+/* of the von Mises kernel, spectral Poisson, the same leap-frog push.           */
+int or_pic_run_bspline(double *x, double *v, int64_t N, int p, double h, int Ng, double L, double dt, double qm,
+                       double charge, double background, int nsteps, int backstep, double *W_out)
+{
+    double *rho = (double *)malloc(sizeof(double) * (size_t)Ng);
+    double *E = (double *)malloc(sizeof(double) * (size_t)Ng);
+    double *Ei = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int n = 0; n < nsteps; ++n) {
+        or_deposit_bspline(x, N, p, h, Ng, L, rho);
+        for (int g = 0; g < Ng; ++g) rho[g] = background + charge * rho[g];
+        or_poisson_spectral(rho, Ng, L, E);
+        if (W_out) W_out[n] = or_field_energy(E, Ng, L);
+        or_gather_bspline(x, N, p, h, E, Ng, L, Ei);
+        or_push(x, v, Ei, N, L, dt, qm, (n == 0 && backstep) ? 0.5 : 1.0);
+    }
+    free(rho); free(E); free(Ei);
+    return 0;
+}
+
 /* Sec. III.B: damping rate from the field energy.  The slope of ln W through
  * the first two strict local maxima after t = 0 (steps n >= 1) is the energy
  * decay rate; the amplitude rate gamma is half of it.  Returns 0 and sets

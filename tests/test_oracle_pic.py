@@ -113,3 +113,28 @@ def test_damping_fit_on_synthetic_energy(oracle):
     g, p1, p2 = oracle.damping_rate(W, dt)
     assert g == pytest.approx(-0.15, abs=0.01)
     assert p2 > p1 >= 1
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_cold_langmuir_frequency_standard_shapes(oracle, order):
+    # The standard deposit and gather each multiply mode k by the B-spline's transform
+    # S(k) = sinc(k dx / 2)^(order + 1), so omega = (2/dt) asin(dt S(k) / 2) as for the
+    # von Mises kernel with A_1 replaced by S(k).
+    L, Ng, dt = 4 * math.pi, 32, 0.1
+    u, v = I.langmuir_load(4096, L, 0.01)
+    r = oracle.pic_run_bspline(I.from_fixed(u, L), v, L, Ng, dt, 200, order=order)
+    W = r["energy"]
+    t = dt * np.arange(W.size)
+    k, dx = 2 * math.pi / L, L / Ng
+    S = (math.sin(k * dx / 2) / (k * dx / 2)) ** (order + 1)
+    w_th = (2 / dt) * math.asin(dt * S / 2)
+    p, _ = so.curve_fit(lambda t, a, w: a * np.cos(w * t) ** 2, t, W, p0=[W[0], w_th])
+    assert p[1] == pytest.approx(w_th, rel=2e-4)
+    assert abs(w_th - (2 / dt) * math.asin(dt / 2)) > 5e-4  # the shape factor is resolved
+
+
+def test_standard_pic_conserves_momentum(oracle):
+    L, Ng, dt = 4 * math.pi, 64, 0.1
+    u, v = I.landau_load(5, 2048, L, 0.05, 1.0)
+    r = oracle.pic_run_bspline(I.from_fixed(u, L), v, L, Ng, dt, 20, order=1)
+    assert abs(r["v"].sum() - v.sum()) <= 1e-10 * np.abs(v).sum()
