@@ -753,13 +753,149 @@ def run_shapes(args, rank, world, local_rank):
     ctx.close()
 
 
+def landau_theory(vth, k=1.0, factor=1.0):
+    """Damping rate (Im omega) of the kinetic Langmuir root, 1 + F^2/(k v_th)^2 (1 + z Z(z)) = 0,
+    z = omega/(sqrt 2 k v_th), with the deposit/gather smoothing factor F of mode k (1: none)."""
+    import scipy.special as sp
+    a2 = (factor / (k * vth)) ** 2
+
+    def D(w):
+        z = w / (math.sqrt(2.0) * k * vth)
+        return 1.0 + a2 * (1.0 + z * 1j * math.sqrt(math.pi) * sp.wofz(z))
+
+    # Newton's method on D from Bohm-Gross estimates with several damping guesses; the least
+    # damped root that converges is the Landau root
+    best = None
+    with np.errstate(all="ignore"):
+        for gi in (0.01, 0.1, 0.3, 0.6):
+            w = complex(math.sqrt(factor ** 2 + 3.0 * (k * vth) ** 2), -gi)
+            for _ in range(200):
+                h = 1e-7
+                dD = (D(w + h) - D(w - h)) / (2 * h)
+                if not np.isfinite(dD) or dD == 0:
+                    break
+                dw = D(w) / dD
+                w -= dw
+                if abs(dw) < 1e-13:
+                    break
+            if np.isfinite(w) and abs(D(w)) < 1e-9 and w.real > 0 and (best is None or w.imag > best.imag):
+                best = w
+    return best.imag if best is not None else float("nan")
+
+
+def run_landau_stats(args, rank, world, local_rank):
+    """Ensemble statistics of Sec. III.B on the GPU: Landau damping with k = 1 (L = 2 pi),
+    perturbation 0.02 cos x, N = 2^15, Ng = 256, dt = 0.01, 1500 steps, for thermal velocities
+    0.20 .. 0.45; for each, the same 30 loads (common random numbers) advanced by standard PIC
+    (CIC) and by the von Mises KDE (width by CV at t = 0, and sigma = 2 dx), each arm one
+    ensemble with one captured graph per step; per load the amplitude damping rate from the
+    first two peaks of ln W; mean error against the kinetic root (plain, and with the arm's
+    own smoothing of mode 1), t statistics, and the paired CRN comparison."""
+    import scipy.special as sps
+    import torch
+
+    import kde_inputs as I
+    import paper_1804_11174_gb300 as kp
+    from paper_1804_11174_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = "cuda:%d" % local_rank
+    L, Ng, N, dt, steps, R = 2 * math.pi, 256, 1 << 15, 0.01, args.stat_steps, args.ens_size
+    dx = L / Ng
+    ctx = kp.Context(local_rank)
+    cand = I.log_candidates(1.0, 1e3, 16)
+    kap_2dx = 1.0 / (2 * dx) ** 2
+    cic_factor = (math.sin(dx / 2) / (dx / 2)) ** 2
+    out = {}
+    t_total = 0.0
+    for vth in (0.20, 0.25, 0.30, 0.35, 0.40, 0.45):
+        loads = [I.landau_load(1000 * int(round(vth * 100)) + r, N, L, 0.02, vth) for r in range(R)]
+        u0 = np.concatenate([a for a, _ in loads])
+        v0 = np.concatenate([b.astype(np.float32) for _, b in loads])
+        kcv = []
+        for a, _ in loads:
+            _, am, _ = ctx.cv(torch.from_numpy(a.view(np.int32)).to(dev), L, cand, spectral=True)
+            kcv.append(float(cand[am]))
+        arms = {"pic_cic": (0, [kap_2dx] * R, [cic_factor] * R),
+                "kde_cv_width": (None, kcv, [float(sps.ive(1, k) / sps.ive(0, k)) for k in kcv]),
+                "kde_sigma_2dx": (None, [kap_2dx] * R, [float(sps.ive(1, kap_2dx) / sps.ive(0, kap_2dx))] * R)}
+        g_plain = landau_theory(vth)
+        res = {"theory_plain": g_plain}
+        rates = {}
+        for name, (shape, kaps, fac) in arms.items():
+            du = torch.from_numpy(u0.view(np.int32)).to(dev)
+            dv = torch.from_numpy(v0).to(dev)
+            ens = kp.Ensemble(ctx, [N] * R, [Ng] * R, kaps, L, dt, du, dv)
+            if shape == 0:
+                ens.set_shape(1)
+            en = torch.zeros(R * steps, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ens.run(steps, en, use_graph=True)
+            torch.cuda.synchronize()
+            t_total += time.perf_counter() - t0
+            W = en.cpu().numpy().reshape(R, steps)
+            ens.close()
+            g = []
+            for r in range(R):
+                try:
+                    g.append(kp.damping_rate(W[r], dt))
+                except kp.KdeError:
+                    g.append(float("nan"))
+            g = np.array(g)
+            ok = np.isfinite(g)
+            gs = np.array([landau_theory(vth, factor=f) for f in fac])
+            ok_own = ok & np.isfinite(gs)
+            e_plain, e_own = g - g_plain, g - gs
+            n_ok = int(ok.sum())
+
+            def tstat(e):
+                m = np.isfinite(e)
+                n = int(m.sum())
+                if n < 2:
+                    return None, None, None
+                sd = float(np.std(e[m], ddof=1))
+                return float(np.mean(e[m])), sd, float(np.mean(e[m]) / (sd / math.sqrt(n)))
+
+            m1, s1, t1 = tstat(e_plain)
+            m2, s2, t2 = tstat(np.where(ok_own, e_own, np.nan)) if ok_own.sum() > 1 else (None, None, None)
+            rates[name] = g
+            res[name] = {"mean_rate": float(np.mean(g[ok])), "sd_rate": s1, "loads_with_two_peaks": n_ok,
+                         "error_vs_plain_theory": m1, "t_vs_plain_theory": t1,
+                         "theory_with_own_smoothing_mean": float(np.nanmean(gs)) if np.isfinite(gs).any() else None,
+                         "error_vs_own_theory": m2, "t_vs_own_theory": t2,
+                         "kappa_median": float(np.median(kaps)) if shape is None else None}
+        # paired (common random numbers): the CIC arm's absolute error minus the KDE arm's, per load
+        for kde in ("kde_cv_width", "kde_sigma_2dx"):
+            d = np.abs(rates["pic_cic"] - g_plain) - np.abs(rates[kde] - g_plain)
+            ok = np.isfinite(d)
+            sd = float(np.std(d[ok], ddof=1))
+            res["paired_abs_error_pic_minus_" + kde] = {"mean": float(np.mean(d[ok])), "sd": sd,
+                                                        "t": float(np.mean(d[ok]) / (sd / math.sqrt(ok.sum())))}
+        out["%.2f" % vth] = res
+    particle_steps = 6 * 3 * R * N * steps
+    line = {"metric": METRIC, "value": particle_steps / t_total, "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * t_total / (6 * 3 * steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Landau ensemble statistics: k = 1, 0.02 cos x, N = 2^15, Ng = 256, dt = 0.01, "
+                                   "%d steps, %d common-random-number loads per v_th, v_th 0.20..0.45; arms: CIC "
+                                   "standard PIC, von Mises at the CV width, von Mises at sigma = 2 dx" % (steps, R)},
+            "by_vth": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep", "serve", "ensemble", "shapes"])
+    ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep", "serve", "ensemble", "shapes",
+                                                            "landau_stats"])
+    ap.add_argument("--ens-size", type=int, default=30, help="landau_stats: loads per thermal velocity")
+    ap.add_argument("--stat-steps", type=int, default=1500, help="landau_stats: PIC steps per run")
     ap.add_argument("--realisations", type=int, default=256, help="ensemble: realisations")
     ap.add_argument("--loads", type=int, default=8, help="shapes: independent particle loads")
     ap.add_argument("--requests", type=int, default=1000, help="serving: requests in the sample")
@@ -780,6 +916,8 @@ def main():
         run_ensemble(args, rank, world, local_rank)
     elif args.workload == "shapes":
         run_shapes(args, rank, world, local_rank)
+    elif args.workload == "landau_stats":
+        run_landau_stats(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -258,6 +258,12 @@ typedef struct pic_state {
     double h_target;      /* state, in/out: target h of the last optimisation; 0 = none yet */
     int64_t n_opt;        /* state, in/out: optimisations so far */
     double *ad_log_p;     /* device float64[steps] ln p-value per step (indexed by step), or NULL */
+    /* Standard PIC instead of the KDE deposit/gather (the baseline of the ensemble
+     * comparison in Sec. III.B): shape_order 1 (CIC), 2, 3 or 5 selects the B-spline
+     * shape of that degree and width shape_h (x units; 0 = dx) for the deposit and the
+     * gather; FP32, no width schedule; particles are not reordered.  0 = von Mises. */
+    int32_t shape_order;
+    double shape_h;
 } pic_state;
 
 #define PIC_NO_BACKSTEP 0x100u /* do not halve the first kick at step 0 */
@@ -300,6 +306,10 @@ kde_status kde_ensemble_create(kde_ctx *ctx, kde_ensemble **out, int32_t R, cons
                                const double *kappa, double L, double dt, uint32_t *u, float *v);
 /* New uniform widths (HOST, R entries); a captured step is captured again. */
 kde_status kde_ensemble_set_widths(kde_ensemble *ens, const double *kappa);
+/* Standard PIC for every realisation (pic_state.shape_order / shape_h: B-spline of
+ * degree order in {1, 2, 3, 5}, width h, 0 = dx), or order 0 for the von Mises KDE
+ * step; a captured step is captured again. */
+kde_status kde_ensemble_set_shape(kde_ensemble *ens, int32_t order, double h);
 /* Integrated squared error of each realisation's deposited density against
  * 1 + alpha cos(2 pi mode x / L) at the current positions (one sample of the
  * MISE of Sec. II.B): mise (device float64[R]) = dx sum_g (rho_g - truth_g)^2. */

@@ -55,7 +55,7 @@ class _PicState(ctypes.Structure):
         ("alpha", _D), ("kappa_min", _D), ("kappa_max", _D),
         ("energy", _P), ("kappa_star", _P), ("step", _I64), ("flags", _U32),
         ("width_ad", _I32), ("ad_threshold", _D), ("adjust_rate", _D), ("ad_log_pth", _D), ("h_target", _D),
-        ("n_opt", _I64), ("ad_log_p", _P),
+        ("n_opt", _I64), ("ad_log_p", _P), ("shape_order", _I32), ("shape_h", _D),
     ]
 
 
@@ -101,6 +101,7 @@ def load_library(path: str | None = None):
         "kde_cv_cic": (S, [_P, _P, _I64, _D, _P, _I32, _P, _P]),
         "kde_ensemble_create": (S, [_P, ctypes.POINTER(_P), _I32, _P, _P, _P, _D, _D, _P, _P]),
         "kde_ensemble_set_widths": (S, [_P, _P]),
+        "kde_ensemble_set_shape": (S, [_P, _I32, _D]),
         "kde_ensemble_mise": (S, [_P, _D, _I32, _P]),
         "kde_ensemble_run": (S, [_P, _I32, _P, _I32]),
         "kde_ensemble_destroy": (S, [_P]),
@@ -357,7 +358,8 @@ class PicState:
                  qm: float = -1.0, charge: float = -1.0, background: float = 1.0, width_every: int = 0,
                  cand=None, alpha: float = 0.5, kappa_min: float = 0.0, kappa_max: float = 1e6,
                  max_steps: int = 0, fd: bool = False, backstep: bool = True, cv_spectral: bool = False,
-                 width_ad: bool = False, ad_threshold: float = 0.01, adjust_rate: float = 0.05):
+                 width_ad: bool = False, ad_threshold: float = 0.01, adjust_rate: float = 0.05,
+                 shape_order: int = 0, shape_h: float = 0.0):
         torch = _torch()
         self.u, self.v, self.kappa, self.id = u, v, kappa, ids
         f64 = v.dtype == torch.float64
@@ -382,6 +384,7 @@ class PicState:
         c.width_ad = int(bool(width_ad))
         c.ad_threshold, c.adjust_rate = float(ad_threshold), float(adjust_rate)
         c.ad_log_pth, c.h_target, c.n_opt = 0.0, 0.0, 0
+        c.shape_order, c.shape_h = int(shape_order), float(shape_h)
         self.c = c
 
     def _sync_in(self):
@@ -424,6 +427,10 @@ class Ensemble:
     def set_widths(self, kappa):
         k = np.ascontiguousarray(kappa, dtype=np.float64)
         self.ctx._check("kde_ensemble_set_widths", self.ctx.lib.kde_ensemble_set_widths(self.h, k.ctypes.data))
+
+    def set_shape(self, order: int, h: float = 0.0):
+        """Standard PIC with the B-spline shape of degree `order` (0: back to the von Mises KDE)."""
+        self.ctx._check("kde_ensemble_set_shape", self.ctx.lib.kde_ensemble_set_shape(self.h, int(order), float(h)))
 
     def mise(self, alpha: float, mode: int = 1):
         torch = _torch()

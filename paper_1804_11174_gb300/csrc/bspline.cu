@@ -183,3 +183,85 @@ extern "C" kde_status kde_gather_bspline(kde_ctx *ctx, const uint32_t *u, int64_
     KDE_LAUNCHED(ctx, "bsp_gather_kernel");
     return KDE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Standard-PIC step pieces for pic_step (shape_order > 0): deposit straight
+// into the step's int64 accumulators, and gather + leap-frog push in place
+// (no reordering: the shapes need no sorted order).
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(BSP_THREADS)
+    bsp_gather_push_kernel(uint32_t *u, float *v, int64_t N, int Ng, float r, int W, const float *__restrict__ field,
+                           float kick_qm_dt, float dt_scale)
+{
+    extern __shared__ float sf[];
+    for (int g = threadIdx.x; g < Ng; g += BSP_THREADS) sf[g] = field[g];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * BSP_THREADS + threadIdx.x; i < N; i += (int64_t)gridDim.x * BSP_THREADS) {
+        const uint32_t ui = u[i];
+        const uint64_t q = (uint64_t)ui * (uint64_t)Ng;
+        const int cell = (int)(q >> 32);
+        const float frac = (float)(uint32_t)q * (1.0f / 4294967296.0f);
+        float e = 0.f;
+        for (int k = -W; k <= W; ++k) {
+            const float b = bsp_eval<P>(((float)k - frac) * r);
+            int g = (cell + k) % Ng;
+            g = g < 0 ? g + Ng : g;
+            e = fmaf(b, sf[g], e);
+        }
+        const float vn = v[i] + kick_qm_dt * (e * r);
+        v[i] = vn;
+        // u += rint(v dt / L 2^32) modulo 2^32 (periodic wrap for free)
+        float d = vn * dt_scale;
+        if (!(fabsf(d) < 2147483520.0f)) d = fmodf(d, 4294967296.0f);
+        u[i] = ui + (uint32_t)(long long)__float2ll_rn(d);
+    }
+}
+
+kde_status kde_bspline_deposit_acc(kde_ctx *ctx, const uint32_t *u, int64_t N, int order, double h, int Ng, double L,
+                                   long long *acc, double *bound_out)
+{
+    const double dx = L / Ng;
+    const float r = (float)(dx / h);
+    const int W = bsp_window(order, h, dx);
+    const double wcoef = (L / (double)N) / h;
+    const double bound = (double)N * wcoef * bsp_peak(order) * 1.0000001;
+    const double scale = kde_acc_scale(bound);
+    *bound_out = bound;
+    KDE_CUDA(ctx, cudaMemsetAsync(acc, 0, (size_t)Ng * 8, ctx->stream), "bspline acc memset");
+    const int grid = bsp_grid(ctx, N);
+    const size_t smem = (size_t)Ng * 8;
+    {
+        KdeProfScope _ps(ctx, PROF_DEPOSIT);
+        switch (order) {
+        case 1: bsp_deposit_kernel<1><<<grid, BSP_THREADS, smem, ctx->stream>>>(u, N, Ng, r, W, (float)wcoef, scale, acc); break;
+        case 2: bsp_deposit_kernel<2><<<grid, BSP_THREADS, smem, ctx->stream>>>(u, N, Ng, r, W, (float)wcoef, scale, acc); break;
+        case 3: bsp_deposit_kernel<3><<<grid, BSP_THREADS, smem, ctx->stream>>>(u, N, Ng, r, W, (float)wcoef, scale, acc); break;
+        default: bsp_deposit_kernel<5><<<grid, BSP_THREADS, smem, ctx->stream>>>(u, N, Ng, r, W, (float)wcoef, scale, acc); break;
+        }
+    }
+    KDE_LAUNCHED(ctx, "bsp_deposit_kernel");
+    return KDE_OK;
+}
+
+kde_status kde_bspline_gather_push(kde_ctx *ctx, uint32_t *u, float *v, int64_t N, int order, double h, int Ng,
+                                   double L, const float *E, double kick_qm_dt, double dt_scale)
+{
+    const double dx = L / Ng;
+    const float r = (float)(dx / h);
+    const int W = bsp_window(order, h, dx);
+    const int grid = bsp_grid(ctx, N);
+    const size_t smem = (size_t)Ng * 4;
+    const float kq = (float)kick_qm_dt, ds = (float)dt_scale;
+    {
+        KdeProfScope _ps(ctx, PROF_GATHER);
+        switch (order) {
+        case 1: bsp_gather_push_kernel<1><<<grid, BSP_THREADS, smem, ctx->stream>>>(u, v, N, Ng, r, W, E, kq, ds); break;
+        case 2: bsp_gather_push_kernel<2><<<grid, BSP_THREADS, smem, ctx->stream>>>(u, v, N, Ng, r, W, E, kq, ds); break;
+        case 3: bsp_gather_push_kernel<3><<<grid, BSP_THREADS, smem, ctx->stream>>>(u, v, N, Ng, r, W, E, kq, ds); break;
+        default: bsp_gather_push_kernel<5><<<grid, BSP_THREADS, smem, ctx->stream>>>(u, v, N, Ng, r, W, E, kq, ds); break;
+        }
+    }
+    KDE_LAUNCHED(ctx, "bsp_gather_push_kernel");
+    return KDE_OK;
+}

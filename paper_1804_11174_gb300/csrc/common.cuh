@@ -291,6 +291,13 @@ struct SortPayload {
 };
 kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, uint32_t *u_out,
                            const SortPayload *pl, int npl, uint32_t *perm_out);
+// standard-PIC shapes inside pic_step: deposit of the B-spline shape (degree
+// order, width h) into int64 accumulators acc[Ng] (zeroed here; *bound_out = the
+// largest possible node value), and gather + leap-frog push in place
+kde_status kde_bspline_deposit_acc(kde_ctx *ctx, const uint32_t *u, int64_t N, int order, double h, int Ng, double L,
+                                   long long *acc, double *bound_out);
+kde_status kde_bspline_gather_push(kde_ctx *ctx, uint32_t *u, float *v, int64_t N, int order, double h, int Ng,
+                                   double L, const float *E, double kick_qm_dt, double dt_scale);
 // ascending sort of N 32-bit codes (LSD radix, four stable 8-bit passes);
 // tmp: N-element scratch; u may alias neither out nor tmp
 kde_status kde_radix_sort_u32(kde_ctx *ctx, const uint32_t *u, int64_t N, uint32_t *out, uint32_t *tmp);

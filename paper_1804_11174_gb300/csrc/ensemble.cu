@@ -199,6 +199,24 @@ extern "C" kde_status kde_ensemble_set_widths(kde_ensemble *e, const double *kap
     return KDE_OK;
 }
 
+extern "C" kde_status kde_ensemble_set_shape(kde_ensemble *e, int32_t order, double h)
+{
+    if (!e) return KDE_EINVAL;
+    if (!(order == 0 || order == 1 || order == 2 || order == 3 || order == 5) || h < 0)
+        return kde_fail(e->ctx, KDE_EINVAL, "kde_ensemble_set_shape: order in {0, 1, 2, 3, 5}, h >= 0");
+    for (int r = 0; r < e->R; ++r) {
+        e->ps[r].shape_order = order;
+        e->ps[r].shape_h = h;
+    }
+    if (e->graph) {
+        cudaSetDevice(e->ctx->device);
+        cudaStreamSynchronize(e->stream);
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    return KDE_OK;
+}
+
 extern "C" kde_status kde_ensemble_mise(kde_ensemble *e, double alpha, int32_t mode, double *mise)
 {
     if (!e || !mise) return KDE_EINVAL;

@@ -25,6 +25,32 @@ __global__ void norm_from_kappa_kernel(const T *kappa, int64_t N, T *norm, unsig
     norm[i] = (T)kde_norm(k);
 }
 
+// standard PIC with a B-spline shape: deposit, Poisson, energy, gather + push
+static kde_status pic_run_bspline(kde_ctx *ctx, pic_state *st, int n_steps)
+{
+    const int64_t N = st->N;
+    const int Ng = st->Ng;
+    const double L = st->L;
+    const double h = st->shape_h > 0 ? st->shape_h : L / Ng;
+    const bool fd = (st->flags & KDE_POISSON_FD) != 0;
+    long long *acc = (long long *)kde_ws(ctx, WS_ACC, (size_t)Ng * 8);
+    float *E = (float *)kde_ws(ctx, WS_GRID0, (size_t)Ng * sizeof(float));
+    if (!acc || !E) return KDE_ENOMEM;
+    for (int s = 0; s < n_steps; ++s) {
+        const int64_t step = st->step;
+        double bound = 0.0;
+        KDE_TRY(kde_bspline_deposit_acc(ctx, st->u, N, st->shape_order, h, Ng, L, acc, &bound));
+        KDE_TRY(kde_poisson_impl<float>(ctx, nullptr, acc, 1.0 / kde_acc_scale(bound), Ng, L, st->charge,
+                                        st->background, fd, E));
+        if (st->energy) KDE_TRY(kde_energy_impl<float>(ctx, E, Ng, L, st->energy + step));
+        const double kick = (step == 0 && !(st->flags & PIC_NO_BACKSTEP)) ? 0.5 : 1.0;
+        KDE_TRY(kde_bspline_gather_push(ctx, st->u, (float *)st->v, N, st->shape_order, h, Ng, L, E,
+                                        kick * st->qm * st->dt, st->dt * 4294967296.0 / L));
+        st->step = step + 1;
+    }
+    return KDE_OK;
+}
+
 template <typename T>
 static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
 {
@@ -180,7 +206,7 @@ extern "C" kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps)
     }
     if (st->kappa && !st->kappa_norm)
         return kde_fail(ctx, KDE_EINVAL, "pic_step: per-particle widths need the kappa_norm array");
-    if (!st->kappa && !(st->kappa_uniform > 0 && st->kappa_uniform <= KDE_KAPPA_MAX))
+    if (!st->kappa && st->shape_order == 0 && !(st->kappa_uniform > 0 && st->kappa_uniform <= KDE_KAPPA_MAX))
         return kde_fail(ctx, KDE_EINVAL, "pic_step: kappa_uniform must be in (0, 1e6]");
     if (!st->width_ad && st->width_every > 0 && st->n_cand > 0) {
         if (!st->kappa || !st->cand || st->n_cand > 256 || st->N < 2 || !(st->alpha >= 0) ||
@@ -191,6 +217,17 @@ extern "C" kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps)
         for (int c = 0; c < st->n_cand; ++c)
             if (!(st->cand[c] > 0 && st->cand[c] <= KDE_KAPPA_MAX))
                 return kde_fail(ctx, KDE_EINVAL, "pic_step: candidate %d outside (0, 1e6]", c);
+    }
+    if (st->shape_order != 0) {
+        const double h = st->shape_h > 0 ? st->shape_h : st->L / st->Ng;
+        if (!(st->shape_order == 1 || st->shape_order == 2 || st->shape_order == 3 || st->shape_order == 5) ||
+            !((st->shape_order + 1) * h < st->L) || st->shape_h < 0 || (st->flags & KDE_F64) || st->kappa ||
+            st->width_ad || (st->width_every > 0 && st->n_cand > 0))
+            return kde_fail(ctx, KDE_EINVAL,
+                            "pic_step: a B-spline shape needs order in {1, 2, 3, 5}, 0 < (order+1) h < L, FP32, "
+                            "no particle-wise widths and no width schedule");
+        cudaSetDevice(ctx->device);
+        return pic_run_bspline(ctx, st, n_steps);
     }
     cudaSetDevice(ctx->device);
     if (st->flags & KDE_F64) return pic_run<double>(ctx, st, n_steps);

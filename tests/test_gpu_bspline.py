@@ -88,3 +88,70 @@ def test_bspline_rejects_bad_arguments(ctx, kp):
         ctx.deposit_bspline(u, 64, L, 1, L)  # (order + 1) h >= L
     with pytest.raises(kp.KdeError):
         ctx.cv_cic(u, L, [L / 2])  # h >= L/4
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_standard_pic_step_matches_oracle(ctx, kp, oracle, order):
+    Lp, Ng, dt, N, steps = 4 * math.pi, 64, 0.1, 4096, 3
+    u, v = I.landau_load(11, N, Lp, 0.05, 1.0)
+    v32 = v.astype(np.float32)
+    st = kp.PicState(to_dev_u(u), to_dev(v32), Lp, Ng, dt, max_steps=steps, shape_order=order)
+    ctx.pic_step(st, steps)
+    ctx.sync()
+    r = oracle.pic_run_bspline(I.from_fixed(u, Lp), v32, Lp, Ng, dt, steps, order=order)
+    np.testing.assert_allclose(st.energy.cpu().numpy()[:steps], r["energy"], rtol=1e-5)
+    x = I.from_fixed(st.u.cpu().numpy().view(np.uint32), Lp)
+    dxp = np.abs((x - r["x"] + Lp / 2) % Lp - Lp / 2)
+    assert dxp.max() <= 1e-6 * Lp
+    assert rel_l2(st.v.cpu().numpy(), r["v"]) <= 1e-5
+
+
+def test_standard_pic_cold_langmuir_frequency(ctx, kp):
+    import scipy.optimize as so
+    Lp, Ng, dt = 4 * math.pi, 32, 0.1
+    u, v = I.langmuir_load(4096, Lp, 0.01)
+    st = kp.PicState(to_dev_u(u), to_dev(v.astype(np.float32)), Lp, Ng, dt, max_steps=200, shape_order=1)
+    ctx.pic_step(st, 200)
+    ctx.sync()
+    W = st.energy.cpu().numpy()
+    t = dt * np.arange(W.size)
+    k, dx = 2 * math.pi / Lp, Lp / Ng
+    w_th = (2 / dt) * math.asin(dt * (math.sin(k * dx / 2) / (k * dx / 2)) ** 2 / 2)
+    p, _ = so.curve_fit(lambda t, a, w: a * np.cos(w * t) ** 2, t, W, p0=[W[0], w_th])
+    assert p[1] == pytest.approx(w_th, rel=5e-4)
+
+
+def test_ensemble_standard_pic_equals_pic_step(ctx, kp):
+    Lp = 4 * math.pi
+    Ns, Ngs = [3000, 5000, 2048], [64, 128, 100]
+    us, vs = [], []
+    for r, N in enumerate(Ns):
+        u, v = I.landau_load(50 + r, N, Lp, 0.05, 1.0)
+        us.append(u)
+        vs.append(v.astype(np.float32))
+    du = to_dev_u(np.concatenate(us))
+    dv = to_dev(np.concatenate(vs))
+    ens = kp.Ensemble(ctx, Ns, Ngs, [30.0] * 3, Lp, 0.1, du, dv)
+    ens.set_shape(1)
+    en = torch.zeros(3 * 5, dtype=torch.float64, device="cuda:0")
+    ens.run(5, en, use_graph=True)
+    ctx.sync()
+    en = en.cpu().numpy().reshape(3, 5)
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    for r in range(3):
+        st = kp.PicState(to_dev_u(us[r]), to_dev(vs[r]), Lp, Ngs[r], 0.1, max_steps=5, shape_order=1)
+        ctx.pic_step(st, 5)
+        ctx.sync()
+        np.testing.assert_array_equal(en[r], st.energy.cpu().numpy())
+        assert torch.equal(du[off[r]:off[r + 1]], st.u) and torch.equal(dv[off[r]:off[r + 1]], st.v)
+    ens.close()
+
+
+def test_standard_pic_rejects_bad_states(ctx, kp):
+    u, v = I.landau_load(1, 1000, L, 0.05, 1.0)
+    bad = kp.PicState(to_dev_u(u), to_dev(v, torch.float64), L, 64, 0.1, max_steps=2, shape_order=1)
+    with pytest.raises(kp.KdeError):
+        ctx.pic_step(bad, 1)  # FP64 is not offered for the B-spline shapes
+    bad = kp.PicState(to_dev_u(u), to_dev(v), L, 64, 0.1, max_steps=2, shape_order=4)
+    with pytest.raises(kp.KdeError):
+        ctx.pic_step(bad, 1)
