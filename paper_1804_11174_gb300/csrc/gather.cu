@@ -171,14 +171,17 @@ __global__ void __launch_bounds__(GAT_THREADS) gather_kernel(GatherArgs<T> A)
 }
 
 // ---------------------------------------------------------------------------
-// FP32 gather with packed pair arithmetic: each lane carries two particles (a
-// warp covers 64 consecutive sorted particles), and every node record is kept
-// pre-duplicated in shared memory -- (sin, sin, -cos, -cos) and (E, E) -- so
-// one 128-bit and one 64-bit broadcast load feed two particles' f32x2
-// multiply-adds.  The node loop runs as two contiguous segments (before and
-// after the wrap point), so it carries no per-node index arithmetic.
+// FP32 gather with packed pair arithmetic: each lane carries GAT2_NP = 4
+// particles (a warp covers 128 consecutive sorted particles) as two f32x2
+// pairs, and every node record is kept pre-duplicated in shared memory --
+// (sin, sin, -cos, -cos) and (E, E) -- so one 128-bit and one 64-bit broadcast
+// load feed four particles' multiply-adds.  The node loop runs as two
+// contiguous segments (before and after the wrap point), so it carries no
+// per-node index arithmetic.
 // ---------------------------------------------------------------------------
-#define GAT2_WARPS 8
+#define GAT2_WARPS 4
+#define GAT2_NP 4
+#define GAT2_ITEM (32 * GAT2_NP)  // particles per warp
 
 __global__ void __launch_bounds__(GAT2_WARPS * 32) gather2_kernel(GatherArgs<float> A)
 {
@@ -210,17 +213,20 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32) gather2_kernel(GatherArgs<flo
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = ((int64_t)blockIdx.x * GAT2_WARPS + warp) * 64;
-    int64_t jj[2] = {base + lane, base + 32 + lane};
-    float bs[2], bc[2], nm[2], kap[2];
-    uint32_t uu[2];
-    bool valid[2];
+    const int64_t base = ((int64_t)blockIdx.x * GAT2_WARPS + warp) * GAT2_ITEM;
+    float bs[GAT2_NP], bc[GAT2_NP], nm[GAT2_NP], kap[GAT2_NP], vin[GAT2_NP], nin[GAT2_NP];
+    uint32_t uu[GAT2_NP], idin[GAT2_NP];
+    bool valid[GAT2_NP];
     int lo = 0x3fffffff, hi = -0x3fffffff;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int64_t j = jj[h];
+    for (int h = 0; h < GAT2_NP; ++h) {
+        const int64_t j = base + h * 32 + lane;
         valid[h] = j < A.N;
         uu[h] = valid[h] ? A.u[j] : 0u;
+        // the push's inputs are loaded now, so that their latency hides behind the node loop
+        vin[h] = (A.u_out && valid[h]) ? A.v_in[j] : 0.f;
+        nin[h] = (A.norm_out && valid[h]) ? A.norm_in[j] : 0.f;
+        idin[h] = (A.id_out && valid[h]) ? A.id_in[j] : 0u;
         float k = A.kappa ? (valid[h] ? A.kappa[j] : 1.0f) : A.kappa_u;
         if (valid[h] && !(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
             kde_flag(A.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
@@ -253,38 +259,39 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32) gather2_kernel(GatherArgs<flo
     if (len <= 0) return;  // whole warp past the end
     int g0 = lo % Ng;
     if (g0 < 0) g0 += Ng;
-    const kde_f2 bsv = kde_pk(bs[0], bs[1]), bcv = kde_pk(bc[0], bc[1]);
-    kde_f2 acc = kde_pk(0.f, 0.f);
+    const kde_f2 bsA = kde_pk(bs[0], bs[1]), bcA = kde_pk(bc[0], bc[1]);
+    const kde_f2 bsB = kde_pk(bs[2], bs[3]), bcB = kde_pk(bc[2], bc[3]);
+    kde_f2 accA = kde_pk(0.f, 0.f), accB = kde_pk(0.f, 0.f);
     const int e1 = g0 + len < Ng ? g0 + len : Ng;  // first segment [g0, e1), then [0, len - (e1 - g0))
     const int e2 = len - (e1 - g0);
-#pragma unroll 2
-    for (int g = g0; g < e1; ++g) {
+    auto node = [&](int g) {
         const float4 q = SC[g];
         const float2 f = FF[g];
-        const kde_f2 sv = kde_fma2(kde_pk(q.x, q.y), bcv, kde_mul2(kde_pk(q.z, q.w), bsv));
-        acc = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), kde_pk(f.x, f.y), acc);
-    }
+        const kde_f2 S2 = kde_pk(q.x, q.y), C2 = kde_pk(q.z, q.w), F2 = kde_pk(f.x, f.y);
+        const kde_f2 svA = kde_fma2(S2, bcA, kde_mul2(C2, bsA));
+        const kde_f2 svB = kde_fma2(S2, bcB, kde_mul2(C2, bsB));
+        accA = kde_fma2(kde_ex2neg2(kde_mul2(svA, svA)), F2, accA);
+        accB = kde_fma2(kde_ex2neg2(kde_mul2(svB, svB)), F2, accB);
+    };
 #pragma unroll 2
-    for (int g = 0; g < e2; ++g) {
-        const float4 q = SC[g];
-        const float2 f = FF[g];
-        const kde_f2 sv = kde_fma2(kde_pk(q.x, q.y), bcv, kde_mul2(kde_pk(q.z, q.w), bsv));
-        acc = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), kde_pk(f.x, f.y), acc);
-    }
-    float ea[2];
-    kde_upk(acc, ea[0], ea[1]);
+    for (int g = g0; g < e1; ++g) node(g);
+#pragma unroll 2
+    for (int g = 0; g < e2; ++g) node(g);
+    float ea[GAT2_NP];
+    kde_upk(accA, ea[0], ea[1]);
+    kde_upk(accB, ea[2], ea[3]);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < GAT2_NP; ++h) {
         if (!valid[h]) continue;
-        const int64_t j = jj[h];
+        const int64_t j = base + h * 32 + lane;
         const float Ei = ea[h] * nm[h] * A.coef;
         if (A.u_out) {
-            const float v = A.v_in[j] + A.kick_qm_dt * Ei;
+            const float v = vin[h] + A.kick_qm_dt * Ei;
             A.v_out[j] = v;
             A.u_out[j] = advance_position(uu[h], v * A.dt_scale);
             if (A.kappa_out) A.kappa_out[j] = kap[h];
-            if (A.norm_out) A.norm_out[j] = A.norm_in[j];
-            if (A.id_out) A.id_out[j] = A.id_in[j];
+            if (A.norm_out) A.norm_out[j] = nin[h];
+            if (A.id_out) A.id_out[j] = idin[h];
         } else {
             A.out[A.perm ? A.perm[j] : j] = Ei;
         }
@@ -305,7 +312,7 @@ static kde_status launch_gather2(kde_ctx *ctx, GatherArgs<float> &A)
                  "gather2 attribute");
         attr = true;
     }
-    unsigned grid = (unsigned)((A.N + GAT2_WARPS * 64 - 1) / (GAT2_WARPS * 64));
+    unsigned grid = (unsigned)((A.N + GAT2_WARPS * GAT2_ITEM - 1) / (GAT2_WARPS * GAT2_ITEM));
     if (grid == 0) grid = 1;
     {
         KdeProfScope _ps(ctx, PROF_GATHER);
