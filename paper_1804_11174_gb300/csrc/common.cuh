@@ -81,6 +81,7 @@ enum WsSlot {
     WS_AD_T,
     WS_AD_PART,
     WS_AD_OUT,
+    WS_CV_GPAR,
     WS_NSLOTS
 };
 

@@ -49,7 +49,42 @@ template <typename T> struct DepSrc {
     const unsigned int *wmax_bits;   // if not null: bound = N * coef * norm_bound * w_max (float bits)
     double norm_bound;
     unsigned int *status;
+    int scale_exp;  // KDE_ES_FROM_BOUND, or the exponent es of the fixed-point scale 2^es
 };
+
+#define KDE_ES_FROM_BOUND (-100000)
+
+// exponent es of the fixed-point scale kde_acc_scale(bound) = 2^es
+__device__ __forceinline__ int acc_scale_exp(double bound)
+{
+    int e;
+    frexp(bound > 0 ? bound : 1.0, &e);
+    return 62 - e;
+}
+
+// x 2^es rounded to the nearest integer, ties to even, in integer arithmetic: for
+// -100 <= es <= 100 the same value as __double2ll_rn((double)x * 2^es) (the product
+// is exact in FP64), without touching the FP64 pipe, which is slow on this part.
+// |x| 2^es must stay below 2^62 (the scale's bound guarantees it).
+__device__ __forceinline__ long long fix_pow2(float x, int es)
+{
+    const uint32_t b = __float_as_uint(x);
+    const int be = (int)((b >> 23) & 0xffu);
+    if (be == 0) return 0;  // zero or subnormal: |x| 2^es < 2^-126 2^100 < 1/2
+    const int ex = be - 150 + es;  // |x| 2^es = m 2^ex with the 24-bit significand m
+    const uint32_t m = (b & 0x7fffffu) | 0x800000u;
+    long long q;
+    if (ex >= 0) {
+        q = (long long)m << (ex < 39 ? ex : 39);
+    } else if (ex < -24) {
+        q = 0;  // below 1/2
+    } else {
+        const int sh = -ex;  // 1 .. 24
+        const uint32_t qq = m >> sh, rem = m & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        q = (long long)(qq + ((rem > half || (rem == half && (qq & 1u))) ? 1u : 0u));
+    }
+    return (b >> 31) ? -q : q;
+}
 
 __device__ __forceinline__ int window_nodes_f(float kappa, int Ng, float xcut)
 {
@@ -257,10 +292,26 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
         const int wn_ = window_nodes_f(k, Ng, (float)KDE_XCUT);
         wloc = wn_ > wloc ? wn_ : wloc;
     }
+    // the fixed-point scale 2^es, worked out by one thread: FP64 stays off the other threads
+    __shared__ int s_es;
+    if (tid == 0) {
+        int es = S.scale_exp;
+        if (es == KDE_ES_FROM_BOUND) {
+            double bound = S.bound;
+            if (S.wmax_bits)
+                bound = (double)S.N * (double)S.coef * S.norm_bound * (double)__uint_as_float(*S.wmax_bits);
+            es = acc_scale_exp(bound);
+        }
+        s_es = es;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wloc = max(wloc, __shfl_xor_sync(0xffffffffu, wloc, o));
     if (lane == 0) red[warp] = wloc;
     __syncthreads();
+    const int es = s_es;
+    const bool fix_int = es >= -100 && es <= 100;
+    // the FP64 conversion, for extreme bounds only; 2^es built from its bits
+    const double scale = __longlong_as_double((long long)(1023 + (es < -1000 ? -1000 : (es > 1000 ? 1000 : es))) << 52);
     int W = 0;
 #pragma unroll
     for (int k = 0; k < DEP_WARPS; ++k) W = red[k] > W ? red[k] : W;
@@ -272,9 +323,6 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
         R = Ng;
     }
     const int ngroups = (R + 63) >> 6;
-    double bound = S.bound;
-    if (S.wmax_bits) bound = (double)S.N * (double)S.coef * S.norm_bound * (double)__uint_as_float(*S.wmax_bits);
-    const double scale = kde_acc_scale(bound);
 
     auto node_pair = [&](int gi, int &ga, int &gb, kde_f2 &SS, kde_f2 &nCC, bool &va, bool &vb) {
         const int ra = gi * 64 + lane, rb = ra + 32;
@@ -312,9 +360,9 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
             float aa, ab;
             kde_upk(sweep(0, n, SS, nCC), aa, ab);
             long long v;
-            if (va && (v = __double2ll_rn((double)aa * scale)) != 0)
+            if (va && (v = fix_int ? fix_pow2(aa, es) : __double2ll_rn((double)aa * scale)) != 0)
                 atomicAdd((unsigned long long *)&S.acc[ga], (unsigned long long)v);
-            if (vb && (v = __double2ll_rn((double)ab * scale)) != 0)
+            if (vb && (v = fix_int ? fix_pow2(ab, es) : __double2ll_rn((double)ab * scale)) != 0)
                 atomicAdd((unsigned long long *)&S.acc[gb], (unsigned long long)v);
         }
         return;
@@ -342,7 +390,7 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
         for (int k = 0; k < sr; ++k) a += part[k * DEP2_PART + r];
         int g = g_lo + r;
         g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
-        const long long v = __double2ll_rn((double)a * scale);
+        const long long v = fix_int ? fix_pow2(a, es) : __double2ll_rn((double)a * scale);
         if (v) atomicAdd((unsigned long long *)&S.acc[g], (unsigned long long)v);
     }
 }
@@ -422,6 +470,7 @@ kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T
     S.wmax_bits = wmax_bits;
     S.norm_bound = norm_bound;
     S.status = ctx->d_status;
+    S.scale_exp = KDE_ES_FROM_BOUND;
     unsigned grid = (unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK);
     {
         KdeProfScope _ps(ctx, PROF_DEPOSIT);
@@ -467,55 +516,75 @@ __host__ __device__ inline int cv_grid_points(double kappa_max)
     return M;
 }
 
+// per-candidate parameters of the grid deposit
+struct GridPar {
+    float k;       // the candidate: uniform width, or the scale of the relative widths
+    float norm_u;  // uniform norm (uniform widths)
+    int M;         // grid points
+    int es;        // fixed-point scale 2^es of the grid sums
+    float w_u;     // the weight 1/N
+};
+
+// one thread per candidate: the FP64 Bessel norm of the largest width, the grid size and
+// the fixed-point scale, worked out once instead of in every thread of the deposit
+__global__ void cv_grid_par_kernel(CandList cl, const unsigned int *krmax_bits, int64_t N, GridPar *par)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cl.n) return;
+    const double kmax = cl.scale_mode ? cl.k[c] * (double)__uint_as_float(*krmax_bits) : cl.k[c];
+    const double nb = kde_norm(kmax);  // bound of a node value: N * (1/N) * the largest norm
+    GridPar p;
+    p.k = (float)cl.k[c];
+    p.norm_u = (float)nb;
+    p.M = cv_grid_points(kmax);
+    p.es = acc_scale_exp(nb);
+    p.w_u = (float)(1.0 / (double)N);
+    par[c] = p;
+}
+
 __global__ void __launch_bounds__(DEP_THREADS)
-    cv_grid_deposit_kernel(const uint32_t *u, int64_t N, const float *kappa_rel, const float *lnorm,
-                           const unsigned int *krmax_bits, CandList cl, long long *acc, unsigned int *status)
+    cv_grid_deposit_kernel(const uint32_t *u, int64_t N, const float *kappa_rel, const float *lnorm, int scale_mode,
+                           const GridPar *par, long long *acc, unsigned int *status)
 {
     __shared__ float4 rsc[DEP_CHUNK];
     __shared__ float2 rwn[DEP_CHUNK];
     __shared__ float part[DEP_WARPS * DEP2_PART];
     __shared__ int red[DEP_WARPS];
     const int c = blockIdx.y;
+    const GridPar p = par[c];
     DepSrc<float> S{};
     S.u = u;
     S.N = N;
     S.coef = 1.0f;
     S.w = nullptr;
-    S.w_u = (float)(1.0 / (double)N);
+    S.w_u = p.w_u;
     S.nodes = nullptr;
     S.acc = acc + (size_t)c * CV_MAXM;
     S.status = status;
     S.wmax_bits = nullptr;
-    double kmax;
-    if (cl.scale_mode) {
-        kmax = cl.k[c] * (double)__uint_as_float(*krmax_bits);
+    S.norm = nullptr;
+    if (scale_mode) {
         S.kappa = kappa_rel;
-        S.kscale = (float)cl.k[c];
+        S.kscale = p.k;
         S.lnorm = lnorm + (size_t)c * N;
-        S.norm = nullptr;
-        S.bound = kde_norm(kmax);  // N * (1/N) * largest norm
     } else {
-        kmax = cl.k[c];
         S.kappa = nullptr;
-        S.kappa_u = (float)cl.k[c];
+        S.kappa_u = p.k;
         S.kscale = 1.0f;
         S.lnorm = nullptr;
-        S.norm = nullptr;
-        S.norm_u = (float)kde_norm(kmax);
-        S.bound = kde_norm(kmax);
+        S.norm_u = p.norm_u;
     }
-    S.Ng = cv_grid_points(kmax);
+    S.scale_exp = p.es;
+    S.Ng = p.M;
     deposit_chunk_body_x2(S, blockIdx.x, rsc, rwn, part, red);
 }
 
 // FP64 trapezoid sum of fhat^2 on each candidate's grid: f2[c] = (2 pi / M) sum_g fhat_g^2
-__global__ void cv_grid_square_kernel(const long long *acc, const float *kappa_rel_unused,
-                                      const unsigned int *krmax_bits, CandList cl, double *f2)
+__global__ void cv_grid_square_kernel(const long long *acc, const GridPar *par, double *f2)
 {
     const int c = blockIdx.x;
-    double kmax = cl.scale_mode ? cl.k[c] * (double)__uint_as_float(*krmax_bits) : cl.k[c];
-    const int M = cv_grid_points(kmax);
-    const double inv = 1.0 / kde_acc_scale(kde_norm(kmax));
+    const int M = par[c].M;
+    const double inv = __longlong_as_double((long long)(1023 - par[c].es) << 52);  // 2^-es
     __shared__ double red[256];
     double s = 0.0;
     for (int g = threadIdx.x; g < M; g += blockDim.x) {
@@ -529,7 +598,6 @@ __global__ void cv_grid_square_kernel(const long long *acc, const float *kappa_r
         __syncthreads();
     }
     if (threadIdx.x == 0) f2[c] = KDE_TWO_PI / M * red[0];
-    (void)kappa_rel_unused;
 }
 
 kde_status kde_cv_integral_term(kde_ctx *ctx, const uint32_t *u_sorted, int64_t N, const float *kappa_rel,
@@ -539,14 +607,18 @@ kde_status kde_cv_integral_term(kde_ctx *ctx, const uint32_t *u_sorted, int64_t 
     long long *acc = (long long *)kde_ws(ctx, WS_CV_ACC, (size_t)cl.n * CV_MAXM * sizeof(long long));
     if (!acc) return KDE_ENOMEM;
     KDE_CUDA(ctx, cudaMemsetAsync(acc, 0, (size_t)cl.n * CV_MAXM * sizeof(long long), ctx->stream), "cv acc memset");
+    GridPar *par = (GridPar *)kde_ws(ctx, WS_CV_GPAR, (size_t)cl.n * sizeof(GridPar));
+    if (!par) return KDE_ENOMEM;
+    cv_grid_par_kernel<<<(cl.n + 63) / 64, 64, 0, ctx->stream>>>(cl, krmax_bits, N, par);
+    KDE_LAUNCHED(ctx, "cv_grid_par_kernel");
     dim3 grid((unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK), (unsigned)cl.n);
     {
         KdeProfScope _ps(ctx, PROF_CV_GRID);
-    cv_grid_deposit_kernel<<<grid, DEP_THREADS, 0, ctx->stream>>>(u_sorted, N, kappa_rel, lnorm, krmax_bits, cl, acc,
-                                                                    ctx->d_status);
+        cv_grid_deposit_kernel<<<grid, DEP_THREADS, 0, ctx->stream>>>(u_sorted, N, kappa_rel, lnorm, cl.scale_mode,
+                                                                        par, acc, ctx->d_status);
     }
     KDE_LAUNCHED(ctx, "cv_grid_deposit_kernel");
-    cv_grid_square_kernel<<<cl.n, 256, 0, ctx->stream>>>(acc, kappa_rel, krmax_bits, cl, f2_out);
+    cv_grid_square_kernel<<<cl.n, 256, 0, ctx->stream>>>(acc, par, f2_out);
     KDE_LAUNCHED(ctx, "cv_grid_square_kernel");
     return KDE_OK;
 }
