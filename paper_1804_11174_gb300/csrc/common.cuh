@@ -214,6 +214,20 @@ __device__ __forceinline__ kde_f2 kde_ex2neg2(kde_f2 x)
     kde_upk(x, a, b);
     return kde_pk(kde_ex2(-a), kde_ex2(-b));
 }
+// 2^x for both lanes of a packed pair
+__device__ __forceinline__ kde_f2 kde_ex22(kde_f2 x)
+{
+    float a, b;
+    kde_upk(x, a, b);
+    return kde_pk(kde_ex2(a), kde_ex2(b));
+}
+
+// largest width for the cosine form of the FP32 kernel value,
+// 2^(K cos x_j cos x_g + K sin x_j sin x_g - K) with K = kappa log2(e): three
+// multiply-adds per pair instead of the half-angle form's four, at the price of an
+// exponent that carries about K 2^-24 of cancellation error near the peak (a
+// relative error of about 2e-8 kappa in the L2 norm of a density)
+#define KDE_COSFORM_KMAX 32.0f
 
 __device__ __forceinline__ void kde_flag(unsigned int *status, unsigned code, unsigned detail)
 {

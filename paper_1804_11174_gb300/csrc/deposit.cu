@@ -253,44 +253,47 @@ __device__ void deposit_chunk_body(const DepSrc<T> &S, int64_t chunk, DepRec<T> 
 // ---------------------------------------------------------------------------
 // FP32 chunk body with packed pair arithmetic: each lane owns two nodes (a warp
 // pass covers 64 consecutive nodes) and every particle record is staged
-// pre-duplicated -- (beta sin, beta sin, beta cos, beta cos) and (w n, w n) --
-// so one 128-bit and one 64-bit broadcast load feed the f32x2 multiply-adds of
-// both nodes.  Same node range, slicing and fixed-order combination as the
-// scalar body.
+// pre-duplicated, so that one 128-bit and one 64-bit broadcast load feed the
+// f32x2 multiply-adds of both nodes.  Same node range, slicing and fixed-order
+// combination as the scalar body.  Two forms of the kernel value, chosen per
+// chunk by its largest width:
+//  * half-angle (any width): 2^-(S_g beta c_j - C_g beta s_j)^2 with (s, c) the sine
+//    and cosine of half the angle; records (beta s, beta s, beta c, beta c) and
+//    (w n, w n); four multiply-adds per pair;
+//  * cosine (largest width <= KDE_COSFORM_KMAX, when allowed): 2^(K cos(x_j - x_g))
+//    2^-K with K = kappa log2(e); records (K cos, K cos, K sin, K sin) of the full
+//    angle and (w n 2^-K, w n 2^-K); three multiply-adds per pair.
 // ---------------------------------------------------------------------------
 #define DEP2_PART 512
 
 __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, float4 *rsc, float2 *rwn, float *part,
-                                      int *red)
+                                      int *red, bool allow_cos)
 {
     const int64_t i0 = chunk * DEP_CHUNK;
     if (i0 >= S.N) return;
     const int n = (int)(S.N - i0 < DEP_CHUNK ? S.N - i0 : DEP_CHUNK);
     const int Ng = S.Ng;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int wloc = 0;
+    // pass 1: the smallest width (it sets the window) and the largest (it sets the form)
+    float kmin = (float)KDE_KAPPA_MAX, kmax = 0.f;
     for (int t = tid; t < n; t += DEP_THREADS) {
         const int64_t j = i0 + t;
-        const uint32_t uu = S.u[j];
         float k = S.kappa ? S.kscale * S.kappa[j] : S.kappa_u;
         if (!(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
             kde_flag(S.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
             k = (float)KDE_KAPPA_MAX;
         }
-        float nm;
-        if (S.lnorm) nm = exp2f(S.lnorm[j]);
-        else if (S.norm) nm = S.norm[j];
-        else if (S.kappa) nm = (float)kde_norm((double)k);
-        else nm = S.norm_u;
-        const float wj = S.w ? S.w[j] : S.w_u;
-        float sh, ch;
-        kde_half_sincos(uu, sh, ch);
-        const float beta = sqrtf((float)(2.0 * KDE_LOG2E) * k);
-        rsc[t] = make_float4(beta * sh, beta * sh, beta * ch, beta * ch);
-        const float wn = wj * S.coef * nm;
-        rwn[t] = make_float2(wn, wn);
-        const int wn_ = window_nodes_f(k, Ng, (float)KDE_XCUT);
-        wloc = wn_ > wloc ? wn_ : wloc;
+        kmin = fminf(kmin, k);
+        kmax = fmaxf(kmax, k);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    if (lane == 0) {
+        red[warp] = __float_as_int(kmin);
+        red[DEP_WARPS + warp] = __float_as_int(kmax);
     }
     // the fixed-point scale 2^es, worked out by one thread: FP64 stays off the other threads
     __shared__ int s_es;
@@ -304,17 +307,47 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
         }
         s_es = es;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wloc = max(wloc, __shfl_xor_sync(0xffffffffu, wloc, o));
-    if (lane == 0) red[warp] = wloc;
     __syncthreads();
     const int es = s_es;
     const bool fix_int = es >= -100 && es <= 100;
     // the FP64 conversion, for extreme bounds only; 2^es built from its bits
     const double scale = __longlong_as_double((long long)(1023 + (es < -1000 ? -1000 : (es > 1000 ? 1000 : es))) << 52);
-    int W = 0;
 #pragma unroll
-    for (int k = 0; k < DEP_WARPS; ++k) W = red[k] > W ? red[k] : W;
+    for (int k = 0; k < DEP_WARPS; ++k) {
+        kmin = fminf(kmin, __int_as_float(red[k]));
+        kmax = fmaxf(kmax, __int_as_float(red[DEP_WARPS + k]));
+    }
+    // the window shrinks as the width grows: the smallest width's window covers all
+    const int W = window_nodes_f(kmin, Ng, (float)KDE_XCUT);
+    const bool cosf = allow_cos && kmax <= KDE_COSFORM_KMAX;
+    // pass 2: the particle records
+    for (int t = tid; t < n; t += DEP_THREADS) {
+        const int64_t j = i0 + t;
+        const uint32_t uu = S.u[j];
+        float k = S.kappa ? S.kscale * S.kappa[j] : S.kappa_u;
+        if (!(k > 0.f && k <= (float)KDE_KAPPA_MAX)) k = (float)KDE_KAPPA_MAX;
+        float nm;
+        if (S.lnorm) nm = exp2f(S.lnorm[j]);
+        else if (S.norm) nm = S.norm[j];
+        else if (S.kappa) nm = (float)kde_norm((double)k);
+        else nm = S.norm_u;
+        const float wj = S.w ? S.w[j] : S.w_u;
+        const float wn = wj * S.coef * nm;
+        float sh, ch;
+        kde_half_sincos(uu, sh, ch);
+        if (cosf) {
+            const float K = (float)KDE_LOG2E * k;
+            const float cx = (ch - sh) * (ch + sh), sx = 2.f * sh * ch;
+            rsc[t] = make_float4(K * cx, K * cx, K * sx, K * sx);
+            const float wk = wn * kde_ex2(-K);
+            rwn[t] = make_float2(wk, wk);
+        } else {
+            const float beta = sqrtf((float)(2.0 * KDE_LOG2E) * k);
+            rsc[t] = make_float4(beta * sh, beta * sh, beta * ch, beta * ch);
+            rwn[t] = make_float2(wn, wn);
+        }
+    }
+    __syncthreads();
     const int c_first = kde_cell(S.u[i0], Ng), c_last = kde_cell(S.u[i0 + n - 1], Ng);
     int g_lo = c_first - W;
     int R = c_last + W - g_lo + 1;
@@ -335,18 +368,35 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
         float sa, ca, sb, cb;
         node_sc(S, va ? ga : 0, sa, ca);
         node_sc(S, vb ? gb : 0, sb, cb);
-        SS = kde_pk(sa, sb);
-        nCC = kde_pk(-ca, -cb);
+        if (cosf) {
+            // sine and cosine of the full node angle
+            SS = kde_pk(2.f * sa * ca, 2.f * sb * cb);
+            nCC = kde_pk((ca - sa) * (ca + sa), (cb - sb) * (cb + sb));
+        } else {
+            SS = kde_pk(sa, sb);
+            nCC = kde_pk(-ca, -cb);
+        }
     };
     auto sweep = [&](int p0, int p1, kde_f2 SS, kde_f2 nCC) -> kde_f2 {
         kde_f2 acc = kde_pk(0.f, 0.f);
+        if (cosf) {
 #pragma unroll 4
-        for (int p = p0; p < p1; ++p) {
-            const float4 q = rsc[p];
-            const float2 w2 = rwn[p];
-            // s = S_g (beta cos_j) - C_g (beta sin_j) for both nodes
-            const kde_f2 sv = kde_fma2(SS, kde_pk(q.z, q.w), kde_mul2(nCC, kde_pk(q.x, q.y)));
-            acc = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), kde_pk(w2.x, w2.y), acc);
+            for (int p = p0; p < p1; ++p) {
+                const float4 q = rsc[p];
+                const float2 w2 = rwn[p];
+                // K cos(x_j - x_g) = sin_g (K sin_j) + cos_g (K cos_j) for both nodes
+                const kde_f2 ev = kde_fma2(SS, kde_pk(q.z, q.w), kde_mul2(nCC, kde_pk(q.x, q.y)));
+                acc = kde_fma2(kde_ex22(ev), kde_pk(w2.x, w2.y), acc);
+            }
+        } else {
+#pragma unroll 4
+            for (int p = p0; p < p1; ++p) {
+                const float4 q = rsc[p];
+                const float2 w2 = rwn[p];
+                // s = S_g (beta cos_j) - C_g (beta sin_j) for both nodes
+                const kde_f2 sv = kde_fma2(SS, kde_pk(q.z, q.w), kde_mul2(nCC, kde_pk(q.x, q.y)));
+                acc = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), kde_pk(w2.x, w2.y), acc);
+            }
         }
         return acc;
     };
@@ -400,8 +450,8 @@ __global__ void __launch_bounds__(DEP_THREADS) deposit_chunk_x2_kernel(DepSrc<fl
     __shared__ float4 rsc[DEP_CHUNK];
     __shared__ float2 rwn[DEP_CHUNK];
     __shared__ float part[DEP_WARPS * DEP2_PART];
-    __shared__ int red[DEP_WARPS];
-    deposit_chunk_body_x2(S, blockIdx.x, rsc, rwn, part, red);
+    __shared__ int red[2 * DEP_WARPS];
+    deposit_chunk_body_x2(S, blockIdx.x, rsc, rwn, part, red, true);
 }
 
 template <typename T>
@@ -549,7 +599,7 @@ __global__ void __launch_bounds__(DEP_THREADS)
     __shared__ float4 rsc[DEP_CHUNK];
     __shared__ float2 rwn[DEP_CHUNK];
     __shared__ float part[DEP_WARPS * DEP2_PART];
-    __shared__ int red[DEP_WARPS];
+    __shared__ int red[2 * DEP_WARPS];
     const int c = blockIdx.y;
     const GridPar p = par[c];
     DepSrc<float> S{};
@@ -576,7 +626,8 @@ __global__ void __launch_bounds__(DEP_THREADS)
     }
     S.scale_exp = p.es;
     S.Ng = p.M;
-    deposit_chunk_body_x2(S, blockIdx.x, rsc, rwn, part, red);
+    // the CV integral term keeps the half-angle form: its sums carry the CV's accuracy
+    deposit_chunk_body_x2(S, blockIdx.x, rsc, rwn, part, red, false);
 }
 
 // FP64 trapezoid sum of fhat^2 on each candidate's grid: f2[c] = (2 pi / M) sum_g fhat_g^2

@@ -173,11 +173,16 @@ __global__ void __launch_bounds__(GAT_THREADS) gather_kernel(GatherArgs<T> A)
 // ---------------------------------------------------------------------------
 // FP32 gather with packed pair arithmetic: each lane carries GAT2_NP = 4
 // particles (a warp covers 128 consecutive sorted particles) as two f32x2
-// pairs, and every node record is kept pre-duplicated in shared memory --
-// (sin, sin, -cos, -cos) and (E, E) -- so one 128-bit and one 64-bit broadcast
-// load feed four particles' multiply-adds.  The node loop runs as two
-// contiguous segments (before and after the wrap point), so it carries no
-// per-node index arithmetic.
+// pairs, and every node record is kept pre-duplicated in shared memory, so one
+// 128-bit and one 64-bit broadcast load feed four particles' multiply-adds.  The
+// node loop runs as two contiguous segments (before and after the wrap point), so
+// it carries no per-node index arithmetic.  The form of the kernel value is chosen
+// per block by its largest width, as in the packed deposit:
+//  * half-angle: nodes (sin, sin, -cos, -cos) of half the node angle, particles
+//    (beta sin, beta cos) of half theirs, 2^-(S_g beta c_j - C_g beta s_j)^2;
+//  * cosine (largest width <= KDE_COSFORM_KMAX): nodes (sin, sin, cos, cos) of the
+//    full angle, particles (K cos, K sin), 2^(K cos(x_j - x_g)), and 2^-K folded into
+//    the particle's norm; three multiply-adds per pair instead of four.
 // ---------------------------------------------------------------------------
 #define GAT2_WARPS 4
 #define GAT2_NP 4
@@ -186,13 +191,61 @@ __global__ void __launch_bounds__(GAT_THREADS) gather_kernel(GatherArgs<T> A)
 __global__ void __launch_bounds__(GAT2_WARPS * 32) gather2_kernel(GatherArgs<float> A)
 {
     extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ float kred[GAT2_WARPS];
     const int Ng = A.Ng;
-    float4 *SC = (float4 *)sm;           // (S, S, -C, -C)
-    float2 *FF = (float2 *)(SC + Ng);    // (E, E)
+    float4 *SC = (float4 *)sm;         // node angle records
+    float2 *FF = (float2 *)(SC + Ng);  // (E, E)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x * GAT2_WARPS + warp) * GAT2_ITEM;
+    float nm[GAT2_NP], kap[GAT2_NP], vin[GAT2_NP], nin[GAT2_NP];
+    uint32_t uu[GAT2_NP], idin[GAT2_NP];
+    bool valid[GAT2_NP];
+    int lo = 0x3fffffff, hi = -0x3fffffff;
+    float kmax = 0.f;
+#pragma unroll
+    for (int h = 0; h < GAT2_NP; ++h) {
+        const int64_t j = base + h * 32 + lane;
+        valid[h] = j < A.N;
+        uu[h] = valid[h] ? A.u[j] : 0u;
+        // the push's inputs are loaded now, so that their latency hides behind the node loop
+        vin[h] = (A.u_out && valid[h]) ? A.v_in[j] : 0.f;
+        nin[h] = (A.norm_out && valid[h]) ? A.norm_in[j] : 0.f;
+        idin[h] = (A.id_out && valid[h]) ? A.id_in[j] : 0u;
+        float k = A.kappa ? (valid[h] ? A.kappa[j] : 1.0f) : A.kappa_u;
+        if (valid[h] && !(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
+            kde_flag(A.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
+            k = (float)KDE_KAPPA_MAX;
+        }
+        kap[h] = k;
+        nm[h] = A.norm ? (valid[h] ? A.norm[j] : 0.f) : (A.kappa ? (float)kde_norm((double)k) : A.norm_u);
+        if (valid[h]) {
+            kmax = fmaxf(kmax, k);
+            const int cell = kde_cell(uu[h], Ng);
+            const int W = window_nodes_g(k, Ng, (float)KDE_XCUT);
+            lo = min(lo, cell - W);
+            hi = max(hi, cell + W);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    if (lane == 0) kred[warp] = kmax;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < GAT2_WARPS; ++w) kmax = fmaxf(kmax, kred[w]);
+    const bool cosf = kmax <= KDE_COSFORM_KMAX;
     for (int g = threadIdx.x; g < Ng; g += GAT2_WARPS * 32) {
-        float2 sc = A.nodes[g];
-        SC[g] = make_float4(sc.x, sc.x, -sc.y, -sc.y);
-        float f = A.field[g];
+        const float2 sc = A.nodes[g];
+        if (cosf) {
+            const float sf = 2.f * sc.x * sc.y, cf = (sc.y - sc.x) * (sc.y + sc.x);
+            SC[g] = make_float4(sf, sf, cf, cf);
+        } else {
+            SC[g] = make_float4(sc.x, sc.x, -sc.y, -sc.y);
+        }
+        const float f = A.field[g];
         FF[g] = make_float2(f, f);
     }
     if (blockIdx.x == 0 && A.energy) {
@@ -212,71 +265,66 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32) gather2_kernel(GatherArgs<flo
     }
     __syncthreads();
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = ((int64_t)blockIdx.x * GAT2_WARPS + warp) * GAT2_ITEM;
-    float bs[GAT2_NP], bc[GAT2_NP], nm[GAT2_NP], kap[GAT2_NP], vin[GAT2_NP], nin[GAT2_NP];
-    uint32_t uu[GAT2_NP], idin[GAT2_NP];
-    bool valid[GAT2_NP];
-    int lo = 0x3fffffff, hi = -0x3fffffff;
-#pragma unroll
-    for (int h = 0; h < GAT2_NP; ++h) {
-        const int64_t j = base + h * 32 + lane;
-        valid[h] = j < A.N;
-        uu[h] = valid[h] ? A.u[j] : 0u;
-        // the push's inputs are loaded now, so that their latency hides behind the node loop
-        vin[h] = (A.u_out && valid[h]) ? A.v_in[j] : 0.f;
-        nin[h] = (A.norm_out && valid[h]) ? A.norm_in[j] : 0.f;
-        idin[h] = (A.id_out && valid[h]) ? A.id_in[j] : 0u;
-        float k = A.kappa ? (valid[h] ? A.kappa[j] : 1.0f) : A.kappa_u;
-        if (valid[h] && !(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
-            kde_flag(A.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
-            k = (float)KDE_KAPPA_MAX;
-        }
-        kap[h] = k;
-        nm[h] = A.norm ? (valid[h] ? A.norm[j] : 0.f) : (A.kappa ? (float)kde_norm((double)k) : A.norm_u);
-        float sh, ch;
-        kde_half_sincos(uu[h], sh, ch);
-        const float beta = sqrtf((float)(2.0 * KDE_LOG2E) * k);
-        bs[h] = beta * sh;
-        bc[h] = beta * ch;
-        if (valid[h]) {
-            const int cell = kde_cell(uu[h], Ng);
-            const int W = window_nodes_g(k, Ng, (float)KDE_XCUT);
-            lo = min(lo, cell - W);
-            hi = max(hi, cell + W);
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
     int len = hi - lo + 1;
     if (len >= Ng) {
         lo = 0;
         len = Ng;
     }
     if (len <= 0) return;  // whole warp past the end
+    // (ps, pc) pair with the node's (sin, sin) and (c, c) columns: half-angle (beta cos,
+    // beta sin) of half the particle angle, cosine form (K sin, K cos) of the full one
+    float ps[GAT2_NP], pc[GAT2_NP];
+#pragma unroll
+    for (int h = 0; h < GAT2_NP; ++h) {
+        float sh, ch;
+        kde_half_sincos(uu[h], sh, ch);
+        if (cosf) {
+            const float K = (float)KDE_LOG2E * kap[h];
+            ps[h] = K * (2.f * sh * ch);
+            pc[h] = K * ((ch - sh) * (ch + sh));
+            nm[h] *= kde_ex2(-K);
+        } else {
+            const float beta = sqrtf((float)(2.0 * KDE_LOG2E) * kap[h]);
+            ps[h] = beta * ch;
+            pc[h] = beta * sh;
+        }
+    }
     int g0 = lo % Ng;
     if (g0 < 0) g0 += Ng;
-    const kde_f2 bsA = kde_pk(bs[0], bs[1]), bcA = kde_pk(bc[0], bc[1]);
-    const kde_f2 bsB = kde_pk(bs[2], bs[3]), bcB = kde_pk(bc[2], bc[3]);
+    const kde_f2 psA = kde_pk(ps[0], ps[1]), pcA = kde_pk(pc[0], pc[1]);
+    const kde_f2 psB = kde_pk(ps[2], ps[3]), pcB = kde_pk(pc[2], pc[3]);
     kde_f2 accA = kde_pk(0.f, 0.f), accB = kde_pk(0.f, 0.f);
     const int e1 = g0 + len < Ng ? g0 + len : Ng;  // first segment [g0, e1), then [0, len - (e1 - g0))
     const int e2 = len - (e1 - g0);
-    auto node = [&](int g) {
+    auto node_half = [&](int g) {
         const float4 q = SC[g];
         const float2 f = FF[g];
         const kde_f2 S2 = kde_pk(q.x, q.y), C2 = kde_pk(q.z, q.w), F2 = kde_pk(f.x, f.y);
-        const kde_f2 svA = kde_fma2(S2, bcA, kde_mul2(C2, bsA));
-        const kde_f2 svB = kde_fma2(S2, bcB, kde_mul2(C2, bsB));
+        const kde_f2 svA = kde_fma2(S2, psA, kde_mul2(C2, pcA));
+        const kde_f2 svB = kde_fma2(S2, psB, kde_mul2(C2, pcB));
         accA = kde_fma2(kde_ex2neg2(kde_mul2(svA, svA)), F2, accA);
         accB = kde_fma2(kde_ex2neg2(kde_mul2(svB, svB)), F2, accB);
     };
+    auto node_cos = [&](int g) {
+        const float4 q = SC[g];
+        const float2 f = FF[g];
+        const kde_f2 S2 = kde_pk(q.x, q.y), C2 = kde_pk(q.z, q.w), F2 = kde_pk(f.x, f.y);
+        const kde_f2 evA = kde_fma2(S2, psA, kde_mul2(C2, pcA));
+        const kde_f2 evB = kde_fma2(S2, psB, kde_mul2(C2, pcB));
+        accA = kde_fma2(kde_ex22(evA), F2, accA);
+        accB = kde_fma2(kde_ex22(evB), F2, accB);
+    };
+    if (cosf) {
 #pragma unroll 2
-    for (int g = g0; g < e1; ++g) node(g);
+        for (int g = g0; g < e1; ++g) node_cos(g);
 #pragma unroll 2
-    for (int g = 0; g < e2; ++g) node(g);
+        for (int g = 0; g < e2; ++g) node_cos(g);
+    } else {
+#pragma unroll 2
+        for (int g = g0; g < e1; ++g) node_half(g);
+#pragma unroll 2
+        for (int g = 0; g < e2; ++g) node_half(g);
+    }
     float ea[GAT2_NP];
     kde_upk(accA, ea[0], ea[1]);
     kde_upk(accB, ea[2], ea[3]);

@@ -150,6 +150,53 @@ def test_gather_per_particle_and_fp64(ctx, oracle):
     assert rel_l2(out64, oracle.gather(x, f, L, kappa=k)) <= TOL64
 
 
+@pytest.mark.parametrize("kappa", [0.3, 12.0, 32.0, 32.5, 90.0])
+def test_kernel_value_forms(ctx, oracle, kappa):
+    # widths up to 32 take the cosine form of the FP32 kernel value (three multiply-adds
+    # a pair, an exponent that loses about K 2^-24 near the peak), wider ones the
+    # half-angle form; both stay within a few 1e-7 of the oracle in L2 on this load
+    L = 4 * math.pi
+    N, Ng = 20000, 256
+    u, x, _ = landau(17, N, L)
+    rho = ctx.deposit(to_dev_u(u), Ng, L, kappa_uniform=kappa).cpu().numpy()
+    assert rel_l2(rho, oracle.deposit(x, Ng, L, kappa_u=kappa)) <= 2e-6
+    f = np.sin(2 * math.pi * np.arange(Ng) / Ng) + 0.5
+    out = ctx.gather(to_dev_u(u), to_dev(f), L, kappa_uniform=kappa).cpu().numpy()
+    assert rel_l2(out, oracle.gather(x, f.astype(np.float32), L, kappa_u=kappa)) <= 2e-6
+
+
+def test_kernel_value_forms_mixed_chunks(ctx, oracle):
+    # narrow kernels on one half of the box, wide ones on the other: chunks and blocks
+    # of either form and the ones that straddle the change
+    L = 4 * math.pi
+    N, Ng = 30000, 128
+    u, x, _ = landau(23, N, L)
+    k = (np.where(x < L / 2, 10.0, 80.0) * (0.9 + 0.2 * I.uniforms(23, 9, N))).astype(np.float32)
+    rho = ctx.deposit(to_dev_u(u), Ng, L, kappa=to_dev(k)).cpu().numpy()
+    assert rel_l2(rho, oracle.deposit(x, Ng, L, kappa=k.astype(np.float64))) <= 2e-6
+    f = np.cos(2 * math.pi * np.arange(Ng) / Ng)
+    out = ctx.gather(to_dev_u(u), to_dev(f), L, kappa=to_dev(k)).cpu().numpy()
+    assert rel_l2(out, oracle.gather(x, f, L, kappa=k.astype(np.float64))) <= 2e-6
+
+
+def test_full_size_landau_deposit_gather_narrow(ctx, oracle):
+    # the Landau workload with the widths that Silverman's rule gives it (kappa ~ 8-30),
+    # which run in the cosine form
+    L = 4 * math.pi
+    N, Ng = 1 << 20, 256
+    u, x, _ = landau(4, N, L)
+    k = I.log_uniform(4, I.STREAM_KAPPA, N, 8.0, 30.0).astype(np.float32)
+    ud = to_dev_u(u)
+    rho = ctx.deposit(ud, Ng, L, kappa=to_dev(k)).cpu().numpy()
+    ref = oracle.deposit(x, Ng, L, kappa=k.astype(np.float64))
+    assert rel_l2(rho, ref) <= TOL32
+    f = oracle.poisson(1.0 - ref, L)
+    out = ctx.gather(ud, to_dev(f), L, kappa=to_dev(k)).cpu().numpy()
+    idx = np.linspace(0, N - 1, 4096).astype(np.int64)
+    refg = oracle.gather(x[idx], f.astype(np.float32), L, kappa=k[idx].astype(np.float64))
+    assert rel_l2(out[idx], refg) <= TOL32
+
+
 def test_full_size_landau_deposit_gather(ctx, oracle):
     # the Landau workload: N = 2^20, Ng = 256, particle-wise widths; every node of the
     # deposit and a sample of gathered particles against the oracle
