@@ -266,6 +266,125 @@ __device__ void deposit_chunk_body(const DepSrc<T> &S, int64_t chunk, DepRec<T> 
 // ---------------------------------------------------------------------------
 #define DEP2_PART 512
 
+// node phase of the packed deposit: each lane owns P pairs of nodes, so a warp pass
+// covers 64 P consecutive nodes of the chunk's range [g_lo, g_lo + R); with fewer
+// groups than warps the warps split the particles into slices whose partial sums
+// are combined in a fixed order
+template <int P>
+__device__ __forceinline__ void dep2_nodes(const DepSrc<float> &S, int n, int g_lo, int R, bool cosf, int es,
+                                           const float4 *rsc, const float2 *rwn, float *part)
+{
+    constexpr int GW = 64 * P;
+    const int Ng = S.Ng;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ngroups = (R + GW - 1) / GW;
+    const bool fix_int = es >= -100 && es <= 100;
+    // the FP64 conversion, for extreme bounds only; 2^es built from its bits
+    const double scale = __longlong_as_double((long long)(1023 + (es < -1000 ? -1000 : (es > 1000 ? 1000 : es))) << 52);
+
+    int gn[2 * P];
+    bool ok[2 * P];
+    kde_f2 SS[P], CC[P], acc[P];
+    auto nodes_of = [&](int gi) {
+#pragma unroll
+        for (int m = 0; m < 2 * P; ++m) {
+            const int r = gi * GW + m * 32 + lane;
+            ok[m] = r < R;
+            int g = g_lo + r;
+            g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
+            gn[m] = g;
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            float sa, ca, sb, cb;
+            node_sc(S, ok[2 * q] ? gn[2 * q] : 0, sa, ca);
+            node_sc(S, ok[2 * q + 1] ? gn[2 * q + 1] : 0, sb, cb);
+            if (cosf) {
+                // sine and cosine of the full node angle
+                SS[q] = kde_pk(2.f * sa * ca, 2.f * sb * cb);
+                CC[q] = kde_pk((ca - sa) * (ca + sa), (cb - sb) * (cb + sb));
+            } else {
+                SS[q] = kde_pk(sa, sb);
+                CC[q] = kde_pk(-ca, -cb);
+            }
+        }
+    };
+    auto sweep = [&](int p0, int p1) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) acc[q] = kde_pk(0.f, 0.f);
+        if (cosf) {
+#pragma unroll 4
+            for (int p = p0; p < p1; ++p) {
+                const float4 r4 = rsc[p];
+                const float2 w2 = rwn[p];
+                const kde_f2 qs = kde_pk(r4.z, r4.w), qc = kde_pk(r4.x, r4.y), w = kde_pk(w2.x, w2.y);
+                // K cos(x_j - x_g) = sin_g (K sin_j) + cos_g (K cos_j)
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    acc[q] = kde_fma2(kde_ex22(kde_fma2(SS[q], qs, kde_mul2(CC[q], qc))), w, acc[q]);
+            }
+        } else {
+#pragma unroll 4
+            for (int p = p0; p < p1; ++p) {
+                const float4 r4 = rsc[p];
+                const float2 w2 = rwn[p];
+                const kde_f2 qs = kde_pk(r4.z, r4.w), qc = kde_pk(r4.x, r4.y), w = kde_pk(w2.x, w2.y);
+                // s = S_g (beta cos_j) - C_g (beta sin_j)
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const kde_f2 sv = kde_fma2(SS[q], qs, kde_mul2(CC[q], qc));
+                    acc[q] = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), w, acc[q]);
+                }
+            }
+        }
+    };
+    auto fix = [&](float a) -> long long { return fix_int ? fix_pow2(a, es) : __double2ll_rn((double)a * scale); };
+
+    if (ngroups >= DEP_WARPS) {
+        for (int gi = warp; gi < ngroups; gi += DEP_WARPS) {
+            nodes_of(gi);
+            sweep(0, n);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                float a0, a1;
+                kde_upk(acc[q], a0, a1);
+                long long v;
+                if (ok[2 * q] && (v = fix(a0)) != 0) atomicAdd((unsigned long long *)&S.acc[gn[2 * q]], (unsigned long long)v);
+                if (ok[2 * q + 1] && (v = fix(a1)) != 0)
+                    atomicAdd((unsigned long long *)&S.acc[gn[2 * q + 1]], (unsigned long long)v);
+            }
+        }
+        return;
+    }
+    // every warp works: warp w takes node group w mod ngroups and one of that group's
+    // particle slices (the groups' slice counts differ by at most one); ngroups GW <= DEP2_PART
+    const int gi = warp % ngroups, sl = warp / ngroups;
+    const int slices = (DEP_WARPS - gi + ngroups - 1) / ngroups;
+    {
+        const int p0 = (int)((int64_t)n * sl / slices), p1 = (int)((int64_t)n * (sl + 1) / slices);
+        nodes_of(gi);
+        sweep(p0, p1);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            float a0, a1;
+            kde_upk(acc[q], a0, a1);
+            part[sl * DEP2_PART + gi * GW + 64 * q + lane] = a0;
+            part[sl * DEP2_PART + gi * GW + 64 * q + 32 + lane] = a1;
+        }
+    }
+    __syncthreads();
+    for (int r = tid; r < ngroups * GW; r += DEP_THREADS) {
+        if (r >= R) continue;
+        const int gr = r / GW, sr = (DEP_WARPS - gr + ngroups - 1) / ngroups;
+        float a = 0.f;
+        for (int k = 0; k < sr; ++k) a += part[k * DEP2_PART + r];
+        int g = g_lo + r;
+        g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
+        const long long v = fix(a);
+        if (v) atomicAdd((unsigned long long *)&S.acc[g], (unsigned long long)v);
+    }
+}
+
 __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, float4 *rsc, float2 *rwn, float *part,
                                       int *red, bool allow_cos)
 {
@@ -309,9 +428,6 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
     }
     __syncthreads();
     const int es = s_es;
-    const bool fix_int = es >= -100 && es <= 100;
-    // the FP64 conversion, for extreme bounds only; 2^es built from its bits
-    const double scale = __longlong_as_double((long long)(1023 + (es < -1000 ? -1000 : (es > 1000 ? 1000 : es))) << 52);
 #pragma unroll
     for (int k = 0; k < DEP_WARPS; ++k) {
         kmin = fminf(kmin, __int_as_float(red[k]));
@@ -355,94 +471,13 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
         g_lo = 0;
         R = Ng;
     }
-    const int ngroups = (R + 63) >> 6;
-
-    auto node_pair = [&](int gi, int &ga, int &gb, kde_f2 &SS, kde_f2 &nCC, bool &va, bool &vb) {
-        const int ra = gi * 64 + lane, rb = ra + 32;
-        va = ra < R;
-        vb = rb < R;
-        ga = g_lo + ra;
-        ga = ga < 0 ? ga + Ng : (ga >= Ng ? ga - Ng : ga);
-        gb = g_lo + rb;
-        gb = gb < 0 ? gb + Ng : (gb >= Ng ? gb - Ng : gb);
-        float sa, ca, sb, cb;
-        node_sc(S, va ? ga : 0, sa, ca);
-        node_sc(S, vb ? gb : 0, sb, cb);
-        if (cosf) {
-            // sine and cosine of the full node angle
-            SS = kde_pk(2.f * sa * ca, 2.f * sb * cb);
-            nCC = kde_pk((ca - sa) * (ca + sa), (cb - sb) * (cb + sb));
-        } else {
-            SS = kde_pk(sa, sb);
-            nCC = kde_pk(-ca, -cb);
-        }
-    };
-    auto sweep = [&](int p0, int p1, kde_f2 SS, kde_f2 nCC) -> kde_f2 {
-        kde_f2 acc = kde_pk(0.f, 0.f);
-        if (cosf) {
-#pragma unroll 4
-            for (int p = p0; p < p1; ++p) {
-                const float4 q = rsc[p];
-                const float2 w2 = rwn[p];
-                // K cos(x_j - x_g) = sin_g (K sin_j) + cos_g (K cos_j) for both nodes
-                const kde_f2 ev = kde_fma2(SS, kde_pk(q.z, q.w), kde_mul2(nCC, kde_pk(q.x, q.y)));
-                acc = kde_fma2(kde_ex22(ev), kde_pk(w2.x, w2.y), acc);
-            }
-        } else {
-#pragma unroll 4
-            for (int p = p0; p < p1; ++p) {
-                const float4 q = rsc[p];
-                const float2 w2 = rwn[p];
-                // s = S_g (beta cos_j) - C_g (beta sin_j) for both nodes
-                const kde_f2 sv = kde_fma2(SS, kde_pk(q.z, q.w), kde_mul2(nCC, kde_pk(q.x, q.y)));
-                acc = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), kde_pk(w2.x, w2.y), acc);
-            }
-        }
-        return acc;
-    };
-
-    if (ngroups >= DEP_WARPS) {
-        for (int gi = warp; gi < ngroups; gi += DEP_WARPS) {
-            int ga, gb;
-            bool va, vb;
-            kde_f2 SS, nCC;
-            node_pair(gi, ga, gb, SS, nCC, va, vb);
-            float aa, ab;
-            kde_upk(sweep(0, n, SS, nCC), aa, ab);
-            long long v;
-            if (va && (v = fix_int ? fix_pow2(aa, es) : __double2ll_rn((double)aa * scale)) != 0)
-                atomicAdd((unsigned long long *)&S.acc[ga], (unsigned long long)v);
-            if (vb && (v = fix_int ? fix_pow2(ab, es) : __double2ll_rn((double)ab * scale)) != 0)
-                atomicAdd((unsigned long long *)&S.acc[gb], (unsigned long long)v);
-        }
-        return;
-    }
-    // every warp works: warp w takes node group w mod ngroups and one of that group's
-    // particle slices (the groups' slice counts differ by at most one)
-    const int gi = warp % ngroups, sl = warp / ngroups;
-    const int slices = (DEP_WARPS - gi + ngroups - 1) / ngroups;
-    {
-        const int p0 = (int)((int64_t)n * sl / slices), p1 = (int)((int64_t)n * (sl + 1) / slices);
-        int ga, gb;
-        bool va, vb;
-        kde_f2 SS, nCC;
-        node_pair(gi, ga, gb, SS, nCC, va, vb);
-        float aa, ab;
-        kde_upk(sweep(p0, p1, SS, nCC), aa, ab);
-        part[sl * DEP2_PART + gi * 64 + lane] = aa;
-        part[sl * DEP2_PART + gi * 64 + 32 + lane] = ab;
-    }
-    __syncthreads();
-    for (int r = tid; r < ngroups * 64; r += DEP_THREADS) {
-        if (r >= R) continue;
-        const int gr = r >> 6, sr = (DEP_WARPS - gr + ngroups - 1) / ngroups;
-        float a = 0.f;
-        for (int k = 0; k < sr; ++k) a += part[k * DEP2_PART + r];
-        int g = g_lo + r;
-        g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
-        const long long v = fix_int ? fix_pow2(a, es) : __double2ll_rn((double)a * scale);
-        if (v) atomicAdd((unsigned long long *)&S.acc[g], (unsigned long long)v);
-    }
+    // two node pairs a lane halve the particle loads per pair: taken where the wider
+    // groups compute no extra nodes and their partial sums fit the buffer
+    const int n64 = (R + 63) >> 6, n128 = (R + 127) >> 7;
+    if (2 * n128 == n64 && (n128 >= DEP_WARPS || n128 * 128 <= DEP2_PART))
+        dep2_nodes<2>(S, n, g_lo, R, cosf, es, rsc, rwn, part);
+    else
+        dep2_nodes<1>(S, n, g_lo, R, cosf, es, rsc, rwn, part);
 }
 
 __global__ void __launch_bounds__(DEP_THREADS) deposit_chunk_x2_kernel(DepSrc<float> S)
