@@ -265,6 +265,8 @@ __device__ void deposit_chunk_body(const DepSrc<T> &S, int64_t chunk, DepRec<T> 
 //    angle and (w n 2^-K, w n 2^-K); three multiply-adds per pair.
 // ---------------------------------------------------------------------------
 #define DEP2_PART 512
+#define DEP2_UNROLL_P1 4
+#define DEP2_UNROLL_P2 8
 
 // node phase of the packed deposit: each lane owns P pairs of nodes, so a warp pass
 // covers 64 P consecutive nodes of the chunk's range [g_lo, g_lo + R); with fewer
@@ -275,6 +277,7 @@ __device__ __forceinline__ void dep2_nodes(const DepSrc<float> &S, int n, int g_
                                            const float4 *rsc, const float2 *rwn, float *part)
 {
     constexpr int GW = 64 * P;
+    constexpr int U = P == 2 ? DEP2_UNROLL_P2 : DEP2_UNROLL_P1;  // particle loop unrolling
     const int Ng = S.Ng;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ngroups = (R + GW - 1) / GW;
@@ -313,7 +316,7 @@ __device__ __forceinline__ void dep2_nodes(const DepSrc<float> &S, int n, int g_
 #pragma unroll
         for (int q = 0; q < P; ++q) acc[q] = kde_pk(0.f, 0.f);
         if (cosf) {
-#pragma unroll 4
+#pragma unroll U
             for (int p = p0; p < p1; ++p) {
                 const float4 r4 = rsc[p];
                 const float2 w2 = rwn[p];
@@ -324,7 +327,7 @@ __device__ __forceinline__ void dep2_nodes(const DepSrc<float> &S, int n, int g_
                     acc[q] = kde_fma2(kde_ex22(kde_fma2(SS[q], qs, kde_mul2(CC[q], qc))), w, acc[q]);
             }
         } else {
-#pragma unroll 4
+#pragma unroll U
             for (int p = p0; p < p1; ++p) {
                 const float4 r4 = rsc[p];
                 const float2 w2 = rwn[p];

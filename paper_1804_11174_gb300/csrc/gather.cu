@@ -185,10 +185,39 @@ __global__ void __launch_bounds__(GAT_THREADS) gather_kernel(GatherArgs<T> A)
 //    the particle's norm; three multiply-adds per pair instead of four.
 // ---------------------------------------------------------------------------
 #define GAT2_WARPS 4
-#define GAT2_NP 4
+#define GAT2_NP 4                 // particles a lane (an even number)
 #define GAT2_ITEM (32 * GAT2_NP)  // particles per warp
+#define GAT2_UNROLL 4             // node loop unrolling
+#define GAT2_UNROLL_DEEP 8        // node loop unrolling for windows of GAT2_DEEP_LEN nodes or more
+#define GAT2_DEEP_LEN 128
+#define GAT2_MINB 5               // launch bound: resident blocks per SM
+static constexpr int kGat2Unroll = GAT2_UNROLL;
+static constexpr int kGat2UnrollDeep = GAT2_UNROLL_DEEP;
 
-__global__ void __launch_bounds__(GAT2_WARPS * 32) gather2_kernel(GatherArgs<float> A)
+// the node loop of the packed gather over the window's two contiguous segments
+// [g0, e1) and [0, e2): NPP particle pairs a lane, U nodes unrolled
+template <int U, bool COS, int NPP>
+__device__ __forceinline__ void gat2_nodes(const float4 *SC, const float2 *FF, int g0, int e1, int e2,
+                                           const kde_f2 (&psP)[NPP], const kde_f2 (&pcP)[NPP], kde_f2 (&acc)[NPP])
+{
+    auto node = [&](int g) {
+        const float4 r4 = SC[g];
+        const float2 f = FF[g];
+        const kde_f2 S2 = kde_pk(r4.x, r4.y), C2 = kde_pk(r4.z, r4.w), F2 = kde_pk(f.x, f.y);
+#pragma unroll
+        for (int q = 0; q < NPP; ++q) {
+            const kde_f2 ev = kde_fma2(S2, psP[q], kde_mul2(C2, pcP[q]));
+            if (COS) acc[q] = kde_fma2(kde_ex22(ev), F2, acc[q]);  // 2^(K cos(x_j - x_g))
+            else acc[q] = kde_fma2(kde_ex2neg2(kde_mul2(ev, ev)), F2, acc[q]);  // 2^-(beta sin((x_j - x_g)/2))^2
+        }
+    };
+#pragma unroll U
+    for (int g = g0; g < e1; ++g) node(g);
+#pragma unroll U
+    for (int g = 0; g < e2; ++g) node(g);
+}
+
+__global__ void __launch_bounds__(GAT2_WARPS * 32, GAT2_MINB) gather2_kernel(GatherArgs<float> A)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ float kred[GAT2_WARPS];
@@ -291,43 +320,29 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32) gather2_kernel(GatherArgs<flo
     }
     int g0 = lo % Ng;
     if (g0 < 0) g0 += Ng;
-    const kde_f2 psA = kde_pk(ps[0], ps[1]), pcA = kde_pk(pc[0], pc[1]);
-    const kde_f2 psB = kde_pk(ps[2], ps[3]), pcB = kde_pk(pc[2], pc[3]);
-    kde_f2 accA = kde_pk(0.f, 0.f), accB = kde_pk(0.f, 0.f);
+    constexpr int NPP = GAT2_NP / 2;  // packed particle pairs a lane
+    kde_f2 psP[NPP], pcP[NPP], acc[NPP];
+#pragma unroll
+    for (int q = 0; q < NPP; ++q) {
+        psP[q] = kde_pk(ps[2 * q], ps[2 * q + 1]);
+        pcP[q] = kde_pk(pc[2 * q], pc[2 * q + 1]);
+        acc[q] = kde_pk(0.f, 0.f);
+    }
     const int e1 = g0 + len < Ng ? g0 + len : Ng;  // first segment [g0, e1), then [0, len - (e1 - g0))
     const int e2 = len - (e1 - g0);
-    auto node_half = [&](int g) {
-        const float4 q = SC[g];
-        const float2 f = FF[g];
-        const kde_f2 S2 = kde_pk(q.x, q.y), C2 = kde_pk(q.z, q.w), F2 = kde_pk(f.x, f.y);
-        const kde_f2 svA = kde_fma2(S2, psA, kde_mul2(C2, pcA));
-        const kde_f2 svB = kde_fma2(S2, psB, kde_mul2(C2, pcB));
-        accA = kde_fma2(kde_ex2neg2(kde_mul2(svA, svA)), F2, accA);
-        accB = kde_fma2(kde_ex2neg2(kde_mul2(svB, svB)), F2, accB);
-    };
-    auto node_cos = [&](int g) {
-        const float4 q = SC[g];
-        const float2 f = FF[g];
-        const kde_f2 S2 = kde_pk(q.x, q.y), C2 = kde_pk(q.z, q.w), F2 = kde_pk(f.x, f.y);
-        const kde_f2 evA = kde_fma2(S2, psA, kde_mul2(C2, pcA));
-        const kde_f2 evB = kde_fma2(S2, psB, kde_mul2(C2, pcB));
-        accA = kde_fma2(kde_ex22(evA), F2, accA);
-        accB = kde_fma2(kde_ex22(evB), F2, accB);
-    };
+    // long windows take the deeper unrolling (more exp2 in flight), short ones the
+    // shallower (less remainder work)
+    const bool deep = len >= GAT2_DEEP_LEN;
     if (cosf) {
-#pragma unroll 2
-        for (int g = g0; g < e1; ++g) node_cos(g);
-#pragma unroll 2
-        for (int g = 0; g < e2; ++g) node_cos(g);
+        if (deep) gat2_nodes<kGat2UnrollDeep, true, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
+        else gat2_nodes<kGat2Unroll, true, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
     } else {
-#pragma unroll 2
-        for (int g = g0; g < e1; ++g) node_half(g);
-#pragma unroll 2
-        for (int g = 0; g < e2; ++g) node_half(g);
+        if (deep) gat2_nodes<kGat2UnrollDeep, false, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
+        else gat2_nodes<kGat2Unroll, false, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
     }
     float ea[GAT2_NP];
-    kde_upk(accA, ea[0], ea[1]);
-    kde_upk(accB, ea[2], ea[3]);
+#pragma unroll
+    for (int q = 0; q < NPP; ++q) kde_upk(acc[q], ea[2 * q], ea[2 * q + 1]);
 #pragma unroll
     for (int h = 0; h < GAT2_NP; ++h) {
         if (!valid[h]) continue;
