@@ -99,7 +99,7 @@ struct kde_ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     std::string err;
-    unsigned int *d_status = nullptr;  // [0] code, [1] detail
+    unsigned int *d_status = nullptr;  // [0] code, [1] detail, [2] sort-scan ticket (zero between calls), [3] spare
     void *ws[WS_NSLOTS] = {};
     size_t ws_bytes[WS_NSLOTS] = {};
     // cached tables keyed by (Ng, precision): half-angle sines/cosines of the nodes

@@ -1,24 +1,28 @@
 // sort.cu -- stable counting sort of particles by bin (cell) index.
 //
-// Each warp owns a contiguous unit of `unit` particles (a multiple of 32).
-//   count   : warp-private shared histogram of its unit -> counts[bin][unit]
-//             (bin-major, so that the destination order of the segments is the
-//             flat index bin * nunits + unit)
-//   scan    : exclusive scan of the flat counts array: tiles of 4096 scanned
-//             in place plus a one-block scan of the tile totals
-//   scatter : the warp loads its unit up front, then ranks equal keys in each
+// A block of wpb warps owns a tile of wpb * unit particles; warp w of the block
+// owns the w-th contiguous unit of the tile (unit a multiple of 32).
+//   count   : the block's histogram of its tile (keys shared by several lanes of a
+//             warp are added once, by their leader) -> counts[bin][block]
+//             (bin-major, so that the destination order of the tiles' segments is
+//             the flat index bin * nblocks + block)
+//   scan    : exclusive scan of the flat counts array: tiles of 4096 scanned in
+//             place plus a one-block scan of the tile totals
+//   scatter : each warp histograms its unit in shared memory, the block turns the
+//             warps' histograms into destination starts (its segment start plus the
+//             counts of the earlier warps), then every warp ranks equal keys in each
 //             32-particle step with __match_any_sync and writes every particle
-//             (position and payloads) to its segment start + running count +
-//             rank.
+//             (position and payloads) to its start + rank.
 // The order inside a bin is the input order (stable), so results are
-// deterministic.  Units are small enough to keep thousands of warps in flight.
+// deterministic.  The count table has one entry per (bin, block) rather than per
+// (bin, warp), so it stays small next to the particle data.
 //
 // The same kernels in digit mode (key = a bit field of the code) give an LSD
 // radix sort of the full 32-bit codes: four stable passes of 8-bit digits.
 #include "common.cuh"
 
 #define SORT_MAX_COUNTS (1 << 22)
-#define SCAN_TILE 4096
+#define SCAN_TILE 2048
 #define SCAN_THREADS 256
 
 __device__ __forceinline__ int bin_of(uint32_t u, int nbins) { return (int)(((uint64_t)u * (uint64_t)nbins) >> 32); }
@@ -32,78 +36,103 @@ __device__ __forceinline__ int sort_key(uint32_t u, int nbins, int shift)
     return bin_of(u, nbins);
 }
 
+#define SORT_MAXR 4  // 32-particle steps whose loads are issued together
+#define COUNT_MAXR 8  // the same for the count kernel
+
+// the block's histogram of its tile; each thread issues the loads of COUNT_MAXR
+// steps before it uses any of them
 template <bool DIGIT>
 __global__ void sort_count_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int shift, int unit,
-                                  int nunits, unsigned int *counts)
+                                  int nblk, unsigned int *counts)
 {
     extern __shared__ unsigned int hist[];
-    const int wpb = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int un = blockIdx.x * wpb + warp;
-    unsigned int *h = hist + (size_t)warp * nbins;
-    for (int b = lane; b < nbins; b += 32) h[b] = 0;
-    __syncwarp();
-    if (un >= nunits) return;
-    const int64_t i0 = (int64_t)un * unit, i1 = i0 + unit < N ? i0 + unit : N;
-    for (int64_t i = i0 + lane; i < i1; i += 32) atomicAdd(&h[sort_key<DIGIT>(u[i], nbins, shift)], 1u);
-    __syncwarp();
-    for (int b = lane; b < nbins; b += 32) counts[(size_t)b * nunits + un] = h[b];
+    const int lane = threadIdx.x & 31;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const int64_t tile = (int64_t)(blockDim.x >> 5) * unit;
+    const int64_t t0 = (int64_t)blockIdx.x * tile, t1 = t0 + tile < N ? t0 + tile : N;
+    for (int64_t c0 = t0 + (threadIdx.x & ~31); c0 < t1; c0 += (int64_t)blockDim.x * COUNT_MAXR) {
+        uint32_t uu[COUNT_MAXR];
+#pragma unroll
+        for (int r = 0; r < COUNT_MAXR; ++r) {
+            const int64_t i = c0 + (int64_t)r * blockDim.x + lane;
+            uu[r] = i < t1 ? u[i] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < COUNT_MAXR; ++r) {
+            const int64_t i = c0 + (int64_t)r * blockDim.x + lane;
+            const int key = i < t1 ? sort_key<DIGIT>(uu[r], nbins, shift) : -1;
+            const unsigned int peers = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (unsigned int)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) counts[(size_t)b * nblk + blockIdx.x] = hist[b];
 }
 
-// exclusive scan of each SCAN_TILE-element tile in place; tile totals out
-__global__ void __launch_bounds__(SCAN_THREADS) sort_scan_tiles_kernel(unsigned int *a, int64_t n, unsigned int *tot)
+// exclusive scan of each SCAN_TILE-element tile in place (coalesced rounds of
+// SCAN_THREADS elements, all loads issued first); the tile totals go to tot, and the
+// block that finishes last (a ticket taken after a fence) scans them in place and
+// puts the ticket back to zero
+__global__ void __launch_bounds__(SCAN_THREADS) sort_scan_kernel(unsigned int *a, int64_t n, unsigned int *tot,
+                                                                 unsigned int *ticket)
 {
+    constexpr int R = SCAN_TILE / SCAN_THREADS;
     __shared__ unsigned int wsum[SCAN_THREADS / 32];
-    const int per = SCAN_TILE / SCAN_THREADS;  // 16 consecutive elements per thread
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * per;
-    unsigned int v[SCAN_TILE / SCAN_THREADS];
-    unsigned int s = 0;
+    __shared__ bool last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // block-wide exclusive scan of one value a thread; returns the prefix, adds the total to carry
+    auto block_scan = [&](unsigned int v, unsigned int &carry) -> unsigned int {
+        unsigned int inc = v;
 #pragma unroll
-    for (int k = 0; k < per; ++k) {
-        v[k] = base + k < n ? a[base + k] : 0u;
-        s += v[k];
-    }
-    // exclusive scan of the per-thread sums across the block
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned int inc = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        unsigned int woff = 0, total = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned int t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+            woff += w < warp ? wsum[w] : 0u;
+            total += wsum[w];
+        }
+        __syncthreads();
+        const unsigned int r = carry + woff + inc - v;
+        carry += total;
+        return r;
+    };
+    const int64_t t0 = (int64_t)blockIdx.x * SCAN_TILE;
+    unsigned int v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = t0 + (int64_t)r * SCAN_THREADS + tid;
+        v[r] = i < n ? a[i] : 0u;
     }
-    if (lane == 31) wsum[warp] = inc;
+    unsigned int carry = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = t0 + (int64_t)r * SCAN_THREADS + tid;
+        const unsigned int x = block_scan(v[r], carry);
+        if (i < n) a[i] = x;
+    }
+    if (tid == 0) {
+        tot[blockIdx.x] = carry;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
-    unsigned int woff = 0, total = 0;
-    for (int w = 0; w < SCAN_THREADS / 32; ++w) {
-        if (w < warp) woff += wsum[w];
-        total += wsum[w];
+    if (!last) return;
+    __threadfence();
+    const int nt = (int)gridDim.x;
+    unsigned int c2 = 0;
+    for (int r0 = 0; r0 < nt; r0 += SCAN_THREADS) {
+        const int i = r0 + tid;
+        const unsigned int x = i < nt ? ((volatile unsigned int *)tot)[i] : 0u;
+        const unsigned int y = block_scan(x, c2);
+        if (i < nt) tot[i] = y;
     }
-    unsigned int run = woff + inc - s;
-#pragma unroll
-    for (int k = 0; k < per; ++k) {
-        if (base + k < n) a[base + k] = run;
-        run += v[k];
-    }
-    if (threadIdx.x == 0) tot[blockIdx.x] = total;
-}
-
-// exclusive scan of the tile totals (at most 1024) in one block
-__global__ void sort_scan_totals_kernel(unsigned int *tot, int ntiles)
-{
-    __shared__ unsigned int wsum[32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    unsigned int v = t < ntiles ? tot[t] : 0u;
-    unsigned int inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned int x = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += x;
-    }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    unsigned int woff = 0;
-    for (int w = 0; w < warp; ++w) woff += wsum[w];
-    if (t < ntiles) tot[t] = woff + inc - v;
+    if (tid == 0) *ticket = 0u;
 }
 
 struct ScatterPl {
@@ -113,30 +142,71 @@ struct ScatterPl {
     int n;
 };
 
-#define SORT_MAXR 8  // 32-particle steps loaded ahead per chunk of the unit
-
-template <bool DIGIT>
+// NPL payload arrays (4- or 8-byte elements) move with the keys; every load of a
+// chunk of SORT_MAXR steps is issued before the chunk is ranked and written
+template <bool DIGIT, int NPL>
 __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int shift, int unit,
-                                    int nunits, const unsigned int *__restrict__ seg,
+                                    int nblk, const unsigned int *__restrict__ seg,
                                     const unsigned int *__restrict__ tiles, uint32_t *u_out, ScatterPl pl,
                                     uint32_t *perm_out)
 {
     extern __shared__ unsigned int hist[];
     const int wpb = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int un = blockIdx.x * wpb + warp;
     unsigned int *h = hist + (size_t)warp * nbins;
-    if (un >= nunits) return;
-    for (int b = lane; b < nbins; b += 32) h[b] = 0;
-    __syncwarp();
+    for (int b = threadIdx.x; b < wpb * nbins; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const int64_t i0 = ((int64_t)blockIdx.x * wpb + warp) * unit;
+    const int64_t i1 = i0 + unit < N ? i0 + unit : N;  // empty when i0 >= N
     const unsigned int lt = (1u << lane) - 1u;
-    const int64_t i0 = (int64_t)un * unit, i1 = i0 + unit < N ? i0 + unit : N;
+    // the warp's histogram of its unit (one leader per key and step; steps ordered by __syncwarp)
     for (int64_t c0 = i0; c0 < i1; c0 += 32 * SORT_MAXR) {
         uint32_t uu[SORT_MAXR];
 #pragma unroll
         for (int r = 0; r < SORT_MAXR; ++r) {
             const int64_t i = c0 + r * 32 + lane;
             uu[r] = i < i1 ? u[i] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < SORT_MAXR; ++r) {
+            const int64_t i = c0 + r * 32 + lane;
+            const int key = i < i1 ? sort_key<DIGIT>(uu[r], nbins, shift) : -1;
+            const unsigned int peers = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && lane == __ffs(peers) - 1) h[key] += __popc(peers);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // destination starts: the block's segment start of each bin plus the earlier warps' counts
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        const size_t flat = (size_t)b * nblk + blockIdx.x;
+        unsigned int run = seg[flat] + tiles[flat / SCAN_TILE];
+        for (int w = 0; w < wpb; ++w) {
+            const unsigned int t = hist[(size_t)w * nbins + b];
+            hist[(size_t)w * nbins + b] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    for (int64_t c0 = i0; c0 < i1; c0 += 32 * SORT_MAXR) {
+        uint32_t uu[SORT_MAXR];
+        uint32_t lo[NPL > 0 ? NPL : 1][SORT_MAXR], hi[NPL > 0 ? NPL : 1][SORT_MAXR];
+#pragma unroll
+        for (int r = 0; r < SORT_MAXR; ++r) {
+            const int64_t i = c0 + r * 32 + lane;
+            const bool ok = i < i1;
+            uu[r] = ok ? u[i] : 0u;
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                if (pl.elem[k] == 8) {
+                    const uint2 w = ok ? ((const uint2 *)pl.src[k])[i] : make_uint2(0u, 0u);
+                    lo[k][r] = w.x;
+                    hi[k][r] = w.y;
+                } else {
+                    lo[k][r] = ok ? ((const uint32_t *)pl.src[k])[i] : 0u;
+                    hi[k][r] = 0u;
+                }
+            }
         }
 #pragma unroll
         for (int r = 0; r < SORT_MAXR; ++r) {
@@ -151,12 +221,12 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
             if (valid && rank == 0) h[key] = before + __popc(peers);
             __syncwarp();
             if (valid) {
-                const size_t flat = (size_t)key * nunits + un;
-                const size_t dst = (size_t)seg[flat] + tiles[flat / SCAN_TILE] + before + rank;
+                const unsigned int dst = before + rank;
                 u_out[dst] = uu[r];
-                for (int k = 0; k < pl.n; ++k) {
-                    if (pl.elem[k] == 8) ((uint64_t *)pl.dst[k])[dst] = ((const uint64_t *)pl.src[k])[i];
-                    else ((uint32_t *)pl.dst[k])[dst] = ((const uint32_t *)pl.src[k])[i];
+#pragma unroll
+                for (int k = 0; k < NPL; ++k) {
+                    if (pl.elem[k] == 8) ((uint2 *)pl.dst[k])[dst] = make_uint2(lo[k][r], hi[k][r]);
+                    else ((uint32_t *)pl.dst[k])[dst] = lo[k][r];
                 }
                 if (perm_out) perm_out[dst] = (uint32_t)i;
             }
@@ -164,40 +234,47 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
     }
 }
 
+template <bool DIGIT, int NPL>
+static void set_scatter_attr(kde_ctx *ctx)
+{
+    cudaFuncSetAttribute(sort_scatter_kernel<DIGIT, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+}
+
 template <bool DIGIT>
 static kde_status sort_pass(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, int shift, uint32_t *u_out,
                             const SortPayload *pl, int npl, uint32_t *perm_out)
 {
+    // warps per block: the scatter's warp-private histograms must fit the shared-memory budget
+    int wpb = 8;
+    while (wpb > 1 && (size_t)wpb * nbins * 4 > 96 * 1024) wpb >>= 1;
     int unit = 256;
-    while ((int64_t)nbins * ((N + unit - 1) / unit) > SORT_MAX_COUNTS) unit *= 2;
-    const int nunits = (int)((N + unit - 1) / unit);
-    const int64_t ncounts = (int64_t)nbins * nunits;
+    while ((int64_t)nbins * ((N + (int64_t)wpb * unit - 1) / ((int64_t)wpb * unit)) > SORT_MAX_COUNTS) unit *= 2;
+    const int nblk = (int)((N + (int64_t)wpb * unit - 1) / ((int64_t)wpb * unit));
+    const int64_t ncounts = (int64_t)nbins * nblk;
     const int ntiles = (int)((ncounts + SCAN_TILE - 1) / SCAN_TILE);
     unsigned int *counts = (unsigned int *)kde_ws(ctx, WS_SORT_COUNTS, (size_t)ncounts * 4);
     unsigned int *tiles = (unsigned int *)kde_ws(ctx, WS_SORT_STARTS, (size_t)ntiles * 4);
     if (!counts || !tiles) return KDE_ENOMEM;
-    // warps per block: warp-private histograms must fit the shared-memory budget
-    int wpb = 8;
-    while (wpb > 1 && (size_t)wpb * nbins * 4 > 96 * 1024) wpb >>= 1;
     const size_t smem = (size_t)wpb * nbins * 4;
     static bool attr_set = false;
     if (!attr_set) {
         KDE_CUDA(ctx,
                  cudaFuncSetAttribute(sort_count_kernel<DIGIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
                  "sort attribute");
-        KDE_CUDA(ctx,
-                 cudaFuncSetAttribute(sort_scatter_kernel<DIGIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      96 * 1024),
-                 "sort attribute");
+        set_scatter_attr<DIGIT, 0>(ctx);
+        set_scatter_attr<DIGIT, 1>(ctx);
+        set_scatter_attr<DIGIT, 2>(ctx);
+        set_scatter_attr<DIGIT, 3>(ctx);
+        set_scatter_attr<DIGIT, 4>(ctx);
+        KDE_CUDA(ctx, cudaGetLastError(), "sort attribute");
         attr_set = true;
     }
-    const int blocks = (nunits + wpb - 1) / wpb;
-    sort_count_kernel<DIGIT><<<blocks, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nunits, counts);
+    KdeProfScope _ps(ctx, PROF_SORT);  // the whole pass: count, scan and scatter
+    sort_count_kernel<DIGIT><<<nblk, wpb * 32, (size_t)nbins * 4, ctx->stream>>>(u, N, nbins, shift, unit, nblk,
+                                                                                counts);
     KDE_LAUNCHED(ctx, "sort_count_kernel");
-    sort_scan_tiles_kernel<<<ntiles, SCAN_THREADS, 0, ctx->stream>>>(counts, ncounts, tiles);
-    KDE_LAUNCHED(ctx, "sort_scan_tiles_kernel");
-    sort_scan_totals_kernel<<<1, 1024, 0, ctx->stream>>>(tiles, ntiles);
-    KDE_LAUNCHED(ctx, "sort_scan_totals_kernel");
+    sort_scan_kernel<<<ntiles, SCAN_THREADS, 0, ctx->stream>>>(counts, ncounts, tiles, ctx->d_status + 2);
+    KDE_LAUNCHED(ctx, "sort_scan_kernel");
     ScatterPl sp{};
     sp.n = npl;
     for (int k = 0; k < npl; ++k) {
@@ -205,10 +282,17 @@ static kde_status sort_pass(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbin
         sp.dst[k] = pl[k].dst;
         sp.elem[k] = pl[k].elem;
     }
-    {
-        KdeProfScope _ps(ctx, PROF_SORT);
-        sort_scatter_kernel<DIGIT><<<blocks, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nunits, counts,
-                                                                            tiles, u_out, sp, perm_out);
+    switch (npl) {
+    case 0: sort_scatter_kernel<DIGIT, 0><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
+                                                                                tiles, u_out, sp, perm_out); break;
+    case 1: sort_scatter_kernel<DIGIT, 1><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
+                                                                                tiles, u_out, sp, perm_out); break;
+    case 2: sort_scatter_kernel<DIGIT, 2><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
+                                                                                tiles, u_out, sp, perm_out); break;
+    case 3: sort_scatter_kernel<DIGIT, 3><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
+                                                                                tiles, u_out, sp, perm_out); break;
+    default: sort_scatter_kernel<DIGIT, 4><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
+                                                                                 tiles, u_out, sp, perm_out); break;
     }
     KDE_LAUNCHED(ctx, "sort_scatter_kernel");
     return KDE_OK;
