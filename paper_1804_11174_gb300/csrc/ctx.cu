@@ -140,6 +140,20 @@ const void *kde_green_table(kde_ctx *ctx, int Ng, double L, bool fd, bool f64)
     return p;
 }
 
+// the width-normalisation table of kde_norm_tab: q(t) = I0e(e^t) sqrt(1 + 2 pi e^t) and
+// h dq/dt (central difference of step 1e-4 in t, error ~1e-9) at t = T0 + i h, in FP64
+__global__ void norm_tab_kernel(float2 *tab)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= KDE_NTAB_N) return;
+    const double t = KDE_NTAB_T0 + i / KDE_NTAB_INVH, d = 1e-4;
+    auto q = [](double tt) {
+        const double k = exp(tt);
+        return kde_i0e(k) * sqrt(1.0 + KDE_TWO_PI * k);
+    };
+    tab[i] = make_float2((float)q(t), (float)((q(t + d) - q(t - d)) / (2.0 * d) / KDE_NTAB_INVH));
+}
+
 // ---------------------------------------------------------------------------
 // C ABI: context
 // ---------------------------------------------------------------------------
@@ -154,8 +168,16 @@ extern "C" kde_status kde_create(kde_ctx **out, int device, void *stream)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 4 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 4 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->norm_tab, KDE_NTAB_N * sizeof(float2));
+    if (e == cudaSuccess) {
+        norm_tab_kernel<<<(KDE_NTAB_N + 255) / 256, 256, 0, ctx->stream>>>(ctx->norm_tab);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->norm_tab) cudaFree(ctx->norm_tab);
         delete ctx;
         return KDE_ECUDA;
     }
@@ -173,6 +195,7 @@ extern "C" kde_status kde_destroy(kde_ctx *ctx)
     for (auto &kv : ctx->node_tab) cudaFree(kv.second);
     for (auto &kv : ctx->green_tab) cudaFree(kv.second);
     if (ctx->ad_tab) cudaFree(ctx->ad_tab);
+    if (ctx->norm_tab) cudaFree(ctx->norm_tab);
     if (ctx->d_status) cudaFree(ctx->d_status);
     for (auto &p : ctx->prof) {
         cudaEventDestroy(p.second.first);

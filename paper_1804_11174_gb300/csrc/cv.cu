@@ -107,7 +107,7 @@ __device__ __forceinline__ float reach_kappa(uint32_t gap)
 __global__ void __launch_bounds__(CV_T)
     cv_prep_kernel(const uint32_t *u, const float *kr, int64_t N, int bin_shift, float2 *sc, uint2 *tile_u,
                    float *tile_kmin, float *k2rel, unsigned int *kr_bits, CandList cl, float *lnorm,
-                   unsigned int *status)
+                   unsigned int *status, const float2 *ntab)
 {
     __shared__ float skmin[CV_WARPS];
     const int64_t j = (int64_t)blockIdx.x * CV_T + threadIdx.x;
@@ -133,7 +133,9 @@ __global__ void __launch_bounds__(CV_T)
         if (valid) {
             atomicMax(&kr_bits[0], __float_as_uint(k));
             atomicMin(&kr_bits[1], __float_as_uint(k));
-            for (int q = 0; q < cl.n; ++q) lnorm[(size_t)q * N + j] = (float)log2(kde_norm(cl.k[q] * (double)k));
+            // log2 of the tabulated FP32 norm (FP64 Bessel series per particle and candidate are slow here)
+            for (int q = 0; q < cl.n; ++q)
+                lnorm[(size_t)q * N + j] = log2f(kde_norm_tab(ntab, (float)(cl.k[q] * (double)k)));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) km = fminf(km, __shfl_xor_sync(0xffffffffu, km, o));
@@ -833,7 +835,7 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
     int bin_shift = 32;
     for (int nb = nbins; nb > 1; nb >>= 1) --bin_shift;
     cv_prep_kernel<<<NT, CV_T, 0, ctx->stream>>>(us, krs, N, bin_shift, sc, tile_u, tile_kmin, k2rel, krmax, cl,
-                                                  lnorm, ctx->d_status);
+                                                  lnorm, ctx->d_status, ctx->norm_tab);
     KDE_LAUNCHED(ctx, "cv_prep_kernel");
 
     // pair totals
@@ -991,7 +993,7 @@ __global__ void adapt_logsum_kernel(const float *loo, int64_t N, double K0, doub
 template <typename T>
 __global__ void adapt_apply_kernel(const float *loo, int64_t N, double xs, const double *kstar_dev, double kstar_h,
                                    const double *part, double alpha, double kmin, double kmax, T *kappa_out,
-                                   T *norm_out)
+                                   T *norm_out, const float2 *ntab)
 {
     __shared__ double s_logg, s_K0, s_ks;
     if (threadIdx.x == 0) {
@@ -1011,7 +1013,11 @@ __global__ void adapt_apply_kernel(const float *loo, int64_t N, double xs, const
     double k = s_ks * exp(2.0 * alpha * (log(f) - s_logg));
     k = k < kmin ? kmin : (k > kmax ? kmax : k);
     kappa_out[i] = (T)k;
-    if (norm_out) norm_out[i] = (T)kde_norm((double)(T)k);
+    if (norm_out) {
+        // FP32 widths take the tabulated norm, FP64 widths the FP64 Bessel series
+        if constexpr (sizeof(T) == 4) norm_out[i] = (T)kde_norm_tab(ntab, (float)k);
+        else norm_out[i] = (T)kde_norm((double)(T)k);
+    }
 }
 
 // the log-mean needs K0 = (2 pi / L) norm(kappa*) before kappa* is known on the host
@@ -1045,10 +1051,12 @@ kde_status kde_adapt_device(kde_ctx *ctx, const float *loo, int64_t N, double L,
     unsigned grid = (unsigned)((N + 255) / 256);
     if (f64)
         adapt_apply_kernel<double><<<grid, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part, alpha, kmin,
-                                                                   kmax, (double *)kappa_out, (double *)norm_out);
+                                                                   kmax, (double *)kappa_out, (double *)norm_out,
+                                                                   ctx->norm_tab);
     else
         adapt_apply_kernel<float><<<grid, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part, alpha, kmin,
-                                                                  kmax, (float *)kappa_out, (float *)norm_out);
+                                                                  kmax, (float *)kappa_out, (float *)norm_out,
+                                                                  ctx->norm_tab);
     KDE_LAUNCHED(ctx, "adapt_apply_kernel");
     return KDE_OK;
 }
@@ -1237,7 +1245,7 @@ extern "C" kde_status kde_cv_cic(kde_ctx *ctx, const uint32_t *u, int64_t N, dou
     int bin_shift = 32;
     for (int nb = nbins; nb > 1; nb >>= 1) --bin_shift;
     cv_prep_kernel<<<NT, CV_T, 0, ctx->stream>>>(us, nullptr, N, bin_shift, sc, tile_u, nullptr, nullptr, nullptr,
-                                                  CandList{}, nullptr, ctx->d_status);
+                                                  CandList{}, nullptr, ctx->d_status, ctx->norm_tab);
     KDE_LAUNCHED(ctx, "cv_prep_kernel");
     const double reach_d = 2.0 * hmax / L * 4294967296.0;  // B_3 support in codes
     const uint32_t reach = reach_d >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)ceil(reach_d);

@@ -50,6 +50,7 @@ template <typename T> struct DepSrc {
     double norm_bound;
     unsigned int *status;
     int scale_exp;  // KDE_ES_FROM_BOUND, or the exponent es of the fixed-point scale 2^es
+    const float2 *ntab;  // FP32 norm table (kde_norm_tab) for per-particle widths without norms, or nullptr
 };
 
 #define KDE_ES_FROM_BOUND (-100000)
@@ -448,7 +449,7 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
         float nm;
         if (S.lnorm) nm = exp2f(S.lnorm[j]);
         else if (S.norm) nm = S.norm[j];
-        else if (S.kappa) nm = (float)kde_norm((double)k);
+        else if (S.kappa) nm = S.ntab ? kde_norm_tab(S.ntab, k) : (float)kde_norm((double)k);
         else nm = S.norm_u;
         const float wj = S.w ? S.w[j] : S.w_u;
         const float wn = wj * S.coef * nm;
@@ -559,6 +560,7 @@ kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T
     S.norm_bound = norm_bound;
     S.status = ctx->d_status;
     S.scale_exp = KDE_ES_FROM_BOUND;
+    S.ntab = ctx->norm_tab;
     unsigned grid = (unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK);
     {
         KdeProfScope _ps(ctx, PROF_DEPOSIT);

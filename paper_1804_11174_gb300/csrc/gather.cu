@@ -53,6 +53,7 @@ template <typename T> struct GatherArgs {
     double *kstar_out;
     double dx;
     unsigned int *status;
+    const float2 *ntab;  // FP32 norm table (kde_norm_tab): per-particle widths without norms
 };
 
 __device__ __forceinline__ int window_nodes_g(float kappa, int Ng, float xcut)
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, GAT2_MINB) gather2_kernel(Gat
             k = (float)KDE_KAPPA_MAX;
         }
         kap[h] = k;
-        nm[h] = A.norm ? (valid[h] ? A.norm[j] : 0.f) : (A.kappa ? (float)kde_norm((double)k) : A.norm_u);
+        nm[h] = A.norm ? (valid[h] ? A.norm[j] : 0.f) : (A.kappa ? kde_norm_tab(A.ntab, k) : A.norm_u);
         if (valid[h]) {
             kmax = fmaxf(kmax, k);
             const int cell = kde_cell(uu[h], Ng);
@@ -367,6 +368,7 @@ static kde_status launch_gather2(kde_ctx *ctx, GatherArgs<float> &A)
     if (!nodes) return KDE_ENOMEM;
     A.nodes = (const float2 *)nodes;
     A.status = ctx->d_status;
+    A.ntab = ctx->norm_tab;
     const size_t smem = (size_t)A.Ng * (sizeof(float4) + sizeof(float2));
     static bool attr = false;
     if (!attr) {

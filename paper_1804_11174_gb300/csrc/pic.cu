@@ -13,7 +13,7 @@
 #include "common.cuh"
 
 template <typename T>
-__global__ void norm_from_kappa_kernel(const T *kappa, int64_t N, T *norm, unsigned int *status)
+__global__ void norm_from_kappa_kernel(const T *kappa, int64_t N, T *norm, unsigned int *status, const float2 *ntab)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -22,7 +22,9 @@ __global__ void norm_from_kappa_kernel(const T *kappa, int64_t N, T *norm, unsig
         kde_flag(status, KDE_DEV_KAPPA_RANGE, (unsigned)i);
         k = KDE_KAPPA_MAX;
     }
-    norm[i] = (T)kde_norm(k);
+    // FP32 state: the tabulated norm; FP64 state: the FP64 Bessel series
+    if constexpr (sizeof(T) == 4) norm[i] = (T)kde_norm_tab(ntab, (float)k);
+    else norm[i] = (T)kde_norm(k);
 }
 
 // standard PIC with a B-spline shape: deposit, Poisson, energy, gather + push
@@ -90,8 +92,8 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
     double h_ad = adsched ? 1.0 / sqrt(st->kappa_uniform) : 0.0;
 
     if (per) {
-        norm_from_kappa_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>((const T *)st->kappa, N,
-                                                                                      norm_arr, ctx->d_status);
+        norm_from_kappa_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
+            (const T *)st->kappa, N, norm_arr, ctx->d_status, ctx->norm_tab);
         KDE_LAUNCHED(ctx, "norm_from_kappa_kernel");
     }
     const double coef = KDE_TWO_PI / L;

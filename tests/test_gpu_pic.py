@@ -58,6 +58,23 @@ def test_one_step(ctx, kp, oracle, per_particle):
     assert np.linalg.norm(vv - r["v"]) <= 1e-5 * np.linalg.norm(r["v"])
 
 
+def test_fp32_width_norm_table(ctx, kp, oracle):
+    # FP32 states take the normalisation 1 / (2 pi I0e(kappa)) of each width from a table
+    # (cubic Hermite in ln kappa, built once per context from the FP64 Bessel series);
+    # over the whole width range (1e-9, 1e6] it stays within 5e-7 of the FP64 value
+    L, Ng, dt, N = 4 * math.pi, 64, 0.1, 4096
+    u, v = I.landau_load(9, N, L, 0.05, 1.0)
+    k = np.exp(np.linspace(math.log(1e-9), math.log(1e6), N)).astype(np.float32)
+    k[-1] = 1e6
+    st = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 1, kappa=k)
+    ctx.pic_step(st, 1)
+    ctx.sync()
+    ks = st.kappa.double().cpu().numpy()
+    ref = np.array([1.0 / (2 * math.pi * oracle.i0e(x)) for x in ks])
+    rel = np.abs(st.kappa_norm.double().cpu().numpy() / ref - 1)
+    assert rel.max() <= 5e-7, rel.max()
+
+
 def test_langmuir_fp64_width_once(ctx, kp, oracle):
     # cold Langmuir wave, FP64, 200 steps, width chosen once at t = 0 by CV over
     # 16 candidates in [1, 1e3]
