@@ -386,35 +386,35 @@ struct CvFast {
     int splits;
     float kk[CVF_MAXC];  // -2 log2(e) kappa_c
     float k[CVF_MAXC];   // kappa_c
+    kde_f2 kk2[CVF_MAXC / 2];  // (kk[2p], kk[2p + 1]) as packed pairs
 };
 
+// candidates in packed pairs: per column one exponent s^2, then for each pair of
+// candidates one f32x2 multiply, two exp2 and one f32x2 add (as a multiply-add by 1)
 template <int NG>
 __device__ __forceinline__ void cvf_columns(const float2 *__restrict__ t, int ncol, float2 me, int self,
-                                            float (&acc)[CVF_MAXC], const CvFast &cf)
+                                            kde_f2 (&acc)[CVF_MAXC / 2], const CvFast &cf)
 {
+    const kde_f2 one2 = kde_pk(1.f, 1.f);
+    auto column = [&](int i) {
+        const float2 o = t[i];
+        const float s = me.x * o.y - me.y * o.x;
+        const float s2 = s * s;
+        const kde_f2 s22 = kde_pk(s2, s2);
+#pragma unroll
+        for (int p = 0; p < 2 * NG; ++p) acc[p] = kde_fma2(kde_ex22(kde_mul2(s22, cf.kk2[p])), one2, acc[p]);
+    };
     if (self < 0) {
 #pragma unroll 2
-        for (int i = 0; i < ncol; ++i) {
-            const float2 o = t[i];
-            const float s = me.x * o.y - me.y * o.x;
-            const float s2 = s * s;
-#pragma unroll
-            for (int q = 0; q < 4 * NG; ++q) acc[q] += kde_ex2(s2 * cf.kk[q]);
-        }
+        for (int i = 0; i < ncol; ++i) column(i);
     } else {
-        for (int i = 0; i < ncol; ++i) {
-            if (i == self) continue;
-            const float2 o = t[i];
-            const float s = me.x * o.y - me.y * o.x;
-            const float s2 = s * s;
-#pragma unroll
-            for (int q = 0; q < 4 * NG; ++q) acc[q] += kde_ex2(s2 * cf.kk[q]);
-        }
+        for (int i = 0; i < ncol; ++i)
+            if (i != self) column(i);
     }
 }
 
 __device__ __forceinline__ void cvf_dispatch(int ng, const float2 *t, int ncol, float2 me, int self,
-                                             float (&acc)[CVF_MAXC], const CvFast &cf)
+                                             kde_f2 (&acc)[CVF_MAXC / 2], const CvFast &cf)
 {
     switch (ng) {
 #define CVF_CASE(G) \
@@ -471,9 +471,9 @@ __global__ void __launch_bounds__(CV_T, 2)
         const bool rvalid = j < N;
         const float2 me = sc[j];
         const uint2 ta = tile_u[a];
-        float acc[CVF_MAXC];
+        kde_f2 acc[CVF_MAXC / 2];
 #pragma unroll
-        for (int q = 0; q < CVF_MAXC; ++q) acc[q] = 0.f;
+        for (int p = 0; p < CVF_MAXC / 2; ++p) acc[p] = kde_pk(0.f, 0.f);
 
         Walk w{0, 0, 0};
         int cnt = 0;
@@ -516,11 +516,16 @@ __global__ void __launch_bounds__(CV_T, 2)
                 const float m = rvalid ? wgt : 0.0f;
                 float lo[32], hi[32];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    lo[q] = acc[q] * m;
-                    hi[q] = acc[q + 32] * m;
-                    acc[q] = 0.f;
-                    acc[q + 32] = 0.f;
+                for (int p = 0; p < 16; ++p) {
+                    float a0, a1, b0, b1;
+                    kde_upk(acc[p], a0, a1);
+                    kde_upk(acc[p + 16], b0, b1);
+                    lo[2 * p] = a0 * m;
+                    lo[2 * p + 1] = a1 * m;
+                    hi[2 * p] = b0 * m;
+                    hi[2 * p + 1] = b1 * m;
+                    acc[p] = kde_pk(0.f, 0.f);
+                    acc[p + 16] = kde_pk(0.f, 0.f);
                 }
                 const float r0 = warp_transpose_sum32(lo, lane);
                 const float r1 = warp_transpose_sum32(hi, lane);
@@ -867,6 +872,12 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
         for (int c = 0; c < n_cand; ++c) {
             cf.k[c] = cc.k[c];
             cf.kk[c] = (float)(-2.0 * KDE_LOG2E) * cc.k[c];
+        }
+        for (int p = 0; p < CVF_MAXC / 2; ++p) {
+            uint32_t lo, hi;
+            memcpy(&lo, &cf.kk[2 * p], 4);
+            memcpy(&hi, &cf.kk[2 * p + 1], 4);
+            cf.kk2[p] = (kde_f2)lo | ((kde_f2)hi << 32);
         }
         part = (double *)kde_ws(ctx, WS_CV_PART, (size_t)cf.nitems * n_cand * 8 + 64);
         if (!part) return KDE_ENOMEM;
