@@ -82,6 +82,7 @@ enum WsSlot {
     WS_AD_PART,
     WS_AD_OUT,
     WS_CV_GPAR,
+    WS_GREEN,
     WS_NSLOTS
 };
 

@@ -101,20 +101,39 @@ const void *kde_node_table(kde_ctx *ctx, int Ng, bool f64)
 // q_m = 2 pi m / L (spectral: E_m = rho_m / (i k_m)) or (2/dx) tan(pi m / Ng)
 // (the finite-difference scheme of Sec. III.A in Fourier form).  Pairing modes
 // m and -m gives the sine; the mean and, for even Ng, the Nyquist mode carry no
-// field.  Evaluated in FP64 with exact integer reduction of the angle.
-template <typename T>
-__global__ void green_kernel(T *G, int Ng, double L, int fd)
+// field.  Evaluated in FP64: first the tables sin(2 pi k / Ng), k < Ng, and 1/q_m,
+// then one block per d sums the M terms with the angle index m d mod Ng carried
+// exactly in integers.
+__global__ void green_tables_kernel(double *sinT, double *invq, int Ng, double L, int fd)
 {
-    int d = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= Ng) return;
-    int M = (Ng - 1) / 2;
-    double dx = L / Ng, acc = 0.0;
-    for (int m = 1; m <= M; ++m) {
-        long long r = ((long long)m * d) % Ng;
-        double q = fd ? (2.0 / dx) * tan(KDE_PI * m / Ng) : KDE_TWO_PI * m / L;
-        acc += 2.0 * sinpi(2.0 * (double)r / Ng) / q;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < Ng) sinT[k] = sinpi(2.0 * (double)k / Ng);
+    const int M = (Ng - 1) / 2;
+    if (k >= 1 && k <= M) invq[k] = 1.0 / (fd ? (2.0 * Ng / L) * tan(KDE_PI * k / Ng) : KDE_TWO_PI * k / L);
+}
+
+#define GREEN_THREADS 128
+template <typename T>
+__global__ void __launch_bounds__(GREEN_THREADS) green_kernel(T *G, int Ng, const double *sinT, const double *invq)
+{
+    __shared__ double red[GREEN_THREADS];
+    const int d = blockIdx.x, M = (Ng - 1) / 2;
+    const int m0 = 1 + threadIdx.x;
+    const int step = (int)(((long long)GREEN_THREADS * d) % Ng);
+    int r = (int)(((long long)m0 * d) % Ng);  // m d mod Ng for this thread's m
+    double acc = 0.0;
+    for (int m = m0; m <= M; m += GREEN_THREADS) {
+        acc += sinT[r] * invq[m];
+        r += step;
+        if (r >= Ng) r -= Ng;
     }
-    G[d] = (T)(acc / Ng);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = GREEN_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) G[d] = (T)(2.0 * red[0] / Ng);
 }
 
 const void *kde_green_table(kde_ctx *ctx, int Ng, double L, bool fd, bool f64)
@@ -130,8 +149,16 @@ const void *kde_green_table(kde_ctx *ctx, int Ng, double L, bool fd, bool f64)
         kde_fail(ctx, KDE_ENOMEM, "Green's function allocation failed");
         return nullptr;
     }
-    if (f64) green_kernel<double><<<(Ng + 127) / 128, 128, 0, ctx->stream>>>((double *)p, Ng, L, fd);
-    else green_kernel<float><<<(Ng + 127) / 128, 128, 0, ctx->stream>>>((float *)p, Ng, L, fd);
+    // scratch for the sine and 1/q tables (a slot of its own: no caller holds it)
+    double *sinT = (double *)kde_ws(ctx, WS_GREEN, (size_t)2 * KDE_MAX_NG * 8);
+    if (!sinT) {
+        cudaFree(p);
+        return nullptr;
+    }
+    double *invq = sinT + KDE_MAX_NG;
+    green_tables_kernel<<<(Ng + 127) / 128, 128, 0, ctx->stream>>>(sinT, invq, Ng, L, fd ? 1 : 0);
+    if (f64) green_kernel<double><<<Ng, GREEN_THREADS, 0, ctx->stream>>>((double *)p, Ng, sinT, invq);
+    else green_kernel<float><<<Ng, GREEN_THREADS, 0, ctx->stream>>>((float *)p, Ng, sinT, invq);
     if (cudaGetLastError() != cudaSuccess) {
         kde_fail(ctx, KDE_ECUDA, "Green's function kernel launch failed");
         return nullptr;
@@ -247,7 +274,7 @@ extern "C" kde_status kde_reserve(kde_ctx *ctx, int64_t N, int32_t Ng, int32_t n
         {WS_SORT_P0, (size_t)Np * 8}, {WS_SORT_P1, (size_t)Np * 8}, {WS_SORT_P2, (size_t)Np * 8},
         {WS_SORT_P3, (size_t)Np * 4}, {WS_SORT_PERM, (size_t)Np * 4}, {WS_NORM, (size_t)Np * 8},
         {WS_ACC, (size_t)(n_cand > 0 ? n_cand : 1) * 8192 * 8 + 64}, {WS_GRID0, KDE_MAX_NG * 8},
-        {WS_GRID1, KDE_MAX_NG * 8}, {WS_WMAX, 64}, {WS_PIC_E, (size_t)Np * 4}, {WS_PIC_LOO, (size_t)Np * 4},
+        {WS_GRID1, KDE_MAX_NG * 8}, {WS_GREEN, 2 * KDE_MAX_NG * 8}, {WS_WMAX, 64}, {WS_PIC_E, (size_t)Np * 4}, {WS_PIC_LOO, (size_t)Np * 4},
         {WS_PIC_KS, 64}};
     for (auto &b : big)
         if (!kde_ws(ctx, (WsSlot)b[0], b[1])) return KDE_ENOMEM;

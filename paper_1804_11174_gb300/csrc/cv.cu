@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(CV_T) cv_pairs_kernel(CvPairArgs A, CvCands cc
             const float wgt = (!SCALE && !diag) ? 2.0f : 1.0f;
             const float2 *t = buf[cur];
             for (int cg = 0; cg < nact; cg += CV_G) {
+                // candidates in packed pairs: exponent s^2 kk + ll, two exp2, one add per pair
                 float kk[CV_G], ll[CV_G], acc[CV_G];
 #pragma unroll
                 for (int q = 0; q < CV_G; ++q) {
@@ -316,27 +317,33 @@ __global__ void __launch_bounds__(CV_T) cv_pairs_kernel(CvPairArgs A, CvCands cc
                         kk[q] = (float)(-2.0 * KDE_LOG2E) * cc.k[c];
                         ll[q] = 0.f;
                     }
-                    acc[q] = 0.f;
                 }
+                kde_f2 kk2[CV_G / 2], ll2[CV_G / 2], acc2[CV_G / 2];
+#pragma unroll
+                for (int p = 0; p < CV_G / 2; ++p) {
+                    kk2[p] = kde_pk(kk[2 * p], kk[2 * p + 1]);
+                    ll2[p] = kde_pk(ll[2 * p], ll[2 * p + 1]);
+                    acc2[p] = kde_pk(0.f, 0.f);
+                }
+                const kde_f2 one2 = kde_pk(1.f, 1.f);
+                auto column = [&](int i) {
+                    const float2 o = t[i];
+                    const float s = me.x * o.y - me.y * o.x;
+                    const float s2 = s * s;
+                    const kde_f2 s22 = kde_pk(s2, s2);
+#pragma unroll
+                    for (int p = 0; p < CV_G / 2; ++p)
+                        acc2[p] = kde_fma2(kde_ex22(kde_fma2(s22, kk2[p], ll2[p])), one2, acc2[p]);
+                };
                 if (!diag) {
 #pragma unroll 2
-                    for (int i = 0; i < ncol; ++i) {
-                        float2 o = t[i];
-                        float s = me.x * o.y - me.y * o.x;
-                        float s2 = s * s;
-#pragma unroll
-                        for (int q = 0; q < CV_G; ++q) acc[q] += kde_ex2(SCALE ? fmaf(s2, kk[q], ll[q]) : s2 * kk[q]);
-                    }
+                    for (int i = 0; i < ncol; ++i) column(i);
                 } else {
-                    for (int i = 0; i < ncol; ++i) {
-                        if (i == tid) continue;
-                        float2 o = t[i];
-                        float s = me.x * o.y - me.y * o.x;
-                        float s2 = s * s;
-#pragma unroll
-                        for (int q = 0; q < CV_G; ++q) acc[q] += kde_ex2(SCALE ? fmaf(s2, kk[q], ll[q]) : s2 * kk[q]);
-                    }
+                    for (int i = 0; i < ncol; ++i)
+                        if (i != tid) column(i);
                 }
+#pragma unroll
+                for (int p = 0; p < CV_G / 2; ++p) kde_upk(acc2[p], acc[2 * p], acc[2 * p + 1]);
 #pragma unroll
                 for (int q = 0; q < CV_G; ++q) {
                     float v = acc[q] * rmask;
