@@ -204,6 +204,7 @@ def run_ours(args, rank, world, local_rank):
     cand = I.log_candidates(w["kmin_c"], w["kmax_c"], w["n_cand"])
     ctx = kp.Context(local_rank)
     ctx.reserve(N, Ng, w["n_cand"])
+    ctx.set_autotune(not args.no_autotune)  # gather tile shape tuned in the first warm-up step
     # each rank simulates its own realisation (independent replicas, weak scaling)
     u0, v0 = I.landau_load(w["seed"] + rank, N, L, 0.05, 1.0)
     u0_t = torch.from_numpy(u0.view(np.int32)).to(dev)
@@ -411,7 +412,8 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(w), "N": N, "Ng": Ng, "dt": dt, "pic_steps_per_step": P,
                    "n_cand": w["n_cand"], "l2": "flushed before every timed step (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "gather_tile_shape": "default" if args.no_autotune else "autotuned"},
         "cv_pairs_per_s": cv_pairs_per_s,
         "cv_ms_per_step": cv_launch_ms,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
@@ -619,6 +621,7 @@ def run_ensemble(args, rank, world, local_rank):
         kap.append(float(cand[am]))
     u = torch.from_numpy(np.concatenate(us).view(np.int32)).to(dev)
     v = torch.from_numpy(np.concatenate(vs)).to(dev)
+    ctx.set_autotune(not args.no_autotune)  # the lanes tune their gathers in the first (uncaptured) step
     ens = kp.Ensemble(ctx, Ns, Ngs, kap, L, 0.1, u, v)
     mise = ens.mise(0.05, 1).cpu().numpy()
     steps = args.steps * 10
@@ -666,7 +669,8 @@ def run_ensemble(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "ensemble of %d Landau realisations, N log-uniform in [2^14, 2^20] (total %d), "
                                    "Ng in {128,256,512,1024}, one CUDA graph per step" % (R, int(Ntot)),
-                       "l2": "inputs larger than L2 (%.0f MB of particle state)" % (Ntot * 8 / 1e6)},
+                       "l2": "inputs larger than L2 (%.0f MB of particle state)" % (Ntot * 8 / 1e6),
+                       "gather_tile_shape": "default" if args.no_autotune else "autotuned"},
             "particle_steps_per_s": Ntot / (t_graph * 1e-3),
             "ms_per_step_graph": t_graph, "ms_per_step_launches": t_launch,
             "ms_per_step_plain_per_realisation": t_plain,
@@ -900,6 +904,7 @@ def main():
     ap.add_argument("--loads", type=int, default=8, help="shapes: independent particle loads")
     ap.add_argument("--requests", type=int, default=1000, help="serving: requests in the sample")
     ap.add_argument("--slots", type=int, default=8, help="serving: slots of the batched server")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the gather's default tile shape")
     ap.add_argument("--cv", default="pairs", choices=["pairs", "spectral"],
                     help="CV evaluation in the width schedule: O(N^2) pair sums or the exact Fourier form")
     args = ap.parse_args()

@@ -83,6 +83,19 @@ const char *kde_last_error(const kde_ctx *ctx);
  * cleared by this call). */
 kde_status kde_sync(kde_ctx *ctx);
 
+/* Tile-shape autotuner of the FP32 gather (no counterpart in the paper: a speed
+ * facility of this library).  The packed gather has several tile shapes (particles a
+ * lane, node-loop unrolling, launch bound) that give bitwise-identical results.  With
+ * enable != 0, the first FP32 gather (kde_gather, or the gather and push of pic_step
+ * and of the ensemble) of each key (grid size, log2 N, uniform width to a quarter
+ * octave, or "per-particle widths") runs every shape twice on its own data, timed by
+ * CUDA events, and keeps the fastest for that key; later calls with the key use it.
+ * Tuning synchronises the stream once per new key and is skipped while the stream is
+ * being captured or when an output aliases an input.  Off by default (the default
+ * shape is used).  kde_autotune_entries reports how many keys have been tuned. */
+kde_status kde_set_autotune(kde_ctx *ctx, int32_t enable);
+kde_status kde_autotune_entries(const kde_ctx *ctx, int32_t *n_out);
+
 /* Grow the workspace for problems of up to N particles, grids of up to Ng nodes
  * and up to n_cand CV candidates, so that later calls allocate nothing. */
 kde_status kde_reserve(kde_ctx *ctx, int64_t N, int32_t Ng, int32_t n_cand);
@@ -294,8 +307,10 @@ kde_status kde_damping_rate(const double *energy, int64_t n, double dt, double *
  * stream, so that they run concurrently; kde_ensemble_run can capture one step
  * of the whole ensemble into a CUDA graph and replay it once per step.  Each
  * realisation's results are bitwise those of pic_step on the same state.  The
- * arrays are reordered by cell within each realisation.  Not a passage of the
- * paper: the paper runs its ensembles one after another.
+ * arrays are reordered by cell within each realisation.  The lanes' contexts take
+ * the autotune setting (kde_set_autotune) of ctx at creation and tune their gathers
+ * in the first, uncaptured step.  Not a passage of the paper: the paper runs its
+ * ensembles one after another.
  * ------------------------------------------------------------------------- */
 typedef struct kde_ensemble kde_ensemble;
 

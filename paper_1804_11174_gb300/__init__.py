@@ -117,6 +117,8 @@ def load_library(path: str | None = None):
         "kde_server_wait": (S, [_P, _I64, _P, _P]),
         "kde_server_destroy": (S, [_P]),
         "kde_profile_read": (S, [_P, ctypes.c_int, _P, _P]),
+        "kde_set_autotune": (S, [_P, ctypes.c_int32]),
+        "kde_autotune_entries": (S, [_P, _P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -292,6 +294,16 @@ class Context:
 
     PROF = {"cv_pairs": 0, "deposit": 1, "gather": 2, "sort": 3, "poisson": 4, "cv_grid": 5, "cv_loo": 6,
             "spectral": 7, "ad": 8}
+
+    def set_autotune(self, on: bool = True):
+        """kde_set_autotune: tune the FP32 gather's tile shape per key on first use."""
+        self._check("kde_set_autotune", self.lib.kde_set_autotune(self.h, int(on)))
+
+    def autotune_entries(self) -> int:
+        """kde_autotune_entries: number of keys tuned so far."""
+        n = ctypes.c_int32()
+        self._check("kde_autotune_entries", self.lib.kde_autotune_entries(self.h, ctypes.addressof(n)))
+        return n.value
 
     def profile_enable(self, on: bool = True):
         """kde_profile_enable: start (or stop) recording per-kernel device times."""

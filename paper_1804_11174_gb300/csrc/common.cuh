@@ -110,6 +110,8 @@ struct kde_ctx {
     // Anderson-Darling per-bin logarithms (one table per context)
     void *ad_tab = nullptr;
     float2 *norm_tab = nullptr;  // FP32 width-normalisation table (kde_norm_tab), built at creation
+    bool autotune = false;                  // kde_set_autotune
+    std::map<uint64_t, int> gat2_tuned;     // packed-gather tile shape per key (gather.cu)
 };
 
 // ---------------------------------------------------------------------------

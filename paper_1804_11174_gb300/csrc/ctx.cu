@@ -240,6 +240,20 @@ extern "C" kde_status kde_set_stream(kde_ctx *ctx, void *stream)
     return KDE_OK;
 }
 
+extern "C" kde_status kde_set_autotune(kde_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return KDE_EINVAL;
+    ctx->autotune = enable != 0;
+    return KDE_OK;
+}
+
+extern "C" kde_status kde_autotune_entries(const kde_ctx *ctx, int32_t *n_out)
+{
+    if (!ctx || !n_out) return KDE_EINVAL;
+    *n_out = (int32_t)ctx->gat2_tuned.size();
+    return KDE_OK;
+}
+
 extern "C" const char *kde_last_error(const kde_ctx *ctx)
 {
     if (!ctx) return "null context";

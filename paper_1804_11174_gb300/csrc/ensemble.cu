@@ -142,7 +142,10 @@ extern "C" kde_status kde_ensemble_create(kde_ctx *ctx, kde_ensemble **out, int3
         if (err == cudaSuccess) e->lane_ev.push_back(ev);
         kde_ctx *lc = nullptr;
         if (err == cudaSuccess && kde_create(&lc, ctx->device, st) != KDE_OK) err = cudaErrorMemoryAllocation;
-        if (err == cudaSuccess) e->lane_ctx.push_back(lc);
+        if (err == cudaSuccess) {
+            lc->autotune = ctx->autotune;  // lanes tune their gathers in the uncaptured first step
+            e->lane_ctx.push_back(lc);
+        }
     }
     if (err == cudaSuccess) err = cudaMalloc(&e->W, sizeof(double) * R);
     if (err == cudaSuccess) err = cudaMalloc(&e->d_step, sizeof(int));

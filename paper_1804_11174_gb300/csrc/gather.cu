@@ -185,15 +185,14 @@ __global__ void __launch_bounds__(GAT_THREADS) gather_kernel(GatherArgs<T> A)
 //    full angle, particles (K cos, K sin), 2^(K cos(x_j - x_g)), and 2^-K folded into
 //    the particle's norm; three multiply-adds per pair instead of four.
 // ---------------------------------------------------------------------------
+// Tile shapes (template parameters of gather2_kernel, chosen per call by the variant
+// table below): NP particles a lane (even), node-loop unrolling UD for windows of
+// GAT2_DEEP_LEN nodes or more and US below, and a launch bound of MINB resident
+// blocks per SM.  Variants with the same NP compute the same sums in the same order
+// (NP sets each warp's node window), so their results are bitwise identical and only
+// the speed differs.
 #define GAT2_WARPS 4
-#define GAT2_NP 4                 // particles a lane (an even number)
-#define GAT2_ITEM (32 * GAT2_NP)  // particles per warp
-#define GAT2_UNROLL 4             // node loop unrolling
-#define GAT2_UNROLL_DEEP 8        // node loop unrolling for windows of GAT2_DEEP_LEN nodes or more
 #define GAT2_DEEP_LEN 128
-#define GAT2_MINB 5               // launch bound: resident blocks per SM
-static constexpr int kGat2Unroll = GAT2_UNROLL;
-static constexpr int kGat2UnrollDeep = GAT2_UNROLL_DEEP;
 
 // the node loop of the packed gather over the window's two contiguous segments
 // [g0, e1) and [0, e2): NPP particle pairs a lane, U nodes unrolled
@@ -218,8 +217,10 @@ __device__ __forceinline__ void gat2_nodes(const float4 *SC, const float2 *FF, i
     for (int g = 0; g < e2; ++g) node(g);
 }
 
-__global__ void __launch_bounds__(GAT2_WARPS * 32, GAT2_MINB) gather2_kernel(GatherArgs<float> A)
+template <int NP, int UD, int US, int MINB>
+__global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherArgs<float> A)
 {
+    constexpr int GAT2_NP = NP, GAT2_ITEM = 32 * NP;
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ float kred[GAT2_WARPS];
     const int Ng = A.Ng;
@@ -335,11 +336,11 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, GAT2_MINB) gather2_kernel(Gat
     // shallower (less remainder work)
     const bool deep = len >= GAT2_DEEP_LEN;
     if (cosf) {
-        if (deep) gat2_nodes<kGat2UnrollDeep, true, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
-        else gat2_nodes<kGat2Unroll, true, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
+        if (deep) gat2_nodes<UD, true, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
+        else gat2_nodes<US, true, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
     } else {
-        if (deep) gat2_nodes<kGat2UnrollDeep, false, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
-        else gat2_nodes<kGat2Unroll, false, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
+        if (deep) gat2_nodes<UD, false, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
+        else gat2_nodes<US, false, NPP>(SC, FF, g0, e1, e2, psP, pcP, acc);
     }
     float ea[GAT2_NP];
 #pragma unroll
@@ -362,6 +363,58 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, GAT2_MINB) gather2_kernel(Gat
     }
 }
 
+// the tile-shape variants of the packed gather: (particles a lane, deep and short
+// unrolling, launch bound)
+#define GAT2_NVARIANTS 3
+
+template <int NP, int UD, int US, int MINB>
+static kde_status gat2_launch(kde_ctx *ctx, const GatherArgs<float> &A)
+{
+    auto kern = gather2_kernel<NP, UD, US, MINB>;
+    static bool attr = false;
+    if (!attr) {
+        KDE_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           KDE_MAX_NG * (int)(sizeof(float4) + sizeof(float2))),
+                 "gather2 attribute");
+        attr = true;
+    }
+    const size_t smem = (size_t)A.Ng * (sizeof(float4) + sizeof(float2));
+    unsigned grid = (unsigned)((A.N + GAT2_WARPS * 32 * NP - 1) / (GAT2_WARPS * 32 * NP));
+    if (grid == 0) grid = 1;
+    kern<<<grid, GAT2_WARPS * 32, smem, ctx->stream>>>(A);
+    KDE_LAUNCHED(ctx, "gather2_kernel");
+    return KDE_OK;
+}
+
+static kde_status gat2_variant(kde_ctx *ctx, const GatherArgs<float> &A, int v)
+{
+    // all with four particles a lane: the warps' particle sets, and so their node windows
+    // and kernel forms, are the same in every variant
+    switch (v) {
+    case 1: return gat2_launch<4, 4, 4, 8>(ctx, A);
+    case 2: return gat2_launch<4, 8, 4, 6>(ctx, A);
+    default: return gat2_launch<4, 8, 4, 5>(ctx, A);
+    }
+}
+
+// autotuner key: grid size, log2 of N, and the uniform width in quarter octaves
+// (0 for per-particle widths, whose windows the host does not see)
+static uint64_t gat2_key(const GatherArgs<float> &A)
+{
+    int lg = 0;
+    while (lg < 40 && (1LL << (lg + 1)) <= A.N) ++lg;
+    int kc = 0;
+    if (!A.kappa) {
+        const double q = 4.0 * log2((double)A.kappa_u) + 128.0;
+        kc = q < 1.0 ? 1 : (q > 255.0 ? 255 : (int)q);
+    }
+    return (uint64_t)A.Ng | ((uint64_t)lg << 16) | ((uint64_t)kc << 24);
+}
+
+// the variant for this call: the tuned one for its key; with autotuning on and no stream
+// capture, a key seen for the first time is tuned on this call's own data (every variant
+// runs twice, timed by events on the stream, the fastest second run wins), provided that
+// repeating the call cannot change its result (no output aliases an input)
 static kde_status launch_gather2(kde_ctx *ctx, GatherArgs<float> &A)
 {
     const void *nodes = kde_node_table(ctx, A.Ng, false);
@@ -369,21 +422,43 @@ static kde_status launch_gather2(kde_ctx *ctx, GatherArgs<float> &A)
     A.nodes = (const float2 *)nodes;
     A.status = ctx->d_status;
     A.ntab = ctx->norm_tab;
-    const size_t smem = (size_t)A.Ng * (sizeof(float4) + sizeof(float2));
-    static bool attr = false;
-    if (!attr) {
-        KDE_CUDA(ctx, cudaFuncSetAttribute(gather2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           KDE_MAX_NG * (int)(sizeof(float4) + sizeof(float2))),
-                 "gather2 attribute");
-        attr = true;
+    const uint64_t key = gat2_key(A);
+    auto it = ctx->gat2_tuned.find(key);
+    int v = it != ctx->gat2_tuned.end() ? it->second : 0;
+    bool tune = false;
+    if (it == ctx->gat2_tuned.end() && ctx->autotune) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(ctx->stream, &cap);
+        auto apart = [](const void *out, const void *in) { return !out || out != in; };
+        const bool idem = !A.u_out || (apart(A.u_out, A.u) && apart(A.v_out, A.v_in) && apart(A.kappa_out, A.kappa) &&
+                                       apart(A.norm_out, A.norm_in) && apart(A.norm_out, A.norm) &&
+                                       apart(A.id_out, A.id_in));
+        tune = cap == cudaStreamCaptureStatusNone && idem;
     }
-    unsigned grid = (unsigned)((A.N + GAT2_WARPS * GAT2_ITEM - 1) / (GAT2_WARPS * GAT2_ITEM));
-    if (grid == 0) grid = 1;
-    {
+    if (!tune) {
         KdeProfScope _ps(ctx, PROF_GATHER);
-        gather2_kernel<<<grid, GAT2_WARPS * 32, smem, ctx->stream>>>(A);
+        return gat2_variant(ctx, A, v);
     }
-    KDE_LAUNCHED(ctx, "gather2_kernel");
+    cudaEvent_t ev[2 * GAT2_NVARIANTS + 1];
+    for (auto &e : ev) KDE_CUDA(ctx, cudaEventCreate(&e), "autotune event");
+    KDE_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream), "autotune event");
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < GAT2_NVARIANTS; ++k) {
+            KDE_TRY(gat2_variant(ctx, A, k));
+            KDE_CUDA(ctx, cudaEventRecord(ev[1 + r * GAT2_NVARIANTS + k], ctx->stream), "autotune event");
+        }
+    KDE_CUDA(ctx, cudaEventSynchronize(ev[2 * GAT2_NVARIANTS]), "autotune wait");
+    float best = 3.0e38f;
+    for (int k = 0; k < GAT2_NVARIANTS; ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[GAT2_NVARIANTS + k], ev[GAT2_NVARIANTS + k + 1]);
+        if (ms < best) {
+            best = ms;
+            v = k;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    ctx->gat2_tuned[key] = v;
     return KDE_OK;
 }
 

@@ -225,3 +225,39 @@ def test_max_size_sampled(ctx, oracle):
     g = np.arange(0, Ng, 97)
     ref = oracle.kde_at(x, g * L / Ng, L, kappa=k.astype(np.float64))
     assert rel_l2(rho[g], ref) <= TOL32
+
+
+def test_gather_autotune_keeps_results(ctx, kp):
+    # the gather's tile shapes give bitwise-identical results; the tuner times them on
+    # the first call of each key and keeps the fastest for later calls
+    L = 4 * math.pi
+    N, Ng = 30001, 256
+    u, _, _ = landau(31, N, L)
+    f = np.sin(2 * math.pi * np.arange(Ng) / Ng) + 0.2
+    k = I.log_uniform(31, I.STREAM_KAPPA, N, 5.0, 500.0).astype(np.float32)
+    ud, fd = to_dev_u(u), to_dev(f)
+    refs = [ctx.gather(ud, fd, L, kappa_uniform=ku).cpu().numpy() for ku in (4.0, 300.0)]
+    refs.append(ctx.gather(ud, fd, L, kappa=to_dev(k)).cpu().numpy())
+    c2 = kp.Context(0)
+    try:
+        c2.set_autotune(True)
+        for rep in range(2):
+            outs = [c2.gather(ud, fd, L, kappa_uniform=ku).cpu().numpy() for ku in (4.0, 300.0)]
+            outs.append(c2.gather(ud, fd, L, kappa=to_dev(k)).cpu().numpy())
+            for a, b in zip(outs, refs):
+                np.testing.assert_array_equal(a, b)
+        assert c2.autotune_entries() == 3
+        # pic_step with the tuner on gives the same run bit for bit
+        uu, vv = I.landau_load(32, 20000, L, 0.05, 1.0)
+        kk = I.log_uniform(32, I.STREAM_KAPPA, 20000, 5.0, 50.0).astype(np.float32)
+        runs = []
+        for c in (ctx, c2):
+            st = kp.PicState(to_dev_u(uu), to_dev(vv.astype(np.float32)), L, 128, 0.1, kappa=to_dev(kk), max_steps=4)
+            c.pic_step(st, 4)
+            c.sync()
+            runs.append((st.energy.cpu().numpy(), st.u.cpu().numpy(), st.v.cpu().numpy()))
+        for a, b in zip(*runs):
+            np.testing.assert_array_equal(a, b)
+        assert c2.autotune_entries() == 4
+    finally:
+        c2.close()
