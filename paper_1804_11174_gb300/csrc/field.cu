@@ -5,7 +5,8 @@
 // finite-difference symbol of Sec. III.A); rho' is the total charge density
 // with its mean removed in FP64 (G annihilates constants, and removing the
 // mean first keeps the FP32 sum free of cancellation).  Ng <= 4096, so the
-// whole grid lives in shared memory and each thread owns one output node.
+// whole grid lives in shared memory; each warp owns one output node, its lanes
+// take every 32nd term and a shuffle tree adds them (Ng / 8 blocks of 8 warps).
 #include "common.cuh"
 
 #define POI_THREADS 256
@@ -37,17 +38,17 @@ __global__ void __launch_bounds__(POI_THREADS)
         Gs[l] = G[l];
     }
     __syncthreads();
-    int j = blockIdx.x * POI_THREADS + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (POI_THREADS / 32) + (threadIdx.x >> 5);
     if (j >= Ng) return;
-    T s0 = 0, s1 = 0;
-    int l = 0;
-    for (; l + 1 <= j; l += 2) {  // d = j - l >= 0
-        s0 += Gs[j - l] * rt[l];
-        s1 += Gs[j - l - 1] * rt[l + 1];
+    T s = 0;
+    for (int l = lane; l < Ng; l += 32) {
+        const int d = j - l;
+        s += Gs[d < 0 ? d + Ng : d] * rt[l];
     }
-    for (; l <= j; ++l) s0 += Gs[j - l] * rt[l];
-    for (; l < Ng; ++l) s1 += Gs[j - l + Ng] * rt[l];
-    E[j] = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) E[j] = s;
 }
 
 template <typename T>
@@ -80,7 +81,7 @@ kde_status kde_poisson_impl(kde_ctx *ctx, const T *rho, const long long *acc, do
     }
     {
         KdeProfScope _ps(ctx, PROF_POISSON);
-    poisson_kernel<T><<<(Ng + POI_THREADS - 1) / POI_THREADS, POI_THREADS, smem, ctx->stream>>>(
+    poisson_kernel<T><<<(Ng + POI_THREADS / 32 - 1) / (POI_THREADS / 32), POI_THREADS, smem, ctx->stream>>>(
         rho, acc, acc_inv, Ng, charge, background, G, E_out);
     }
     KDE_LAUNCHED(ctx, "poisson_kernel");
