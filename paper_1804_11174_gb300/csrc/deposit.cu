@@ -397,17 +397,30 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
     const int n = (int)(S.N - i0 < DEP_CHUNK ? S.N - i0 : DEP_CHUNK);
     const int Ng = S.Ng;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // pass 1: the smallest width (it sets the window) and the largest (it sets the form)
+    // every input of the thread's particles loaded at once (one global-load latency per
+    // chunk); the smallest width sets the window, the largest the form
+    constexpr int PER = DEP_CHUNK / DEP_THREADS;
+    uint32_t ru[PER];
+    float rk[PER], rn[PER], rw[PER];
     float kmin = (float)KDE_KAPPA_MAX, kmax = 0.f;
-    for (int t = tid; t < n; t += DEP_THREADS) {
-        const int64_t j = i0 + t;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int t = tid + p * DEP_THREADS;
+        const bool ok = t < n;
+        const int64_t j = i0 + (ok ? t : 0);
+        ru[p] = S.u[j];
         float k = S.kappa ? S.kscale * S.kappa[j] : S.kappa_u;
-        if (!(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
+        rn[p] = S.lnorm ? S.lnorm[j] : (S.norm ? S.norm[j] : 0.f);
+        rw[p] = S.w ? S.w[j] : S.w_u;
+        if (ok && !(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
             kde_flag(S.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
             k = (float)KDE_KAPPA_MAX;
         }
-        kmin = fminf(kmin, k);
-        kmax = fmaxf(kmax, k);
+        rk[p] = k;
+        if (ok) {
+            kmin = fminf(kmin, k);
+            kmax = fmaxf(kmax, k);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -440,19 +453,19 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
     // the window shrinks as the width grows: the smallest width's window covers all
     const int W = window_nodes_f(kmin, Ng, (float)KDE_XCUT);
     const bool cosf = allow_cos && kmax <= KDE_COSFORM_KMAX;
-    // pass 2: the particle records
-    for (int t = tid; t < n; t += DEP_THREADS) {
-        const int64_t j = i0 + t;
-        const uint32_t uu = S.u[j];
-        float k = S.kappa ? S.kscale * S.kappa[j] : S.kappa_u;
-        if (!(k > 0.f && k <= (float)KDE_KAPPA_MAX)) k = (float)KDE_KAPPA_MAX;
+    // the particle records
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int t = tid + p * DEP_THREADS;
+        if (t >= n) break;
+        const uint32_t uu = ru[p];
+        const float k = rk[p];
         float nm;
-        if (S.lnorm) nm = exp2f(S.lnorm[j]);
-        else if (S.norm) nm = S.norm[j];
+        if (S.lnorm) nm = exp2f(rn[p]);
+        else if (S.norm) nm = rn[p];
         else if (S.kappa) nm = S.ntab ? kde_norm_tab(S.ntab, k) : (float)kde_norm((double)k);
         else nm = S.norm_u;
-        const float wj = S.w ? S.w[j] : S.w_u;
-        const float wn = wj * S.coef * nm;
+        const float wn = rw[p] * S.coef * nm;
         float sh, ch;
         kde_half_sincos(uu, sh, ch);
         if (cosf) {
@@ -471,7 +484,7 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
     const int c_first = kde_cell(S.u[i0], Ng), c_last = kde_cell(S.u[i0 + n - 1], Ng);
     int g_lo = c_first - W;
     int R = c_last + W - g_lo + 1;
-    if (R >= Ng || c_last < c_first) {
+    if (R >= Ng || R < 1 || c_last < c_first) {
         g_lo = 0;
         R = Ng;
     }
@@ -560,6 +573,12 @@ kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T
     S.norm_bound = norm_bound;
     S.status = ctx->d_status;
     S.scale_exp = KDE_ES_FROM_BOUND;
+    if (!wmax_bits) {
+        // the scale exponent from the host-known bound, as acc_scale_exp computes it
+        int e;
+        frexp(bound > 0 ? bound : 1.0, &e);
+        S.scale_exp = 62 - e;
+    }
     S.ntab = ctx->norm_tab;
     unsigned grid = (unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK);
     {
