@@ -21,6 +21,7 @@
 #define SP_SUB 256
 #define SP_MAXM 16384
 #define SP_MAXCHUNK 16384
+#define SP_Q 4  // consecutive modes a thread in the structure factor
 
 // modes needed for a width: A_m ~ exp(-m^2 / (2 kappa)) < 1e-17 beyond sqrt(78.4 kappa)
 __host__ __device__ inline int spec_modes(double kappa)
@@ -47,36 +48,65 @@ __device__ void spec_ratios(double kappa, int M, double *A)
     for (int m = 1; m <= M; ++m) A[m] *= A[m - 1];
 }
 
-// structure factor partials: block (chunk, mode block); thread = one mode.  The
-// partials are laid out with stride M; modes above *mlim (when given) are skipped.
+// structure factor partials: block (chunk, mode block); thread = SP_Q consecutive
+// modes m0 .. m0 + SP_Q - 1: one exact-phase sincospi for m0, then each further mode by
+// a rotation with e^{i theta_j} (tabulated per particle in shared memory), which costs
+// four FP32 operations instead of a sincospi and adds at most an ulp or two per step.
+// The partials are laid out with stride M; modes above *mlim (when given) are skipped.
 __global__ void __launch_bounds__(SP_THREADS)
     spec_sf_kernel(const uint32_t *__restrict__ u, int64_t N, int64_t chunk, int M, const int *mlim, double2 *part)
 {
-    extern __shared__ uint32_t us[];
+    extern __shared__ __align__(8) uint32_t us[];
+    float2 *e1 = (float2 *)(us + ((chunk + 1) & ~1LL));  // (cos, sin) of theta_j
     const int Me = mlim ? min(M, *mlim) : M;
-    if (1 + (int)blockIdx.y * SP_THREADS > Me) return;  // the whole mode block is above the limit
+    const int mb = 1 + (int)blockIdx.y * SP_THREADS * SP_Q;
+    if (mb > Me) return;  // the whole mode block is above the limit
     const int64_t j0 = (int64_t)blockIdx.x * chunk;
     const int n = (int)(N - j0 < chunk ? N - j0 : chunk);
-    for (int k = threadIdx.x; k < n; k += SP_THREADS) us[k] = u[j0 + k];
+    for (int k = threadIdx.x; k < n; k += SP_THREADS) {
+        const uint32_t uk = u[j0 + k];
+        us[k] = uk;
+        float s1, c1;
+        sincospif((float)(int32_t)uk * (1.0f / 2147483648.0f), &s1, &c1);
+        e1[k] = make_float2(c1, s1);
+    }
     __syncthreads();
-    const int m = 1 + blockIdx.y * SP_THREADS + threadIdx.x;
-    if (m > Me) return;
-    double cr = 0.0, ci = 0.0;
+    const int m0 = mb + threadIdx.x * SP_Q;
+    if (m0 > Me) return;
+    double cr[SP_Q], ci[SP_Q];
+#pragma unroll
+    for (int q = 0; q < SP_Q; ++q) cr[q] = ci[q] = 0.0;
     for (int k0 = 0; k0 < n; k0 += SP_SUB) {
         const int k1 = k0 + SP_SUB < n ? k0 + SP_SUB : n;
-        float fr = 0.f, fi = 0.f;
-#pragma unroll 4
+        float fr[SP_Q], fi[SP_Q];
+#pragma unroll
+        for (int q = 0; q < SP_Q; ++q) fr[q] = fi[q] = 0.f;
+#pragma unroll 2
         for (int k = k0; k < k1; ++k) {
-            const uint32_t ph = (uint32_t)m * us[k];  // m theta / (2 pi) in 2^-32 turns
+            const uint32_t ph = (uint32_t)m0 * us[k];  // m0 theta / (2 pi) in 2^-32 turns
             float s, c;
             sincospif((float)(int32_t)ph * (1.0f / 2147483648.0f), &s, &c);
-            fr += c;
-            fi += s;
+            const float2 e = e1[k];
+            fr[0] += c;
+            fi[0] += s;
+#pragma unroll
+            for (int q = 1; q < SP_Q; ++q) {
+                const float cn = fmaf(c, e.x, -s * e.y), sn = fmaf(s, e.x, c * e.y);
+                c = cn;
+                s = sn;
+                fr[q] += c;
+                fi[q] += s;
+            }
         }
-        cr += (double)fr;
-        ci += (double)fi;
+#pragma unroll
+        for (int q = 0; q < SP_Q; ++q) {
+            cr[q] += (double)fr[q];
+            ci[q] += (double)fi[q];
+        }
     }
-    part[(size_t)blockIdx.x * M + (m - 1)] = make_double2(cr, ci);
+#pragma unroll
+    for (int q = 0; q < SP_Q; ++q)
+        if (m0 + q <= Me) part[(size_t)blockIdx.x * M + (m0 + q - 1)] = make_double2(cr[q], ci[q]);
 }
 
 // S_m = sum over chunks in chunk order (modes up to *mlim when given)
@@ -231,8 +261,10 @@ static kde_status spec_loo_from_S(kde_ctx *ctx, const uint32_t *u, int64_t N, do
 // structure factor for modes 1..M (or up to *mlim) into S
 static kde_status spec_structure(kde_ctx *ctx, const uint32_t *u, int64_t N, int M, const int *mlim, double2 **S_out)
 {
-    int64_t chunk = 4096;
-    while ((N + chunk - 1) / chunk > 256 && chunk < SP_MAXCHUNK) chunk *= 2;
+    // about a thousand chunks keep every SM busy; the partials stay under 2^22 entries (64 MB)
+    int64_t chunk = 1024;
+    while (((N + chunk - 1) / chunk > 1024 || (N + chunk - 1) / chunk * M > (1 << 22)) && chunk < SP_MAXCHUNK)
+        chunk *= 2;
     const int nchunks = (int)((N + chunk - 1) / chunk);
     double2 *part = (double2 *)kde_ws(ctx, WS_SP_PART, (size_t)nchunks * M * sizeof(double2));
     double2 *S = (double2 *)kde_ws(ctx, WS_SP_S, (size_t)M * sizeof(double2));
@@ -240,14 +272,15 @@ static kde_status spec_structure(kde_ctx *ctx, const uint32_t *u, int64_t N, int
     static bool attr = false;
     if (!attr) {
         KDE_CUDA(ctx, cudaFuncSetAttribute(spec_sf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SP_MAXCHUNK * 4),
+                                           SP_MAXCHUNK * 12 + 8),
                  "spec_sf_kernel attribute");
         attr = true;
     }
     {
         KdeProfScope _ps(ctx, PROF_SPECTRAL);
-        dim3 grid((unsigned)nchunks, (unsigned)((M + SP_THREADS - 1) / SP_THREADS));
-        spec_sf_kernel<<<grid, SP_THREADS, (size_t)chunk * 4, ctx->stream>>>(u, N, chunk, M, mlim, part);
+        dim3 grid((unsigned)nchunks, (unsigned)((M + SP_THREADS * SP_Q - 1) / (SP_THREADS * SP_Q)));
+        spec_sf_kernel<<<grid, SP_THREADS, (size_t)((chunk + 1) & ~1LL) * 4 + (size_t)chunk * 8, ctx->stream>>>(
+            u, N, chunk, M, mlim, part);
     }
     KDE_LAUNCHED(ctx, "spec_sf_kernel");
     spec_reduce_kernel<<<(M + 255) / 256, 256, 0, ctx->stream>>>(part, nchunks, M, mlim, S);
