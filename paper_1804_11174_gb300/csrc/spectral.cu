@@ -12,7 +12,9 @@
 // candidate, and all candidates share one S_m.
 //
 // Phases are exact: m theta_j = 2 pi (m u_j mod 2^32) / 2^32 in integer
-// arithmetic, then one FP32 sincospi.  Sub-chunk sums run in FP32 and are
+// arithmetic, then one FP32 sincospi for the first of every four consecutive
+// modes and a rotation by e^{i theta_j} for the next three (an ulp or two each).
+// Sub-chunk sums run in FP32 and are
 // combined in FP64 in a fixed order; the CV combination and the leave-one-out
 // sums are FP64.  Particles may come in any order (no sort).
 #include "common.cuh"
