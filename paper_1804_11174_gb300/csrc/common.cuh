@@ -112,6 +112,8 @@ struct kde_ctx {
     float2 *norm_tab = nullptr;  // FP32 width-normalisation table (kde_norm_tab), built at creation
     bool autotune = false;                  // kde_set_autotune
     std::map<uint64_t, int> gat2_tuned;     // packed-gather tile shape per key (gather.cu)
+    void *sp_atab = nullptr;                // workspace holding the Bessel ratios of sp_atab_cands (spectral.cu)
+    std::vector<double> sp_atab_cands;
 };
 
 // ---------------------------------------------------------------------------

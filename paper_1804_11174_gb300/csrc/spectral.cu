@@ -126,9 +126,11 @@ __global__ void spec_reduce_kernel(const double2 *part, int nchunks, int M, cons
 }
 
 // one CTA per candidate (caller's order): Bessel ratios (sequential recurrence,
-// one thread), then the three mode sums over the block and CV (x units)
+// one thread; skipped when Atab already holds this candidate list's ratios), then the
+// three mode sums over the block and CV (x units)
 __global__ void __launch_bounds__(SP_THREADS)
-    spec_cv_kernel(const double2 *S, CandList cl, int64_t N, double L, int Astride, double *Atab, double *cv_out)
+    spec_cv_kernel(const double2 *S, CandList cl, int64_t N, double L, int Astride, double *Atab, int ratios_ready,
+                   double *cv_out)
 {
     __shared__ double r0[SP_THREADS], r1[SP_THREADS], r2[SP_THREADS];
     const int c = blockIdx.x;
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(SP_THREADS)
     const double kappa = cl.k[c];
     const int M = spec_modes(kappa);
     double *A = Atab + (size_t)c * Astride;
-    if (threadIdx.x == 0) spec_ratios(kappa, M, A);
+    if (threadIdx.x == 0 && !ratios_ready) spec_ratios(kappa, M, A);
     __syncthreads();
     double sA = 0.0, sAS = 0.0, sA2S = 0.0;
     for (int m = 1 + threadIdx.x; m <= M; m += SP_THREADS) {
@@ -333,7 +335,13 @@ kde_status kde_cv_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, do
     if (!Atab) return KDE_ENOMEM;
     double2 *S = nullptr;
     KDE_TRY(spec_structure(ctx, u, N, M, nullptr, &S));
-    spec_cv_kernel<<<n_cand, SP_THREADS, 0, ctx->stream>>>(S, cl, N, L, Astride, Atab, cv_dev);
+    // the Bessel ratios depend on the candidates only: a width schedule that repeats its
+    // candidate list reuses the table the previous call left in the workspace
+    std::vector<double> key(cand_host, cand_host + n_cand);
+    const bool ready = ctx->sp_atab == (void *)Atab && ctx->sp_atab_cands == key;
+    spec_cv_kernel<<<n_cand, SP_THREADS, 0, ctx->stream>>>(S, cl, N, L, Astride, Atab, ready ? 1 : 0, cv_dev);
+    ctx->sp_atab = (void *)Atab;
+    ctx->sp_atab_cands = key;
     KDE_LAUNCHED(ctx, "spec_cv_kernel");
     spec_argmin_kernel<<<1, 1, 0, ctx->stream>>>(cv_dev, cl, argmin_dev, kstar_dev);
     KDE_LAUNCHED(ctx, "spec_argmin_kernel");
