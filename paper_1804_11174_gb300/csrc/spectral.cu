@@ -183,21 +183,31 @@ __global__ void spec_argmin_kernel(const double *cv, CandList cl, int *argmin, d
 struct SpecSel {
     int M;
     double norm;
+    const double *A;  // the ratios A[0..M]: a row of the candidates' table, or the kernel's own output
 };
-__global__ void spec_select_kernel(CandList cl, const int *argmin, SpecSel *sel, double *A)
+// Atab: the candidates' ratio table (row stride Astride) when the caller has it, else
+// nullptr and the ratios are worked out into A
+__global__ void spec_select_kernel(CandList cl, const int *argmin, SpecSel *sel, double *A, const double *Atab,
+                                   int Astride)
 {
     const double kappa = cl.k[*argmin];
     const int M = spec_modes(kappa);
-    spec_ratios(kappa, M, A);
+    if (Atab) {
+        sel->A = Atab + (size_t)*argmin * Astride;
+    } else {
+        spec_ratios(kappa, M, A);
+        sel->A = A;
+    }
     sel->M = M;
     sel->norm = kde_norm(kappa);
 }
 
 // A_m S_m in FP32 for the leave-one-out sums
-__global__ void spec_as_kernel(const double2 *S, const double *A, const SpecSel *sel, float2 *AS)
+__global__ void spec_as_kernel(const double2 *S, const SpecSel *sel, float2 *AS)
 {
     const int m = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     if (m > sel->M) return;
+    const double *A = sel->A;
     const double2 s = S[m - 1];
     AS[m - 1] = make_float2((float)(A[m] * s.x), (float)(A[m] * s.y));
 }
@@ -243,15 +253,16 @@ __global__ void __launch_bounds__(SP_THREADS)
 // leave-one-out densities at cand[*argmin] from the structure factor S (modes
 // 1..M(kappa*) present)
 static kde_status spec_loo_from_S(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double2 *S,
-                                  const CandList &cl, int Mmax, const int *argmin_dev, float *loo)
+                                  const CandList &cl, int Mmax, const int *argmin_dev, float *loo,
+                                  const double *Atab = nullptr, int Astride = 0)
 {
     double *Asel = (double *)kde_ws(ctx, WS_SP_ASEL, (size_t)(Mmax + 1) * 8 + 64);
     float2 *AS = (float2 *)kde_ws(ctx, WS_SP_AS, (size_t)Mmax * sizeof(float2) + 64);
     SpecSel *sel = (SpecSel *)kde_ws(ctx, WS_SP_SEL, sizeof(SpecSel));
     if (!Asel || !AS || !sel) return KDE_ENOMEM;
-    spec_select_kernel<<<1, 1, 0, ctx->stream>>>(cl, argmin_dev, sel, Asel);
+    spec_select_kernel<<<1, 1, 0, ctx->stream>>>(cl, argmin_dev, sel, Asel, Atab, Astride);
     KDE_LAUNCHED(ctx, "spec_select_kernel");
-    spec_as_kernel<<<(Mmax + 255) / 256, 256, 0, ctx->stream>>>(S, Asel, sel, AS);
+    spec_as_kernel<<<(Mmax + 255) / 256, 256, 0, ctx->stream>>>(S, sel, AS);
     KDE_LAUNCHED(ctx, "spec_as_kernel");
     {
         KdeProfScope _ps(ctx, PROF_CV_LOO);
@@ -345,6 +356,6 @@ kde_status kde_cv_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, do
     KDE_LAUNCHED(ctx, "spec_cv_kernel");
     spec_argmin_kernel<<<1, 1, 0, ctx->stream>>>(cv_dev, cl, argmin_dev, kstar_dev);
     KDE_LAUNCHED(ctx, "spec_argmin_kernel");
-    if (loo) KDE_TRY(spec_loo_from_S(ctx, u, N, L, S, cl, M, argmin_dev, loo));
+    if (loo) KDE_TRY(spec_loo_from_S(ctx, u, N, L, S, cl, M, argmin_dev, loo, Atab, Astride));
     return KDE_OK;
 }
