@@ -1,4 +1,4 @@
-"""The bench's count of algorithmic CV work against brute force."""
+"""The bench's counts of algorithmic work (CV pairs, deposit and gather window pairs) against brute force."""
 import math
 
 import numpy as np
@@ -18,3 +18,21 @@ def test_inradius_pair_count_matches_brute_force():
         r = math.pi if s2 >= 1 else 2 * math.asin(math.sqrt(s2))
         brute = int(np.sum(d[iu] <= r))
         assert cv_inradius_pairs(u, [k]) == brute
+
+
+def test_window_pair_count_matches_node_counts():
+    # the deposit/gather roofline unit: nodes within the truncation radius of a particle,
+    # averaged over positions, equals 2 r Ng / (2 pi) (whole grid once r >= pi)
+    from bench import grid_window_pairs
+    rng = np.random.default_rng(5)
+    Ng = 256
+    th = rng.uniform(0, 2 * math.pi, 20000)
+    g = 2 * math.pi * np.arange(Ng) / Ng
+    for k in [4.0, 12.0, 100.0, 3000.0]:
+        s2 = min(24 * math.log(2) / (2 * k), 1.0)
+        r = 2 * math.asin(math.sqrt(s2))
+        d = np.abs(th[:, None] - g[None, :])
+        d = np.minimum(d, 2 * math.pi - d)
+        counts = np.sum(d <= r, axis=1)
+        est = grid_window_pairs(np.full(th.size, k), Ng)
+        assert abs(counts.sum() - est) <= 0.01 * est + th.size * 1e-6
