@@ -111,7 +111,10 @@ kde_status kde_pack_positions(kde_ctx *ctx, const double *x, int64_t N, double L
  * particle weights, or NULL for w_i = L / N (mean density 1).  rho_out:
  * real[Ng].  Terms below 2^-24 of a kernel's peak may be skipped (truncated
  * support).  N >= 0 (N = 0 gives zeros), 1 <= Ng <= KDE_MAX_NG, L > 0.
- * Flags: KDE_F64. */
+ * Flags: KDE_F64.  In FP32 the per-particle normalisations come from a table of
+ * I0e built in FP64 when the context is created (relative error below 5e-7), and
+ * chunks whose widths are all at most 32 use the form 2^(K cos(theta_g - theta_i) - K),
+ * K = kappa log2(e), whose exponent carries about K 2^-24 of rounding error. */
 kde_status kde_deposit(kde_ctx *ctx, const uint32_t *u, const void *kappa, double kappa_uniform,
                        const void *weight, int64_t N, int32_t Ng, double L, void *rho_out,
                        uint32_t flags);
@@ -238,7 +241,8 @@ typedef struct pic_state {
     void *v;              /* device real[N] velocities v^{n-1/2} (in/out) */
     void *kappa;          /* device real[N] per-particle widths (in/out), or NULL for uniform */
     void *kappa_norm;     /* device real[N] scratch kept equal to 1/(2 pi I0e(kappa_i)) by the
-                             library; required when kappa != NULL */
+                             library (FP32: from the context's table, within 5e-7);
+                             required when kappa != NULL */
     uint32_t *id;         /* device uint32[N] particle labels moved with the particles, or NULL */
     int64_t N;            /* particles, >= 1 */
     int32_t Ng;           /* grid nodes, 1..KDE_MAX_NG */
