@@ -178,6 +178,31 @@ def test_cv_spectral_matches_pairs_and_sweep_size(ctx, oracle):
     np.testing.assert_allclose(ls.cpu().numpy()[idx], lp.cpu().numpy()[idx], rtol=2e-5)
 
 
+def test_cv_spectral_ratio_table_reuse(ctx, kp):
+    # the Bessel-ratio table of a candidate list is kept between calls and reused when
+    # the same list comes back; a different list (even one of the same length) must be
+    # worked out again: results equal those of a fresh context, bit for bit
+    L = 2 * math.pi
+    u = to_dev_u(I.cv_sweep_load(4, 20000))
+    a = I.log_candidates(1.0, 1e4, 16)
+    b = I.log_candidates(2.0, 5e3, 16)
+    runs = []
+    for cands in (a, a, b, a, b[::-1]):
+        cv, am, loo = ctx.cv(u, L, cands, want_loo=True, spectral=True)
+        runs.append((cv, am, loo.cpu().numpy()))
+    fresh = kp.Context(0)
+    try:
+        for cands, (cv, am, loo) in zip((a, a, b, a, b[::-1]), runs):
+            cv2, am2, loo2 = fresh.cv(u, L, cands, want_loo=True, spectral=True)
+            fresh.close()
+            fresh = kp.Context(0)
+            np.testing.assert_array_equal(cv, cv2)
+            assert am == am2
+            np.testing.assert_array_equal(loo, loo2.cpu().numpy())
+    finally:
+        fresh.close()
+
+
 def test_cv_spectral_rejects_scale_mode(ctx, kp):
     u = to_dev_u(np.arange(100, dtype=np.uint32) * 40000)
     with pytest.raises(kp.KdeError):
