@@ -164,11 +164,12 @@ def oracle_sample(n_steps=10, N=1 << 12):
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    # each step: one width-update period (CV + 50 PIC steps) of a 2^15-particle sample
     for _ in range(args.warmup):
         oracle_sample(2)
     vals, times = [], []
     for _ in range(args.steps):
-        v, dt, cores, sample = oracle_sample(10)
+        v, dt, cores, sample = oracle_sample(LANDAU["period"], 1 << 15)
         vals.append(v)
         times.append(dt)
     value = float(np.mean(vals))
@@ -412,7 +413,8 @@ def run_ours(args, rank, world, local_rank):
         ad_variant = {"error": str(e)}
 
     try:
-        cpu_v, cpu_dt, cores, sample = oracle_sample(5, 1 << 12)
+        # one width-update period (CV + 50 PIC steps) of a 2^17-particle sample: 10-30 s of CPU work
+        cpu_v, cpu_dt, cores, sample = oracle_sample(LANDAU["period"], 1 << 17)
         cpu = {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                "seconds": cpu_dt}
     except Exception as e:  # the oracle needs gcc; report its absence instead of failing the bench
