@@ -413,8 +413,8 @@ def run_ours(args, rank, world, local_rank):
         ad_variant = {"error": str(e)}
 
     try:
-        # one width-update period (CV + 50 PIC steps) of a 2^17-particle sample: 10-30 s of CPU work
-        cpu_v, cpu_dt, cores, sample = oracle_sample(LANDAU["period"], 1 << 17)
+        # one width-update period (CV + 50 PIC steps) of a 2^18-particle sample: 10-30 s of CPU work
+        cpu_v, cpu_dt, cores, sample = oracle_sample(LANDAU["period"], 1 << 18)
         cpu = {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                "seconds": cpu_dt}
     except Exception as e:  # the oracle needs gcc; report its absence instead of failing the bench
