@@ -6,8 +6,11 @@
 //             warp are added once, by their leader) -> counts[bin][block]
 //             (bin-major, so that the destination order of the tiles' segments is
 //             the flat index bin * nblocks + block)
-//   scan    : exclusive scan of the flat counts array: tiles of 4096 scanned in
-//             place plus a one-block scan of the tile totals
+//   scan    : exclusive scan of the flat counts array in one kernel: tiles of 2048
+//             scanned in place, then the block that finishes last (a ticket in the
+//             context's status words, put back to zero) scans the tile totals.  A
+//             context's calls must not overlap on the GPU (they share the ticket as
+//             they share the workspace).
 //   scatter : each warp histograms its unit in shared memory, the block turns the
 //             warps' histograms into destination starts (its segment start plus the
 //             counts of the earlier warps), then every warp ranks equal keys in each
