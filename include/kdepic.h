@@ -24,6 +24,8 @@
  *   when the call's flags include KDE_F64.  Positions are always uint32.
  * - Ordering: calls enqueue work on the context's stream and return without
  *   synchronising, except those that return host values (kde_cv, kde_sync).
+ *   A context's calls must not overlap on the GPU (they share its workspace
+ *   and scratch words): use one context per stream or host thread.
  * - Errors: every call returns a kde_status.  Arguments are validated on the
  *   host before anything is launched; on failure nothing is enqueued and
  *   kde_last_error() describes the problem.  Device-side problems (a width out
