@@ -1027,8 +1027,13 @@ __global__ void adapt_apply_kernel(const float *loo, int64_t N, double xs, const
     if (i >= N) return;
     const double n = (double)N;
     double f = ((n - 1.0) * (double)loo[i] + s_K0) / n;
-    // lambda = (f/g)^-alpha, kappa = kappa* / lambda^2
-    double k = s_ks * exp(2.0 * alpha * (log(f) - s_logg));
+    // lambda = (f/g)^-alpha, kappa = kappa* / lambda^2; FP32 widths take FP32 base-2 logarithms
+    // (the log-mean of adapt_logsum_dev_kernel<true> is in the same base), FP64 widths FP64 ones
+    double k;
+    if constexpr (sizeof(T) == 4)
+        k = s_ks * (double)exp2f((float)(2.0 * alpha) * (log2f((float)f) - (float)s_logg));
+    else
+        k = s_ks * exp(2.0 * alpha * (log(f) - s_logg));
     k = k < kmin ? kmin : (k > kmax ? kmax : k);
     kappa_out[i] = (T)k;
     if (norm_out) {
@@ -1038,16 +1043,24 @@ __global__ void adapt_apply_kernel(const float *loo, int64_t N, double xs, const
     }
 }
 
-// the log-mean needs K0 = (2 pi / L) norm(kappa*) before kappa* is known on the host
+// the log-mean needs K0 = (2 pi / L) norm(kappa*) before kappa* is known on the host;
+// one thread of a block works it out (the FP64 Bessel series is slow here).  F32: base-2
+// logarithms in FP32 summed in FP64, for FP32 widths; otherwise natural FP64 logarithms
+template <bool F32>
 __global__ void adapt_logsum_dev_kernel(const float *loo, int64_t N, double xs, const double *kstar_dev, double kstar_h,
                                         double *part)
 {
     __shared__ double red[256];
+    __shared__ double s_K0;
     const double n = (double)N;
-    const double K0 = xs * kde_norm(kstar_dev ? *kstar_dev : kstar_h);
+    if (threadIdx.x == 0) s_K0 = xs * kde_norm(kstar_dev ? *kstar_dev : kstar_h);
+    __syncthreads();
+    const double K0 = s_K0;
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)AD_BLOCKS * 256)
-        s += log(((n - 1.0) * (double)loo[i] + K0) / n);
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)AD_BLOCKS * 256) {
+        const double f = ((n - 1.0) * (double)loo[i] + K0) / n;
+        s += F32 ? (double)log2f((float)f) : log(f);
+    }
     red[threadIdx.x] = s;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
@@ -1064,7 +1077,8 @@ kde_status kde_adapt_device(kde_ctx *ctx, const float *loo, int64_t N, double L,
     double *part = (double *)kde_ws(ctx, WS_CV_RED, AD_BLOCKS * 8);
     if (!part) return KDE_ENOMEM;
     const double xs = KDE_TWO_PI / L;
-    adapt_logsum_dev_kernel<<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part);
+    if (f64) adapt_logsum_dev_kernel<false><<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part);
+    else adapt_logsum_dev_kernel<true><<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part);
     KDE_LAUNCHED(ctx, "adapt_logsum_kernel");
     unsigned grid = (unsigned)((N + 255) / 256);
     if (f64)
