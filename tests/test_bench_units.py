@@ -1,7 +1,9 @@
-"""The bench's counts of algorithmic work (CV pairs, deposit and gather window pairs) against brute force."""
+"""The bench's counts of algorithmic work (CV pairs, deposit and gather window pairs) against brute force,
+and its Landau root solver against the textbook root."""
 import math
 
 import numpy as np
+import pytest
 
 import kde_inputs as I
 
@@ -36,3 +38,14 @@ def test_window_pair_count_matches_node_counts():
         counts = np.sum(d <= r, axis=1)
         est = grid_window_pairs(np.full(th.size, k), Ng)
         assert abs(counts.sum() - est) <= 0.01 * est + th.size * 1e-6
+
+
+def test_landau_theory_root():
+    # the bench's kinetic Langmuir root: k lambda_D = 0.5 gives omega = 1.41566 - 0.15336 i
+    # (textbook value); the statistics workload (k = 1) uses the same solver with a
+    # smoothing factor F of mode k, which lowers omega_p^2 by F^2 and changes the rate
+    from bench import landau_theory
+    assert landau_theory(1.0, k=0.5) == pytest.approx(-0.15336, abs=2e-5)
+    assert landau_theory(2.0, k=0.25) == pytest.approx(-0.15336, abs=2e-5)  # depends on k v_th only
+    g1, g2 = landau_theory(0.4, k=1.0), landau_theory(0.4, k=1.0, factor=0.98)
+    assert math.isfinite(g1) and math.isfinite(g2) and g1 != g2
