@@ -38,3 +38,17 @@ def test_damping_rate_host_entry(kp):
     W = np.exp(-0.3 * t) * np.cos(1.4 * t + 0.3) ** 2 + 1e-12
     g = kp.damping_rate(W, 0.1)
     assert abs(g + 0.15) < 0.01
+
+
+def test_null_context_is_rejected_on_the_host(kp):
+    # argument checks run on the host before anything touches CUDA: a null context gives
+    # KDE_EINVAL (1) and a readable error, with no GPU present
+    import ctypes
+    lib = kp.load_library()
+    n = ctypes.c_int32(-1)
+    assert lib.kde_set_autotune(None, 1) == 1
+    assert lib.kde_autotune_entries(None, ctypes.addressof(n)) == 1 and n.value == -1
+    assert lib.kde_sync(None) == 1
+    assert lib.kde_destroy(None) == 1
+    assert lib.kde_set_stream(None, None) == 1
+    assert lib.kde_last_error(None) == b"null context"
