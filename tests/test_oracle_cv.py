@@ -164,3 +164,67 @@ def test_adaptive_widths_geometric_mean_and_order(oracle):
     # clamping
     kc = oracle.adapt_widths(loo, L, kstar, 0.5, kmin=55.0, kmax=65.0)
     assert kc.min() >= 55.0 and kc.max() <= 65.0
+
+
+def _two_cluster_sample(n_dense=48, n_sparse=5):
+    # a tight cluster around theta = 1 plus a few isolated points: the isolated points'
+    # leave-one-out densities are far below their own kernel's peak, so the pilot with
+    # and without the self term differ by orders of magnitude there
+    th_dense = 1.0 + 0.08 * (I.uniforms(21, 0, n_dense) - 0.5)
+    th_sparse = 2.0 + (2 * math.pi - 2.5) * (np.arange(n_sparse) + 0.5) / n_sparse
+    return np.concatenate([th_dense, th_sparse])
+
+
+def _pilot_full_kde(th, kstar, L):
+    # pilot estimate f~(X_i): the KDE at kappa* evaluated at X_i over all n samples,
+    # its own kernel included (x units), by direct summation with SciPy's i0e
+    d = th[:, None] - th[None, :]
+    K = np.exp(kstar * (np.cos(d) - 1.0)) / (2 * math.pi * sp.i0e(kstar))
+    return (2 * math.pi / L) * K.mean(axis=1)
+
+
+def _loo_direct(th, kstar, L):
+    n = th.size
+    d = th[:, None] - th[None, :]
+    K = np.exp(kstar * (np.cos(d) - 1.0)) / (2 * math.pi * sp.i0e(kstar))
+    np.fill_diagonal(K, 0.0)
+    return (2 * math.pi / L) * K.sum(axis=1) / (n - 1)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.3])
+def test_adaptive_widths_pilot_includes_self_term(oracle, alpha):
+    # Sec. II.C with Silverman's pilot: lambda_i = (f~(X_i)/g)^(-alpha), g the geometric
+    # mean of f~, h_i = h lambda_i, kappa = 1/h^2.  The pilot here is the full KDE at X_i
+    # computed directly (not from the leave-one-out sums); the reading without the self
+    # term must fail on this sample.
+    L = 4 * math.pi
+    th = _two_cluster_sample()
+    kstar = 300.0
+    loo = _loo_direct(th, kstar, L)
+    k = oracle.adapt_widths(loo, L, kstar, alpha)
+    ft = _pilot_full_kde(th, kstar, L)
+    lam = np.exp(-alpha * (np.log(ft) - np.mean(np.log(ft))))
+    np.testing.assert_allclose(k, kstar / lam ** 2, rtol=1e-10)
+    lam_no_self = np.exp(-alpha * (np.log(loo) - np.mean(np.log(loo))))
+    assert np.max(np.abs(kstar / lam_no_self ** 2 / k - 1.0)) > 0.5
+
+
+def test_adaptive_widths_scale_the_kernel_width_by_lambda(oracle):
+    # h_i = h lambda_i (Sec. II.C) measured on the kernels themselves: the circular
+    # standard deviation sqrt(2 (1 - A_1(kappa))) of a von Mises kernel is
+    # kappa^(-1/2) (1 + O(1/kappa)), so the ratio of kernel widths must equal lambda_i
+    # to O(1/kappa).  A_1 from SciPy's ive.  Mapping kappa_i = kappa*/lambda_i (an h^2
+    # scaling) would give sqrt(lambda_i) instead.
+    L = 2 * math.pi
+    th = _two_cluster_sample(64, 6)
+    kstar = 2500.0
+    loo = _loo_direct(th, kstar, L)
+    k = oracle.adapt_widths(loo, L, kstar, 0.5)
+    ft = _pilot_full_kde(th, kstar, L)
+    lam = (ft / np.exp(np.mean(np.log(ft)))) ** -0.5
+    assert lam.max() / lam.min() > 4.0                   # the sample spans a wide range
+    A1 = lambda kk: sp.ive(1, kk) / sp.ive(0, kk)
+    width = np.sqrt(2 * (1 - A1(k)))
+    width_star = math.sqrt(2 * (1 - A1(kstar)))
+    rel = width / width_star / lam - 1.0
+    assert np.max(np.abs(rel)) < 0.5 / k.min()

@@ -167,3 +167,107 @@ def test_push_leapfrog(oracle):
     xn, vn = oracle.push(x, v, Ei, L, dt=0.1, qm=-1.0, kick=0.5)
     np.testing.assert_allclose(vn, [1.0 - 0.5 * 0.2 * 0.1, 0.5 + 0.5 * 0.4 * 0.1])
     np.testing.assert_allclose(xn, np.mod(x + vn * 0.1, L))
+
+
+@pytest.mark.parametrize("Ng", [8, 37, 256])
+def test_field_energy_single_sine_closed_form(oracle, Ng):
+    # W = 1/2 sum_g E_g^2 dx (Sec. III.B).  For E_g = a sin(2 pi m g / Ng) with
+    # 0 < m < Ng/2, sum_g sin^2 = Ng/2, so W = a^2 L / 4 exactly; a constant field c
+    # gives W = c^2 L / 2.
+    L = 4 * math.pi
+    a = 0.37
+    g = np.arange(Ng)
+    for m in (1, 3):
+        E = a * np.sin(2 * math.pi * m * g / Ng)
+        assert oracle.field_energy(E, L) == pytest.approx(a * a * L / 4, rel=1e-13)
+    assert oracle.field_energy(np.full(Ng, 1.5), L) == pytest.approx(1.5 * 1.5 * L / 2, rel=1e-14)
+
+
+def test_field_energy_exchanges_with_kinetic_energy(oracle):
+    # Cold Langmuir oscillation: with deposit and gather through one kernel,
+    # d/dt (1/2 int E^2 dx) = sum_i w v_i E_i = -d/dt (1/2 sum_i w v_i^2)
+    # (Ampere's law dE/dt = -J from continuity and Gauss's law), so the field energy
+    # reported by the oracle plus the kinetic energy of the electrons (mass w = L/N
+    # each, q/m = -1) stays at its t = 0 value, when all of it sits in the field.
+    # A dropped 1/2 or dx in the field energy breaks the balance by a factor >= 2.
+    L = 4 * math.pi
+    N, Ng, kappa, dt = 4096, 64, 10.0, 0.05
+    x = I.from_fixed(I.to_fixed(I.quiet_positions(N, L, 0.01), L), L)
+    v = np.zeros(N)
+    w = L / N
+
+    def field_at(xx):
+        rho = oracle.deposit(xx, Ng, L, kappa_u=kappa)
+        E = oracle.poisson(1.0 - rho, L)
+        return E, oracle.gather(xx, E, L, kappa_u=kappa)
+
+    E, Ei = field_at(x)
+    W0 = oracle.field_energy(E, L)
+    assert W0 > 0
+    x, v = oracle.push(x, v, Ei, L, dt, -1.0, kick=0.5)   # v^{1/2}, x^1
+    ke_prev = 0.5 * w * float(np.sum(v * v))
+    totals, kes = [], []
+    for _ in range(140):                                  # ~ one plasma period
+        E, Ei = field_at(x)
+        Wf = oracle.field_energy(E, L)
+        x, v = oracle.push(x, v, Ei, L, dt, -1.0)
+        ke = 0.5 * w * float(np.sum(v * v))
+        totals.append(Wf + 0.5 * (ke_prev + ke))
+        kes.append(ke)
+        ke_prev = ke
+    totals = np.array(totals)
+    assert np.max(np.abs(totals - W0)) < 0.005 * W0
+    assert max(kes) == pytest.approx(W0, rel=0.005)
+
+
+def test_kde_at_single_particle(oracle):
+    # Eq. (kde) for one particle of weight w: (2 pi / L) w K_kappa(theta_p - theta_1),
+    # the von Mises density.  Normalisation from SciPy (i0e; the vonmises
+    # distribution for moderate widths), not the oracle's own Bessel function.
+    import scipy.stats as st
+    L = 4 * math.pi
+    x1 = np.array([2.3])
+    xp = np.linspace(0.0, L, 53, endpoint=False) + 0.011
+    dth = 2 * math.pi * (xp - x1[0]) / L
+    for k in (0.5, 7.0, 40.0, 3000.0):
+        out = oracle.kde_at(x1, xp, L, kappa_u=k, w=np.array([1.7]))
+        ref = (2 * math.pi / L) * 1.7 * np.exp(k * (np.cos(dth) - 1.0)) / (2 * math.pi * sp.i0e(k))
+        np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-300)
+        if k <= 40.0:
+            ref2 = (2 * math.pi / L) * 1.7 * st.vonmises.pdf(dth, k)
+            np.testing.assert_allclose(out, ref2, rtol=1e-9)
+    # default weight L/N with N = 1 is L
+    out = oracle.kde_at(x1, xp, L, kappa_u=7.0)
+    np.testing.assert_allclose(out, 2 * math.pi * np.exp(7.0 * (np.cos(dth) - 1.0)) / (2 * math.pi * sp.i0e(7.0)),
+                               rtol=1e-12)
+
+
+@pytest.mark.parametrize("k,N", [(3.0, 5), (45.0, 16), (900.0, 96)])
+def test_kde_at_evenly_spaced_between_nodes(oracle, k, N):
+    # N evenly spaced particles, default weights L/N: the KDE is the Fourier series
+    # 1 + 2 sum_p A_pN(kappa) cos(pN (theta - phi)) everywhere, evaluated here at
+    # random points that are not grid nodes.
+    L = 3.0
+    phi = 1.1
+    x = (np.arange(N) / N + phi / (2 * math.pi)) * L
+    xp = I.uniforms(11, 0, 41) * L
+    out = oracle.kde_at(x, xp, L, kappa_u=k)
+    th = 2 * math.pi * xp / L
+    ref = np.ones_like(th)
+    for p in range(1, 60):
+        ref += 2 * A(p * N, k) * np.cos(p * N * (th - phi))
+    np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-13)
+
+
+def test_kde_at_per_particle_widths_superpose(oracle):
+    L = 2.0
+    x = np.array([0.2, 0.9, 1.7])
+    kap = np.array([4.0, 250.0, 60.0])
+    w = np.array([0.5, 1.25, 2.0])
+    xp = I.uniforms(12, 0, 29) * L
+    out = oracle.kde_at(x, xp, L, kappa=kap, w=w)
+    ref = np.zeros_like(xp)
+    for xi, ki, wi in zip(x, kap, w):
+        d = 2 * math.pi * (xp - xi) / L
+        ref += (2 * math.pi / L) * wi * np.exp(ki * (np.cos(d) - 1.0)) / (2 * math.pi * sp.i0e(ki))
+    np.testing.assert_allclose(out, ref, rtol=1e-12)
