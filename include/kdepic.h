@@ -56,12 +56,21 @@ typedef int kde_status;
 #define KDE_ECUDA 3    /* a CUDA runtime call failed */
 #define KDE_EDEVICE 4  /* a kernel reported a problem through the device status word */
 #define KDE_ENOTSUP 5  /* combination of options not supported */
+#define KDE_ECANCELED 6 /* request server: the request was cancelled before it started */
+#define KDE_EBUSY 7     /* request server: the request has started and can no longer be cancelled */
 
 /* flags */
 #define KDE_F64 0x1u         /* real arrays are float64 and arithmetic is FP64 */
 #define KDE_POISSON_FD 0x2u  /* finite-difference Poisson (Sec. III.A) instead of spectral */
 #define KDE_CV_SCALE 0x4u    /* kde_cv: candidates scale per-particle widths kappa_rel */
 #define KDE_CV_SPECTRAL 0x8u /* kde_cv / pic_step: exact Fourier form of the CV (uniform widths) */
+#define KDE_CV_PAIRS 0x10u   /* kde_cv / pic_step: O(N^2) pair sums of the CV (uniform widths) */
+/* Uniform candidate widths without either flag: both forms are exact, and a
+ * cost rule picks the cheaper one per call -- the Fourier form when
+ * 8 M(kappa_max) < N sum_c frac(kappa_c), with M(kappa) the Fourier modes the
+ * exact form keeps and frac(kappa) the share of the circle inside a kernel's
+ * truncation radius (pair sums cost N^2 frac / 2 exponentials per candidate,
+ * the Fourier form about 4 N M(kappa_max) for all candidates together). */
 
 /* Maximum grid size accepted by deposit / gather / Poisson / pic_step. */
 #define KDE_MAX_NG 4096
@@ -98,12 +107,27 @@ kde_status kde_sync(kde_ctx *ctx);
 kde_status kde_set_autotune(kde_ctx *ctx, int32_t enable);
 kde_status kde_autotune_entries(const kde_ctx *ctx, int32_t *n_out);
 
+/* Limit of the bounded device-side waits (no counterpart in the paper: a
+ * robustness facility of this library).  The CV kernels stage column tiles with
+ * bulk copies and wait for each on an mbarrier; a wait that has not seen its copy
+ * land after `polls` polls gives up: the kernel waits (with the default limit)
+ * for every copy it still has in flight, sets the device status word and stops,
+ * and the next kde_cv / kde_sync returns KDE_EDEVICE ("device wait timed out").
+ * The context stays usable.  polls < 0 restores the default (2^26 polls);
+ * polls = 0 makes every such wait give up at once (this exercises the error path
+ * without a fault).  KDE_EINVAL above 2^32 - 1. */
+kde_status kde_set_wait_limit(kde_ctx *ctx, int64_t polls);
+
 /* Grow the workspace for problems of up to N particles, grids of up to Ng nodes
  * and up to n_cand CV candidates, so that later calls allocate nothing. */
 kde_status kde_reserve(kde_ctx *ctx, int64_t N, int32_t Ng, int32_t n_cand);
 
-/* Position encoding: u_i = floor(x_i / L * 2^32) after wrapping x_i into [0, L).
- * x: device float64[N]; u_out: device uint32[N].  N >= 0, L > 0. */
+/* Position encoding on the periodic domain (Sec. III.A, periodic boundary):
+ *   u_i = floor(frac(x_i / L) * 2^32),  frac(t) = t - floor(t),
+ * with x_i / L the correctly rounded FP64 quotient, so positions outside [0, L)
+ * wrap.  A fraction that rounds up to 1 (a tiny negative x_i) gives 2^32 - 1; a
+ * NaN position gives 0.  x: device float64[N]; u_out: device uint32[N].
+ * N >= 0 (N = 0 enqueues nothing), L > 0; KDE_EINVAL otherwise. */
 kde_status kde_pack_positions(kde_ctx *ctx, const double *x, int64_t N, double L, uint32_t *u_out);
 
 /* Deposit (Eq. kde at the grid nodes; per-particle widths as in Sec. II.C):
@@ -132,9 +156,10 @@ kde_status kde_deposit(kde_ctx *ctx, const uint32_t *u, const void *kappa, doubl
  * (98,560 bytes) that every GPU which loads the library holds until the
  * process exits.  Limits: Ng <= KDE_NOALLOC_MAX_NG (4096); larger grids return
  * KDE_EINVAL.  Particles may come in any order; cell-sorted input runs fastest
- * (an unsorted chunk falls back to every node of the grid).  The first call on
- * a device (with that device current) looks up the array's device address; make
- * that first call before any stream capture.  All calls share the one array,
+ * (an unsorted chunk falls back to every node of the grid).  Every call looks up
+ * the array's address on the current device (cudaGetSymbolAddress, checked); the
+ * first call on a device may load the library's module there, so make that first
+ * call before any stream capture.  All calls share the one array,
  * which keeps the previous call's contents (the accumulators are cleared at
  * the start of each call): calls that overlap on the GPU -- on different
  * streams or from different host threads -- race and must be serialised by the
@@ -261,7 +286,8 @@ typedef struct pic_state {
     double *energy;       /* device float64[steps] field energy per step (indexed by step), or NULL */
     double *kappa_star;   /* device float64[steps] CV width in force per step, or NULL */
     int64_t step;         /* step counter (in/out); step 0 gets a half velocity kick */
-    uint32_t flags;       /* KDE_F64, KDE_POISSON_FD, KDE_CV_SPECTRAL (width schedule); PIC_NO_BACKSTEP */
+    uint32_t flags;       /* KDE_F64, KDE_POISSON_FD, KDE_CV_SPECTRAL or KDE_CV_PAIRS (form of the
+                             schedule's CV; neither: the cost rule), PIC_NO_BACKSTEP */
     /* Width-update algorithm of Sec. II.D on the uniform width (kappa == NULL;
      * replaces width_every).  Every step, before the deposit: ln p of the
      * Anderson-Darling test of the positions; if p > 2 ad_threshold then
@@ -295,6 +321,19 @@ typedef struct pic_state {
  * Stream-ordered; no host synchronisation except the width_ad schedule's one
  * read of the p-value (and of the CV argmin on optimisation steps) per step. */
 kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps);
+
+/* pic_step on a state held in HOST memory (no counterpart in the paper: the
+ * end-to-end form of the call for callers whose particles live on the host).
+ * The pointer fields of *st -- u, v, kappa, id, and the histories energy,
+ * kappa_star, ad_log_p (indexed by step) -- are HOST arrays of the sizes
+ * pic_step documents; kappa_norm is ignored (the library keeps the norms on the
+ * device).  The call copies the state into device buffers owned by the context,
+ * runs n_steps of pic_step there, copies the state and the n_steps new history
+ * entries back into the same host arrays, updates st's scalar state (step, the
+ * uniform width and the Sec. II.D schedule state) and synchronises.  Page-locked
+ * host memory makes the copies direct DMA; pageable memory works, more slowly.
+ * Errors as pic_step; device buffers grow like the workspace. */
+kde_status pic_step_host(kde_ctx *ctx, pic_state *st, int32_t n_steps);
 
 /* Damping rate (Sec. III.B) from a field-energy history on the HOST: half the
  * slope of ln W through the first two strict local maxima at steps >= 1.
@@ -399,6 +438,27 @@ kde_status kde_server_submit(kde_server *srv, const kde_request *req, int64_t *t
 /* Wait for a ticket; returns the request's status and the times (ms) from
  * submission and from admission to completion.  Each ticket is waited once. */
 kde_status kde_server_wait(kde_server *srv, int64_t ticket, double *latency_ms, double *service_ms);
+/* Like kde_server_wait, with the times in times[4]: latency from submission and
+ * service time from admission (host clock, ms), then the device-clock interval
+ * of the request on its slot's stream -- from an event recorded before its first
+ * copy to one recorded after its last -- in ms since the server was created (-1
+ * when not available, e.g. for a cancelled request).  Intervals of requests
+ * served by different slots that intersect show their work overlapping. */
+kde_status kde_server_wait_times(kde_server *srv, int64_t ticket, double *times);
+/* Cancel a request that is still queued: it never runs and its wait returns
+ * KDE_ECANCELED.  KDE_EBUSY once it has been admitted (running or done);
+ * KDE_EINVAL for an unknown ticket. */
+kde_status kde_server_cancel(kde_server *srv, int64_t ticket);
+/* HBM accounting and counters (host snapshot): stats[0] committed device bytes
+ * now (transient buffers of running requests + workspace held by the slots'
+ * contexts), stats[1] the largest committed total seen at an admission,
+ * stats[2] the budget, stats[3] requests served, stats[4] cancelled, stats[5]
+ * queued, stats[6] workspaces released to admit a request, stats[7] workspace
+ * held now.  A request is admitted only while the committed total plus its
+ * buffers and its slot's workspace growth fits the budget (or when it is the only
+ * one running), so stats[1] stays within the budget unless a request's actual
+ * workspace outgrows its estimate. */
+kde_status kde_server_stats(kde_server *srv, int64_t *stats);
 /* Finish the queued requests, stop the slots and release everything. */
 kde_status kde_server_destroy(kde_server *srv);
 

@@ -20,7 +20,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Context", "PicState", "Server", "Ensemble", "KdeError", "load_library", "LIB_PATH", "F64", "POISSON_FD", "CV_SCALE", "CV_SPECTRAL",
+__all__ = ["Context", "PicState", "Server", "Ensemble", "KdeError", "load_library", "LIB_PATH", "F64", "POISSON_FD", "CV_SCALE", "CV_SPECTRAL", "CV_PAIRS",
            "PIC_NO_BACKSTEP", "MAX_NG"]
 
 LIB_PATH = _build.LIB
@@ -28,6 +28,7 @@ F64 = 0x1
 POISSON_FD = 0x2
 CV_SCALE = 0x4
 CV_SPECTRAL = 0x8
+CV_PAIRS = 0x10
 PIC_NO_BACKSTEP = 0x100
 MAX_NG = 4096
 
@@ -107,6 +108,7 @@ def load_library(path: str | None = None):
         "kde_ensemble_destroy": (S, [_P]),
         "kde_adapt_widths": (S, [_P, _P, _I64, _D, _D, _D, _D, _D, _P]),
         "pic_step": (S, [_P, ctypes.POINTER(_PicState), _I32]),
+        "pic_step_host": (S, [_P, ctypes.POINTER(_PicState), _I32]),
         "kde_damping_rate": (S, [_P, _I64, _D, _P]),
         "kde_probe_exp2": (S, [_P, _I64, _P, _P]),
         "kde_probe_fma": (S, [_P, _I64, _P, _P]),
@@ -115,9 +117,13 @@ def load_library(path: str | None = None):
         "kde_server_create": (S, [ctypes.POINTER(_P), ctypes.c_int, _I32, _I64]),
         "kde_server_submit": (S, [_P, ctypes.POINTER(_Request), ctypes.POINTER(_I64)]),
         "kde_server_wait": (S, [_P, _I64, _P, _P]),
+        "kde_server_wait_times": (S, [_P, _I64, _P]),
+        "kde_server_cancel": (S, [_P, _I64]),
+        "kde_server_stats": (S, [_P, _P]),
         "kde_server_destroy": (S, [_P]),
         "kde_profile_read": (S, [_P, ctypes.c_int, _P, _P]),
         "kde_set_autotune": (S, [_P, ctypes.c_int32]),
+        "kde_set_wait_limit": (S, [_P, _I64]),
         "kde_autotune_entries": (S, [_P, _P]),
     }
     for name, (res, args) in sigs.items():
@@ -223,16 +229,18 @@ class Context:
                                                       _ptr(field), field.numel(), float(L), _ptr(out), flags))
         return out
 
-    def cv(self, u, L: float, cand, kappa_rel=None, loo=None, want_loo: bool = False, spectral: bool = False):
+    def cv(self, u, L: float, cand, kappa_rel=None, loo=None, want_loo: bool = False, spectral: bool = False,
+           pairs: bool = False):
         """kde_cv: CV(kappa_c) (x units) for every candidate; returns (cv, argmin, loo).
-        spectral=True selects the exact Fourier form (uniform widths)."""
+        spectral=True selects the exact Fourier form, pairs=True the O(N^2) pair sums
+        (uniform widths); neither: the library's cost rule picks the cheaper exact form."""
         torch = _torch()
         cand = np.ascontiguousarray(cand, dtype=np.float64)
         cv = np.empty(cand.size, dtype=np.float64)
         am = ctypes.c_int32()
         if want_loo and loo is None:
             loo = self._new(u.numel(), torch.float32)
-        flags = (CV_SCALE if kappa_rel is not None else 0) | (CV_SPECTRAL if spectral else 0)
+        flags = (CV_SCALE if kappa_rel is not None else 0) | (CV_SPECTRAL if spectral else 0) | (CV_PAIRS if pairs else 0)
         self._check("kde_cv", self.lib.kde_cv(self.h, _ptr(u), _ptr(kappa_rel), u.numel(), float(L),
                                               cand.ctypes.data, cand.size, cv.ctypes.data, ctypes.addressof(am),
                                               _ptr(loo), flags))
@@ -292,8 +300,23 @@ class Context:
         state._sync_in()
         self._check("pic_step", self.lib.pic_step(self.h, ctypes.byref(state.c), int(n_steps)))
 
+    def pic_step_host(self, state: "PicState", n_steps: int):
+        """pic_step_host: pic_step on a state whose tensors live in host memory (pinned for
+        DMA): the library copies it in, runs, copies it back and synchronises."""
+        if state.u.is_cuda or state.v.is_cuda:
+            raise KdeError("pic_step_host", 1, "the state's tensors must be host tensors")
+        if state.max_steps and state.c.step + int(n_steps) > state.max_steps:
+            raise KdeError("pic_step_host", 1, "history holds %d steps; step %d + %d would overflow it"
+                           % (state.max_steps, state.c.step, n_steps))
+        state._sync_in()
+        self._check("pic_step_host", self.lib.pic_step_host(self.h, ctypes.byref(state.c), int(n_steps)))
+
     PROF = {"cv_pairs": 0, "deposit": 1, "gather": 2, "sort": 3, "poisson": 4, "cv_grid": 5, "cv_loo": 6,
             "spectral": 7, "ad": 8}
+
+    def set_wait_limit(self, polls: int = -1):
+        """kde_set_wait_limit: polls of a bounded device wait (-1: default, 0: give up at once)."""
+        self._check("kde_set_wait_limit", self.lib.kde_set_wait_limit(self.h, int(polls)))
 
     def set_autotune(self, on: bool = True):
         """kde_set_autotune: tune the FP32 gather's tile shape per key on first use."""
@@ -370,6 +393,7 @@ class PicState:
                  qm: float = -1.0, charge: float = -1.0, background: float = 1.0, width_every: int = 0,
                  cand=None, alpha: float = 0.5, kappa_min: float = 0.0, kappa_max: float = 1e6,
                  max_steps: int = 0, fd: bool = False, backstep: bool = True, cv_spectral: bool = False,
+                 cv_pairs: bool = False,
                  width_ad: bool = False, ad_threshold: float = 0.01, adjust_rate: float = 0.05,
                  shape_order: int = 0, shape_h: float = 0.0):
         torch = _torch()
@@ -392,7 +416,7 @@ class PicState:
         c.alpha, c.kappa_min, c.kappa_max = float(alpha), float(kappa_min), float(kappa_max)
         c.step = 0
         c.flags = ((F64 if f64 else 0) | (POISSON_FD if fd else 0) | (0 if backstep else PIC_NO_BACKSTEP)
-                   | (CV_SPECTRAL if cv_spectral else 0))
+                   | (CV_SPECTRAL if cv_spectral else 0) | (CV_PAIRS if cv_pairs else 0))
         c.width_ad = int(bool(width_ad))
         c.ad_threshold, c.adjust_rate = float(ad_threshold), float(adjust_rate)
         c.ad_log_pth, c.h_target, c.n_opt = 0.0, 0.0, 0
@@ -526,14 +550,30 @@ class Server:
         self.keep[t.value] = (arrs, am)
         return t.value
 
-    def wait(self, ticket):
-        lat = ctypes.c_double()
-        svc = ctypes.c_double()
-        rc = self.lib.kde_server_wait(self.h, int(ticket), ctypes.addressof(lat), ctypes.addressof(svc))
+    def wait(self, ticket, times=False):
+        """kde_server_wait_times: (latency ms, service ms, argmin), plus the device-clock
+        interval (start, end) in ms since the server started when times=True."""
+        t = (ctypes.c_double * 4)()
+        rc = self.lib.kde_server_wait_times(self.h, int(ticket), ctypes.addressof(t))
         arrs, am = self.keep.pop(ticket)
         if rc != 0:
             raise KdeError("kde_server_wait", rc, "request failed")
-        return lat.value, svc.value, int(am[0])
+        if times:
+            return t[0], t[1], int(am[0]), (t[2], t[3])
+        return t[0], t[1], int(am[0])
+
+    def cancel(self, ticket) -> int:
+        """kde_server_cancel: 0 if the queued request was cancelled, else the status code."""
+        return int(self.lib.kde_server_cancel(self.h, int(ticket)))
+
+    def stats(self) -> dict:
+        """kde_server_stats: HBM accounting and counters."""
+        a = (ctypes.c_int64 * 8)()
+        rc = self.lib.kde_server_stats(self.h, ctypes.addressof(a))
+        if rc != 0:
+            raise KdeError("kde_server_stats", rc, "bad server")
+        keys = ["committed", "committed_peak", "budget", "served", "cancelled", "queued", "trims", "held"]
+        return dict(zip(keys, list(a)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -19,6 +19,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/kdepic.h"
 
 #define KDE_PI 3.14159265358979323846
@@ -83,6 +85,12 @@ enum WsSlot {
     WS_AD_OUT,
     WS_CV_GPAR,
     WS_GREEN,
+    WS_HOST_U,     // device copies of a host-resident PIC state (pic_step_host)
+    WS_HOST_V,
+    WS_HOST_K,
+    WS_HOST_NORM,
+    WS_HOST_ID,
+    WS_HOST_HIST,  // energy, kappa* and ln p histories
     WS_NSLOTS
 };
 
@@ -110,6 +118,7 @@ struct kde_ctx {
     // Anderson-Darling per-bin logarithms (one table per context)
     void *ad_tab = nullptr;
     float2 *norm_tab = nullptr;  // FP32 width-normalisation table (kde_norm_tab), built at creation
+    unsigned wait_polls = 1u << 26;         // polls of a bounded device wait (kde_set_wait_limit)
     bool autotune = false;                  // kde_set_autotune
     std::map<uint64_t, int> gat2_tuned;     // packed-gather tile shape per key (gather.cu)
     void *sp_atab = nullptr;                // workspace holding the Bessel ratios of sp_atab_cands (spectral.cu)
@@ -164,6 +173,16 @@ struct KdeProfScope {
             c->prof.push_back({id, {b, e}});
         }
     }
+};
+
+// NVTX range around the host-side launches of one stage (sort, deposit, Poisson,
+// gather + push, width update, CV pieces), so that a profiler's timeline groups
+// each stage's kernels; without a profiler attached the calls do nothing
+struct KdeRange {
+    explicit KdeRange(const char *name) { nvtxRangePushA(name); }
+    ~KdeRange() { nvtxRangePop(); }
+    KdeRange(const KdeRange &) = delete;
+    KdeRange &operator=(const KdeRange &) = delete;
 };
 
 // number of nodes on each side of a particle's cell that its truncated kernel
@@ -418,6 +437,8 @@ kde_status kde_ad_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double *out
 kde_status kde_loo_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *cand_host,
                                    int n_cand, const int *argmin_dev, float *loo);
 int kde_spec_modes(double kappa);  // Fourier modes the exact form keeps for a width
+// the cost rule between the exact forms of a uniform-width CV curve (true: Fourier form)
+bool kde_cv_prefer_spectral(int64_t N, const double *cand, int n_cand);
 
 // the same results by the exact Fourier form (uniform widths only)
 kde_status kde_cv_spectral_device(kde_ctx *ctx, const uint32_t *u, int64_t N, double L, const double *cand_host,

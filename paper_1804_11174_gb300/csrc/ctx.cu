@@ -247,6 +247,14 @@ extern "C" kde_status kde_set_autotune(kde_ctx *ctx, int32_t enable)
     return KDE_OK;
 }
 
+extern "C" kde_status kde_set_wait_limit(kde_ctx *ctx, int64_t polls)
+{
+    if (!ctx) return KDE_EINVAL;
+    if (polls > 0xFFFFFFFFll) return kde_fail(ctx, KDE_EINVAL, "kde_set_wait_limit: at most 2^32 - 1 polls");
+    ctx->wait_polls = polls < 0 ? (1u << 26) : (unsigned)polls;
+    return KDE_OK;
+}
+
 extern "C" kde_status kde_autotune_entries(const kde_ctx *ctx, int32_t *n_out)
 {
     if (!ctx || !n_out) return KDE_EINVAL;
@@ -299,11 +307,15 @@ extern "C" kde_status kde_reserve(kde_ctx *ctx, int64_t N, int32_t Ng, int32_t n
 // ---------------------------------------------------------------------------
 // position packing
 // ---------------------------------------------------------------------------
-__global__ void pack_kernel(const double *x, int64_t N, double invL, uint32_t *u)
+// u = floor(frac(x / L) * 2^32): an IEEE division (not a multiplication by a
+// rounded 1/L), so that the code is the correctly rounded quotient's.  frac
+// wraps negative positions and positions >= L; a fraction that rounds up to 1
+// (tiny negative x) clamps to the last code.
+__global__ void pack_kernel(const double *x, int64_t N, double L, uint32_t *u)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double t = x[i] * invL;
+    double t = __ddiv_rn(x[i], L);
     t -= floor(t);
     double q = floor(t * 4294967296.0);
     if (q > 4294967295.0) q = 4294967295.0;
@@ -318,7 +330,7 @@ extern "C" kde_status kde_pack_positions(kde_ctx *ctx, const double *x, int64_t 
         return kde_fail(ctx, KDE_EINVAL, "kde_pack_positions: need N >= 0, L > 0 and non-null arrays");
     if (N == 0) return KDE_OK;
     cudaSetDevice(ctx->device);
-    pack_kernel<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(x, N, 1.0 / L, u_out);
+    pack_kernel<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(x, N, L, u_out);
     KDE_LAUNCHED(ctx, "pack_kernel");
     return KDE_OK;
 }

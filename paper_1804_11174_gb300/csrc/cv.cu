@@ -64,10 +64,10 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-// returns false if the phase did not complete within CV_WAIT_LIMIT polls
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+// returns false if the phase did not complete within `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit = CV_WAIT_LIMIT)
 {
-    for (unsigned it = 0; it < CV_WAIT_LIMIT; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -77,6 +77,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
         if (done) return true;
     }
     return false;
+}
+
+// Wait for the staged tile of buffer `cur`.  Thread 0 polls with the context's
+// limit (`polls`) and broadcasts the outcome; on success every other thread
+// observes the completed phase too (its wait returns at once), so all of them
+// read the tile after the barrier's acquire.  On failure every copy still in
+// flight -- the late one and the prefetch issued after it -- is waited for with
+// the full limit before the caller leaves, so no bulk copy lands in shared
+// memory that the CTA has given up.  Returns false on failure (the caller flags
+// KDE_DEV_WAIT_TIMEOUT and stops).
+__device__ __forceinline__ bool tile_wait(uint64_t *bar, unsigned *phase, int cur, bool next_pending, unsigned polls,
+                                          int *s_stop, unsigned int *status)
+{
+    const int tid = threadIdx.x;
+    if (tid == 0) *s_stop = mbar_wait(&bar[cur], phase[cur], polls) ? 0 : 1;
+    __syncthreads();
+    if (*s_stop) {
+        const bool a = mbar_wait(&bar[cur], phase[cur]);
+        const bool b = !next_pending || mbar_wait(&bar[cur ^ 1], phase[cur ^ 1]);
+        if (tid == 0 && !(a && b)) kde_flag(status, KDE_DEV_WAIT_TIMEOUT, 0xffffffffu);
+        return false;
+    }
+    if (tid != 0) mbar_wait(&bar[cur], phase[cur]);
+    phase[cur] ^= 1u;
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -222,6 +247,7 @@ struct CvPairArgs {
     const float *lnorm;
     double *part;  // [gridDim.x][n]
     unsigned int *status;
+    unsigned wait_polls;  // polls of a tile wait before the kernel gives up
 };
 
 template <bool SCALE>
@@ -277,7 +303,6 @@ __global__ void __launch_bounds__(CV_T) cv_pairs_kernel(CvPairArgs A, CvCands cc
     int b_cur = 0, d_cur = 0;
     bool have = fetch(b_cur, d_cur);
     if (have && tid == 0) tma_load_1d(buf[0], A.sc + (size_t)b_cur * CV_T, CV_T * sizeof(float2), &bar[0]);
-    bool pending[2] = {have, false};
     unsigned phase[2] = {0u, 0u};
     bool failed = false;
     for (int k = 0; have; ++k) {
@@ -286,13 +311,7 @@ __global__ void __launch_bounds__(CV_T) cv_pairs_kernel(CvPairArgs A, CvCands cc
         const bool next = fetch(b_nxt, d_nxt);
         if (next && tid == 0)
             tma_load_1d(buf[cur ^ 1], A.sc + (size_t)b_nxt * CV_T, CV_T * sizeof(float2), &bar[cur ^ 1]);
-        pending[cur ^ 1] = next;
-        const bool ok = mbar_wait(&bar[cur], phase[cur]);
-        phase[cur] ^= 1u;
-        pending[cur] = false;
-        if (tid == 0) s_stop = ok ? 0 : 1;
-        __syncthreads();
-        if (s_stop) {
+        if (!tile_wait(bar, phase, cur, next, A.wait_polls, &s_stop, A.status)) {
             failed = true;
             break;
         }
@@ -359,10 +378,6 @@ __global__ void __launch_bounds__(CV_T) cv_pairs_kernel(CvPairArgs A, CvCands cc
         have = next;
     }
     if (failed && tid == 0) kde_flag(A.status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
-    // drain any copy still in flight before the CTA's shared memory goes away
-    for (int q = 0; q < 2; ++q)
-        if (pending[q] && !mbar_wait(&bar[q], phase[q]) && tid == 0)
-            kde_flag(A.status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
     __syncthreads();
     for (int c = tid; c < cc.n; c += CV_T) {
         double s = 0.0;
@@ -451,7 +466,8 @@ __device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane)
 
 __global__ void __launch_bounds__(CV_T, 2)
     cv_pairs_fast_kernel(const float2 *__restrict__ sc, int64_t N, int NT, const uint2 *__restrict__ tile_u,
-                         int *counter, double *part, unsigned int *status, const __grid_constant__ CvFast cf)
+                         int *counter, double *part, unsigned int *status, unsigned wait_polls,
+                         const __grid_constant__ CvFast cf)
 {
     __shared__ __align__(128) float2 buf[2][CV_T];
     __shared__ __align__(8) uint64_t bar[2];
@@ -500,13 +516,7 @@ __global__ void __launch_bounds__(CV_T, 2)
             const bool next = fetch(b_nxt, d_nxt);
             if (next && tid == 0)
                 tma_load_1d(buf[cur ^ 1], sc + (size_t)b_nxt * CV_T, CV_T * sizeof(float2), &bar[cur ^ 1]);
-            const bool ok = mbar_wait(&bar[cur], phase[cur]);
-            phase[cur] ^= 1u;
-            if (tid == 0) s_stop = ok ? 0 : 1;
-            __syncthreads();
-            if (s_stop) {
-                if (next && !mbar_wait(&bar[cur ^ 1], phase[cur ^ 1]) && tid == 0)
-                    kde_flag(status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
+            if (!tile_wait(bar, phase, cur, next, wait_polls, &s_stop, status)) {
                 failed = true;
                 break;
             }
@@ -708,7 +718,8 @@ __device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c)
 __global__ void __launch_bounds__(CV_T) cv_loo_fast_kernel(const float2 *__restrict__ sc, int64_t N, int NT,
                                                            const uint2 *__restrict__ tile_u,
                                                            const uint32_t *__restrict__ perm, const int *argmin,
-                                                           CvCands cc, double xs, float *loo, unsigned int *status)
+                                                           CvCands cc, double xs, float *loo, unsigned int *status,
+                                                           unsigned wait_polls)
 {
     __shared__ __align__(128) float2 buf[2][CV_T];
     __shared__ __align__(8) uint64_t bar[2];
@@ -745,13 +756,7 @@ __global__ void __launch_bounds__(CV_T) cv_loo_fast_kernel(const float2 *__restr
         const bool next = walk_next(w, a, NT, tile_u, ta, kc, b_nxt, d_nxt);
         if (next && tid == 0)
             tma_load_1d(buf[cur ^ 1], sc + (size_t)b_nxt * CV_T, CV_T * sizeof(float2), &bar[cur ^ 1]);
-        const bool ok = mbar_wait(&bar[cur], phase[cur]);
-        phase[cur] ^= 1u;
-        if (tid == 0) s_stop = ok ? 0 : 1;
-        __syncthreads();
-        if (s_stop) {
-            if (next && !mbar_wait(&bar[cur ^ 1], phase[cur ^ 1]) && tid == 0)
-                kde_flag(status, KDE_DEV_WAIT_TIMEOUT, (unsigned)blockIdx.x);
+        if (!tile_wait(bar, phase, cur, next, wait_polls, &s_stop, status)) {
             failed = true;
             break;
         }
@@ -807,6 +812,7 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
                          const double *cand_host, int n_cand, bool scale_mode, double *cv_dev, int *argmin_dev,
                          float *loo, double *kstar_dev)
 {
+    KdeRange r_cv("kdepic CV (pair sums, integral term, leave-one-out)");
     // candidates: internal ascending order
     CandList cl{};
     CvCands cc{};
@@ -867,6 +873,7 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
     A.lnorm = lnorm;
     A.part = part;
     A.status = ctx->d_status;
+    A.wait_polls = ctx->wait_polls;
     int nparts = nblocks;
     if (!scale_mode && n_cand <= CVF_MAXC) {
         // persistent fast path: enough work items for an even finish
@@ -892,7 +899,8 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
         KDE_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), ctx->stream), "cv counter memset");
         {
             KdeProfScope _ps(ctx, PROF_CV_PAIRS);
-            cv_pairs_fast_kernel<<<ctas, CV_T, 0, ctx->stream>>>(sc, N, NT, tile_u, counter, part, ctx->d_status, cf);
+            cv_pairs_fast_kernel<<<ctas, CV_T, 0, ctx->stream>>>(sc, N, NT, tile_u, counter, part, ctx->d_status,
+                                                                 ctx->wait_polls, cf);
         }
         KDE_LAUNCHED(ctx, "cv_pairs_fast_kernel");
         nparts = cf.nitems;
@@ -908,7 +916,10 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
     KDE_LAUNCHED(ctx, "cv_reduce_kernel");
 
     // integral term on fine grids
-    KDE_TRY(kde_cv_integral_term(ctx, us, N, krs, lnorm, krmax, cl, f2));
+    {
+        KdeRange r_("kdepic CV integral term");
+        KDE_TRY(kde_cv_integral_term(ctx, us, N, krs, lnorm, krmax, cl, f2));
+    }
 
     cv_combine_kernel<<<1, 32, 0, ctx->stream>>>(f2, tot, cc, cl, N, L, cv_dev, argmin_dev, kstar_dev);
     KDE_LAUNCHED(ctx, "cv_combine_kernel");
@@ -947,11 +958,26 @@ kde_status kde_cv_device(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel
             if (scale_mode) cv_loo_kernel<true><<<NT, CV_T, 0, ctx->stream>>>(B);
             else
                 cv_loo_fast_kernel<<<NT, CV_T, 0, ctx->stream>>>(sc, N, NT, tile_u, perm, argmin_dev, cc,
-                                                                 KDE_TWO_PI / L, loo, ctx->d_status);
+                                                                 KDE_TWO_PI / L, loo, ctx->d_status, ctx->wait_polls);
         }
         KDE_LAUNCHED(ctx, "cv_loo_kernel");
     }
     return KDE_OK;
+}
+
+// cost rule between the two exact forms of a uniform-width CV curve: pair sums
+// cost about N^2 frac(kappa_c) / 2 exponentials per candidate (frac = share of
+// the circle inside the truncation radius), the Fourier form about 4 N M(kappa_max)
+// exponential-equivalents for the structure factor shared by all candidates
+bool kde_cv_prefer_spectral(int64_t N, const double *cand, int n_cand)
+{
+    double kmax = 0.0, sfrac = 0.0;
+    for (int c = 0; c < n_cand; ++c) {
+        kmax = cand[c] > kmax ? cand[c] : kmax;
+        const double s2 = KDE_XCUT * KDE_LN2 / (2.0 * cand[c]);
+        sfrac += s2 >= 1.0 ? 1.0 : 2.0 * asin(sqrt(s2)) / KDE_PI;
+    }
+    return 8.0 * (double)kde_spec_modes(kmax) < (double)N * sfrac;
 }
 
 extern "C" kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa_rel, int64_t N, double L,
@@ -960,11 +986,14 @@ extern "C" kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa
 {
     if (!ctx) return KDE_EINVAL;
     const bool scale = (flags & KDE_CV_SCALE) != 0;
-    const bool spectral = (flags & KDE_CV_SPECTRAL) != 0;
-    if (flags & ~(KDE_CV_SCALE | KDE_CV_SPECTRAL))
+    bool spectral = (flags & KDE_CV_SPECTRAL) != 0;
+    const bool pairs = (flags & KDE_CV_PAIRS) != 0;
+    if (flags & ~(KDE_CV_SCALE | KDE_CV_SPECTRAL | KDE_CV_PAIRS))
         return kde_fail(ctx, KDE_ENOTSUP, "kde_cv: unsupported flags 0x%x", flags);
     if (scale && spectral)
         return kde_fail(ctx, KDE_ENOTSUP, "kde_cv: the spectral form is for uniform candidate widths");
+    if (spectral && pairs)
+        return kde_fail(ctx, KDE_EINVAL, "kde_cv: KDE_CV_SPECTRAL and KDE_CV_PAIRS exclude each other");
     if (N < 2 || N > 0xFFFFFFFFll || !(L > 0) || !u || !cand || !cv_out || n_cand < 1 || n_cand > CV_MAXC)
         return kde_fail(ctx, KDE_EINVAL, "kde_cv: need 2 <= N < 2^32, L > 0, 1 <= n_cand <= %d, non-null arrays",
                         CV_MAXC);
@@ -972,6 +1001,7 @@ extern "C" kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa
     for (int c = 0; c < n_cand; ++c)
         if (!(cand[c] > 0 && cand[c] <= KDE_KAPPA_MAX))
             return kde_fail(ctx, KDE_EINVAL, "kde_cv: candidate %d = %g outside (0, 1e6]", c, cand[c]);
+    if (!scale && !pairs && !spectral) spectral = kde_cv_prefer_spectral(N, cand, n_cand);
     cudaSetDevice(ctx->device);
     double *cvd = (double *)kde_ws(ctx, WS_CV_OUT, (size_t)n_cand * 8 + 64);
     if (!cvd) return KDE_ENOMEM;
@@ -992,22 +1022,6 @@ extern "C" kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa
 // Silverman particle-wise widths (Sec. II.C)
 // ---------------------------------------------------------------------------
 #define AD_BLOCKS 256
-__global__ void adapt_logsum_kernel(const float *loo, int64_t N, double K0, double *part)
-{
-    __shared__ double red[256];
-    const double n = (double)N;
-    double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)AD_BLOCKS * 256)
-        s += log(((n - 1.0) * (double)loo[i] + K0) / n);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
-}
-
 template <typename T>
 __global__ void adapt_apply_kernel(const float *loo, int64_t N, double xs, const double *kstar_dev, double kstar_h,
                                    const double *part, double alpha, double kmin, double kmax, T *kappa_out,
@@ -1079,7 +1093,7 @@ kde_status kde_adapt_device(kde_ctx *ctx, const float *loo, int64_t N, double L,
     const double xs = KDE_TWO_PI / L;
     if (f64) adapt_logsum_dev_kernel<false><<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part);
     else adapt_logsum_dev_kernel<true><<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part);
-    KDE_LAUNCHED(ctx, "adapt_logsum_kernel");
+    KDE_LAUNCHED(ctx, "adapt_logsum_dev_kernel");
     unsigned grid = (unsigned)((N + 255) / 256);
     if (f64)
         adapt_apply_kernel<double><<<grid, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part, alpha, kmin,

@@ -13,8 +13,6 @@
 // point (an exact power-of-two scale below the largest possible node value)
 // and added with integer atomics, so the grid sum is exact and independent of
 // the order in which chunks finish: results are bitwise reproducible.
-#include <mutex>
-
 #include "common.cuh"
 
 #define DEP_THREADS 256
@@ -837,45 +835,48 @@ __global__ void noalloc_node_kernel(T2 *tab, int Ng)
     tab[g].y = c;
 }
 
-// device address of the scratch array, looked up once per device with that
-// device current (the host-side symbol is only a stand-in)
-static std::mutex g_noalloc_mu;
-static std::map<int, unsigned char *> g_noalloc_addr;
-
-static unsigned char *noalloc_scratch_address(int device)
+// device address of the scratch array on the current device.  Looked up on every
+// call (a host-side table lookup once the module is loaded): a cached address
+// would go stale if the device's context were reset and the module reloaded.
+static unsigned char *noalloc_scratch_address()
 {
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    auto it = g_noalloc_addr.find(device);
-    if (it != g_noalloc_addr.end()) return it->second;
     void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, kde_noalloc_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    g_noalloc_addr[device] = (unsigned char *)p;
+    if (cudaGetSymbolAddress(&p, kde_noalloc_scratch) != cudaSuccess || !p) return nullptr;
     return (unsigned char *)p;
 }
 
+// every launch goes through cudaLaunchKernel, whose return value is that launch's
+// own status (a trailing cudaGetLastError would also report, and clear, errors of
+// unrelated earlier launches on this thread)
 template <typename T>
 static kde_status deposit_noalloc_impl(cudaStream_t stream, unsigned char *scr, const uint32_t *u, const T *kappa,
                                        double kappa_u, const T *weight, int64_t N, int Ng, double L, T *rho_out)
 {
+    typedef typename V2<T>::t T2;
     long long *acc = (long long *)(scr + NOALLOC_ACC_OFF);
-    typename V2<T>::t *nodes = (typename V2<T>::t *)(scr + NOALLOC_NODE_OFF);
+    T2 *nodes = (T2 *)(scr + NOALLOC_NODE_OFF);
     unsigned int *wmax = (unsigned int *)(scr + NOALLOC_WMAX_OFF);
     if (cudaMemsetAsync(acc, 0, (size_t)Ng * sizeof(long long), stream) != cudaSuccess) return KDE_ECUDA;
     if (N == 0) return cudaMemsetAsync(rho_out, 0, (size_t)Ng * sizeof(T), stream) == cudaSuccess ? KDE_OK : KDE_ECUDA;
-    noalloc_node_kernel<typename V2<T>::t><<<(Ng + 255) / 256, 256, 0, stream>>>(nodes, Ng);
+    {
+        void *args[] = {&nodes, &Ng};
+        if (cudaLaunchKernel((const void *)noalloc_node_kernel<T2>, dim3((Ng + 255) / 256), dim3(256), args, 0,
+                             stream) != cudaSuccess)
+            return KDE_ECUDA;
+    }
     const double coef = KDE_TWO_PI / L;
     const double norm_u = kappa ? 0.0 : kde_norm(kappa_u);
     const double norm_bound = kappa ? kde_norm(KDE_KAPPA_MAX) : norm_u;
     const double w_u = L / (double)N;
-    const double bound = (double)N * w_u * coef * norm_bound;
+    double bound = (double)N * w_u * coef * norm_bound;
     if (weight) {
         if (cudaMemsetAsync(wmax, 0, 4, stream) != cudaSuccess) return KDE_ECUDA;
         int blocks = (int)((N + 255) / 256);
         blocks = blocks > 1024 ? 1024 : blocks;
-        wmax_kernel<T><<<blocks, 256, 0, stream>>>(weight, N, wmax, nullptr);
+        unsigned int *no_status = nullptr;
+        void *args[] = {(void *)&weight, &N, &wmax, &no_status};
+        if (cudaLaunchKernel((const void *)wmax_kernel<T>, dim3(blocks), dim3(256), args, 0, stream) != cudaSuccess)
+            return KDE_ECUDA;
     }
     DepSrc<T> S{};
     S.u = u;
@@ -894,10 +895,22 @@ static kde_status deposit_noalloc_impl(cudaStream_t stream, unsigned char *scr, 
     S.wmax_bits = weight ? wmax : nullptr;
     S.norm_bound = norm_bound;
     S.status = nullptr;
-    deposit_chunk_unsorted_kernel<T><<<(unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK), DEP_THREADS, 0, stream>>>(S);
-    acc_to_real_kernel<T><<<(Ng + 255) / 256, 256, 0, stream>>>(acc, Ng, bound, weight ? wmax : nullptr,
-                                                                (double)N * coef * norm_bound, rho_out);
-    return cudaGetLastError() == cudaSuccess ? KDE_OK : KDE_ECUDA;
+    {
+        void *args[] = {&S};
+        if (cudaLaunchKernel((const void *)deposit_chunk_unsorted_kernel<T>,
+                             dim3((unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK)), dim3(DEP_THREADS), args, 0,
+                             stream) != cudaSuccess)
+            return KDE_ECUDA;
+    }
+    {
+        const unsigned int *wb = weight ? wmax : nullptr;
+        double wscale = (double)N * coef * norm_bound;
+        void *args[] = {&acc, &Ng, &bound, (void *)&wb, &wscale, &rho_out};
+        if (cudaLaunchKernel((const void *)acc_to_real_kernel<T>, dim3((Ng + 255) / 256), dim3(256), args, 0,
+                             stream) != cudaSuccess)
+            return KDE_ECUDA;
+    }
+    return KDE_OK;
 }
 
 extern "C" kde_status kde_deposit_noalloc(void *stream, const uint32_t *u, const void *kappa, double kappa_uniform,
@@ -908,9 +921,7 @@ extern "C" kde_status kde_deposit_noalloc(void *stream, const uint32_t *u, const
         return KDE_EINVAL;
     if (!kappa && !(kappa_uniform > 0 && kappa_uniform <= KDE_KAPPA_MAX)) return KDE_EINVAL;
     if (flags & ~KDE_F64) return KDE_ENOTSUP;
-    int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess) return KDE_ECUDA;
-    unsigned char *scr = noalloc_scratch_address(device);
+    unsigned char *scr = noalloc_scratch_address();
     if (!scr) return KDE_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
     if (flags & KDE_F64)

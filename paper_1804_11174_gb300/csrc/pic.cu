@@ -64,6 +64,10 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
     const bool sched = !adsched && st->width_every > 0 && st->n_cand > 0;
     const bool fd = (st->flags & KDE_POISSON_FD) != 0;
     T *norm_arr = (T *)st->kappa_norm;
+    // CV form of the schedule: forced by a flag, else the cheaper exact form (cost rule)
+    const bool cv_spec = (st->flags & KDE_CV_SPECTRAL) ||
+                         (!(st->flags & KDE_CV_PAIRS) && st->n_cand > 0 && st->cand &&
+                          kde_cv_prefer_spectral(N, st->cand, st->n_cand));
 
     // the width update (CV) shares the sort slots; size them for it up front and
     // fetch the pointers again after every update, since a slot may be regrown
@@ -102,7 +106,8 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
         const int64_t step = st->step;
         const bool update = sched && step % st->width_every == 0;
         if (update) {
-            if (st->flags & KDE_CV_SPECTRAL)
+            KdeRange r_("kdepic width update (CV + Silverman)");
+            if (cv_spec)
                 KDE_TRY(kde_cv_spectral_device(ctx, st->u, N, L, st->cand, st->n_cand, cv_dev, amin_dev, loo, ks_dev));
             else
                 KDE_TRY(kde_cv_device(ctx, st->u, nullptr, N, L, st->cand, st->n_cand, false, cv_dev, amin_dev, loo,
@@ -112,6 +117,7 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
             if (!fetch_ws()) return KDE_ENOMEM;
         }
         if (adsched) {
+            KdeRange r_("kdepic Anderson-Darling schedule");
             KDE_TRY(kde_ad_device(ctx, st->u, N, ad_out, st->ad_log_p ? st->ad_log_p + step : nullptr));
             double ad_h[2];
             KDE_CUDA(ctx, cudaMemcpyAsync(ad_h, ad_out, 16, cudaMemcpyDeviceToHost, ctx->stream), "AD result copy");
@@ -126,7 +132,7 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
                 opt = true;
             }
             if (opt) {
-                if (st->flags & KDE_CV_SPECTRAL)
+                if (cv_spec)
                     KDE_TRY(kde_cv_spectral_device(ctx, st->u, N, L, st->cand, st->n_cand, cv_dev, amin_dev, nullptr,
                                                    nullptr));
                 else
@@ -152,15 +158,24 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
             pl[npl++] = SortPayload{norm_arr, ns, (int)sizeof(T)};
         }
         if (st->id) pl[npl++] = SortPayload{st->id, ids, 4};
-        KDE_TRY(kde_sort_by_bin(ctx, st->u, N, Ng, us, pl, npl, nullptr));
+        {
+            KdeRange r_("kdepic sort by cell");
+            KDE_TRY(kde_sort_by_bin(ctx, st->u, N, Ng, us, pl, npl, nullptr));
+        }
 
         const double norm_u = per ? 0.0 : kde_norm(st->kappa_uniform);
         const double norm_bound = per ? kde_norm(KDE_KAPPA_MAX) : norm_u;
         const double bound = (double)N * w_u * coef * norm_bound;
-        KDE_TRY(kde_deposit_sorted<T>(ctx, us, ks, (T)st->kappa_uniform, ns, (T)norm_u, nullptr, (T)w_u, N, Ng, coef,
-                                      acc, bound, nullptr, norm_bound));
-        KDE_TRY(kde_poisson_impl<T>(ctx, nullptr, acc, 1.0 / kde_acc_scale(bound), Ng, L, st->charge,
-                                    st->background, fd, E));
+        {
+            KdeRange r_("kdepic deposit");
+            KDE_TRY(kde_deposit_sorted<T>(ctx, us, ks, (T)st->kappa_uniform, ns, (T)norm_u, nullptr, (T)w_u, N, Ng,
+                                          coef, acc, bound, nullptr, norm_bound));
+        }
+        {
+            KdeRange r_("kdepic Poisson");
+            KDE_TRY(kde_poisson_impl<T>(ctx, nullptr, acc, 1.0 / kde_acc_scale(bound), Ng, L, st->charge,
+                                        st->background, fd, E));
+        }
 
         PushArgs pa{};
         pa.v_in = vs;
@@ -178,8 +193,11 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
         pa.kstar_in = update || sched ? ks_dev : nullptr;
         pa.kstar_out = st->kappa_star ? st->kappa_star + step : nullptr;
         pa.dx = L / Ng;
-        KDE_TRY(kde_gather_sorted<T>(ctx, us, ks, (T)st->kappa_uniform, ns, (T)norm_u, N, E, Ng, KDE_TWO_PI / Ng,
-                                     nullptr, nullptr, &pa));
+        {
+            KdeRange r_("kdepic gather + push");
+            KDE_TRY(kde_gather_sorted<T>(ctx, us, ks, (T)st->kappa_uniform, ns, (T)norm_u, N, E, Ng,
+                                         KDE_TWO_PI / Ng, nullptr, nullptr, &pa));
+        }
         st->step = step + 1;
     }
     return KDE_OK;
@@ -193,8 +211,10 @@ extern "C" kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps)
         !st->u || !st->v || st->step < 0)
         return kde_fail(ctx, KDE_EINVAL, "pic_step: need 1 <= N < 2^32, 1 <= Ng <= %d, L > 0, dt > 0, u and v",
                         KDE_MAX_NG);
-    if (st->flags & ~(KDE_F64 | KDE_POISSON_FD | KDE_CV_SPECTRAL | PIC_NO_BACKSTEP))
+    if (st->flags & ~(KDE_F64 | KDE_POISSON_FD | KDE_CV_SPECTRAL | KDE_CV_PAIRS | PIC_NO_BACKSTEP))
         return kde_fail(ctx, KDE_ENOTSUP, "pic_step: unsupported flags 0x%x", st->flags);
+    if ((st->flags & KDE_CV_SPECTRAL) && (st->flags & KDE_CV_PAIRS))
+        return kde_fail(ctx, KDE_EINVAL, "pic_step: KDE_CV_SPECTRAL and KDE_CV_PAIRS exclude each other");
     if (st->width_ad) {
         if (st->kappa || !st->cand || st->n_cand < 1 || st->n_cand > 256 || st->N < KDE_AD_MIN_N ||
             !(st->ad_threshold > 0 && st->ad_threshold < 0.5) || !(st->adjust_rate > 0 && st->adjust_rate <= 1))
@@ -234,4 +254,61 @@ extern "C" kde_status pic_step(kde_ctx *ctx, pic_state *st, int32_t n_steps)
     cudaSetDevice(ctx->device);
     if (st->flags & KDE_F64) return pic_run<double>(ctx, st, n_steps);
     return pic_run<float>(ctx, st, n_steps);
+}
+
+// ---------------------------------------------------------------------------
+// pic_step on a host-resident state: copy in, run on the device, copy out
+// ---------------------------------------------------------------------------
+extern "C" kde_status pic_step_host(kde_ctx *ctx, pic_state *st, int32_t n_steps)
+{
+    if (!ctx) return KDE_EINVAL;
+    if (!st || n_steps < 0 || st->N < 1 || st->N > 0xFFFFFFFFll || !st->u || !st->v || st->step < 0)
+        return kde_fail(ctx, KDE_EINVAL, "pic_step_host: need a state with 1 <= N < 2^32, u, v and step >= 0");
+    cudaSetDevice(ctx->device);
+    const size_t N = (size_t)st->N;
+    const size_t el = (st->flags & KDE_F64) ? 8 : 4;
+    const size_t hist = (size_t)st->step + (size_t)n_steps;  // histories are indexed by step
+    pic_state d = *st;
+    d.u = (uint32_t *)kde_ws(ctx, WS_HOST_U, N * 4);
+    d.v = kde_ws(ctx, WS_HOST_V, N * el);
+    d.kappa = st->kappa ? kde_ws(ctx, WS_HOST_K, N * el) : nullptr;
+    d.kappa_norm = st->kappa ? kde_ws(ctx, WS_HOST_NORM, N * el) : nullptr;
+    d.id = st->id ? (uint32_t *)kde_ws(ctx, WS_HOST_ID, N * 4) : nullptr;
+    const int nh = (st->energy ? 1 : 0) + (st->kappa_star ? 1 : 0) + (st->ad_log_p ? 1 : 0);
+    double *h = nh ? (double *)kde_ws(ctx, WS_HOST_HIST, (size_t)nh * (hist > 0 ? hist : 1) * 8) : nullptr;
+    if (!d.u || !d.v || (st->kappa && (!d.kappa || !d.kappa_norm)) || (st->id && !d.id) || (nh && !h))
+        return KDE_ENOMEM;
+    int k = 0;
+    d.energy = st->energy ? h + (k++) * hist : nullptr;
+    d.kappa_star = st->kappa_star ? h + (k++) * hist : nullptr;
+    d.ad_log_p = st->ad_log_p ? h + (k++) * hist : nullptr;
+    cudaStream_t s = ctx->stream;
+    KDE_CUDA(ctx, cudaMemcpyAsync(d.u, st->u, N * 4, cudaMemcpyHostToDevice, s), "state copy in");
+    KDE_CUDA(ctx, cudaMemcpyAsync(d.v, st->v, N * el, cudaMemcpyHostToDevice, s), "state copy in");
+    if (st->kappa) KDE_CUDA(ctx, cudaMemcpyAsync(d.kappa, st->kappa, N * el, cudaMemcpyHostToDevice, s), "state copy in");
+    if (st->id) KDE_CUDA(ctx, cudaMemcpyAsync(d.id, st->id, N * 4, cudaMemcpyHostToDevice, s), "state copy in");
+    KDE_TRY(pic_step(ctx, &d, n_steps));
+    KDE_CUDA(ctx, cudaMemcpyAsync(st->u, d.u, N * 4, cudaMemcpyDeviceToHost, s), "state copy out");
+    KDE_CUDA(ctx, cudaMemcpyAsync(st->v, d.v, N * el, cudaMemcpyDeviceToHost, s), "state copy out");
+    if (st->kappa) KDE_CUDA(ctx, cudaMemcpyAsync(st->kappa, d.kappa, N * el, cudaMemcpyDeviceToHost, s), "state copy out");
+    if (st->id) KDE_CUDA(ctx, cudaMemcpyAsync(st->id, d.id, N * 4, cudaMemcpyDeviceToHost, s), "state copy out");
+    const size_t off = (size_t)st->step, cnt = (size_t)n_steps * 8;
+    if (n_steps > 0) {
+        if (st->energy)
+            KDE_CUDA(ctx, cudaMemcpyAsync(st->energy + off, d.energy + off, cnt, cudaMemcpyDeviceToHost, s), "copy out");
+        if (st->kappa_star)
+            KDE_CUDA(ctx, cudaMemcpyAsync(st->kappa_star + off, d.kappa_star + off, cnt, cudaMemcpyDeviceToHost, s),
+                     "copy out");
+        if (st->ad_log_p)
+            KDE_CUDA(ctx, cudaMemcpyAsync(st->ad_log_p + off, d.ad_log_p + off, cnt, cudaMemcpyDeviceToHost, s),
+                     "copy out");
+    }
+    const kde_status rc = kde_sync(ctx);
+    // the scalar state the run advanced
+    st->step = d.step;
+    st->kappa_uniform = d.kappa_uniform;
+    st->ad_log_pth = d.ad_log_pth;
+    st->h_target = d.h_target;
+    st->n_opt = d.n_opt;
+    return rc;
 }

@@ -13,6 +13,16 @@
 // Because every kernel is deterministic and a request only touches its own
 // buffers and its slot's workspace, a result does not depend on which other
 // requests ran beside it.
+//
+// HBM accounting.  Device memory committed at any time is the transient
+// buffers of the running requests plus the workspace every slot's context
+// holds (a context keeps its workspace between requests).  A request's
+// footprint is split into its transient buffers and the workspace it needs; a
+// slot admits the head request when the committed total plus the buffers plus
+// the slot's workspace growth fits the budget.  When only the workspace held by
+// idle slots stands in the way, those slots' workspaces are released first.
+// After each request the slot's actual workspace is measured again, so growth
+// beyond the estimate is charged to later admissions.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -31,7 +41,10 @@ struct Ticket {
     clk::time_point t_submit, t_start, t_end;
     kde_status status = KDE_OK;
     bool done = false;
-    int64_t footprint = 0;
+    bool cancelled = false;
+    int64_t io = 0;  // transient device buffers
+    int64_t ws = 0;  // workspace the request needs in its slot's context
+    double dev_start = -1.0, dev_end = -1.0;  // device clock, ms since the server's epoch event
     std::string err;
 };
 
@@ -39,33 +52,79 @@ struct Ticket {
 
 struct kde_server {
     int device = 0;
-    int64_t budget = 0, in_use = 0;
+    int64_t budget = 0;
+    int64_t io_in_use = 0;         // transient buffers of the running requests
+    int64_t committed_peak = 0;    // largest committed total seen at an admission
+    std::vector<int64_t> held;     // workspace each slot's context holds (or has reserved)
+    std::vector<char> busy;
     std::vector<std::thread> workers;
     std::vector<kde_ctx *> ctxs;
     std::vector<cudaStream_t> streams;
+    cudaEvent_t epoch = nullptr;   // device-clock origin of the request intervals
     std::mutex mu;
     std::condition_variable cv_queue, cv_done;
     std::deque<int64_t> queue;
     std::unordered_map<int64_t, Ticket> tickets;
     int64_t next_id = 1;
     bool stop = false;
-    int64_t served = 0;
+    int64_t served = 0, cancelled = 0, trims = 0;
 };
 
-static int64_t request_footprint(const kde_request &r)
+// transient device buffers of a request (inputs and outputs), in bytes
+static int64_t request_io_bytes(const kde_request &r)
 {
-    // inputs, outputs and the slot workspace a request of this size grows (sort
-    // copies, CV tables), in bytes
     const int64_t N = r.N, Ng = r.Ng;
-    int64_t b = N * 16 + Ng * 16 + (1 << 20);
-    if (r.kind == KDE_REQ_CV) b += N * (8 + 12 + 4 * (int64_t)r.n_cand) + (1 << 22);
-    else b += N * 40 + (16 << 20);
+    int64_t b = N * 4 + (r.kappa ? N * 4 : 0) + 4096;
+    switch (r.kind) {
+    case KDE_REQ_DEPOSIT: b += Ng * 4; break;
+    case KDE_REQ_GATHER: b += Ng * 4 + N * 4; break;
+    case KDE_REQ_PIC: b += N * 4 + (r.kappa ? N * 4 : 0) + (int64_t)(r.n_steps > 0 ? r.n_steps : 1) * 8; break;
+    default: break;
+    }
     return b;
 }
 
-static kde_status run_request(kde_server *S, kde_ctx *ctx, cudaStream_t st, const kde_request &r)
+// workspace a request of this size grows in its slot's context (sort copies, CV
+// tables, grid scratch), in bytes: an upper estimate of what the kernels request
+static int64_t request_ws_bytes(const kde_request &r)
+{
+    const int64_t N = r.N, Ng = r.Ng;
+    // (workspace slots grow by a quarter beyond the request, hence the margins)
+    if (r.kind == KDE_REQ_CV)
+        return N * (32 + 5 * (int64_t)r.n_cand) + (int64_t)r.n_cand * 8192 * 10 + (4 << 20);
+    return N * 48 + Ng * 64 + (16 << 20);
+}
+
+// device memory a context holds: its workspace slots and cached tables
+static int64_t ctx_held_bytes(const kde_ctx *c)
+{
+    int64_t b = 0;
+    for (int i = 0; i < WS_NSLOTS; ++i) b += (int64_t)c->ws_bytes[i];
+    for (auto &kv : c->node_tab) b += (int64_t)kv.first.first * (kv.first.second ? 16 : 8);
+    for (auto &kv : c->green_tab) b += (int64_t)std::get<0>(kv.first) * (std::get<3>(kv.first) ? 8 : 4);
+    return b;
+}
+
+// release the workspace of a context whose slot is idle (its stream has drained)
+static void ctx_trim(kde_ctx *c)
+{
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < WS_NSLOTS; ++i)
+        if (c->ws[i]) {
+            cudaFree(c->ws[i]);
+            c->ws[i] = nullptr;
+            c->ws_bytes[i] = 0;
+        }
+    c->sp_atab = nullptr;  // held in a workspace slot
+    c->sp_atab_cands.clear();
+}
+
+static kde_status run_request(kde_server *S, kde_ctx *ctx, cudaStream_t st, const kde_request &r, cudaEvent_t ev0,
+                              cudaEvent_t ev1)
 {
     const int64_t N = r.N;
+    cudaEventRecord(ev0, st);
     void *bufs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     auto dalloc = [&](int slot, size_t bytes) -> void * {
         if (cudaMallocAsync(&bufs[slot], bytes ? bytes : 16, st) != cudaSuccess) {
@@ -149,10 +208,49 @@ static kde_status run_request(kde_server *S, kde_ctx *ctx, cudaStream_t st, cons
     }
     for (int k = 0; k < 6; ++k)
         if (bufs[k]) cudaFreeAsync(bufs[k], st);
+    cudaEventRecord(ev1, st);
     kde_status s2 = kde_sync(ctx);
     if (rc == KDE_OK) rc = s2;
     (void)S;
     return rc;
+}
+
+// admission of the queue's head on idle slot `slot` (called with the lock held)
+static bool admit_head(kde_server *S, int slot)
+{
+    if (S->queue.empty()) return false;
+    Ticket &t = S->tickets[S->queue.front()];
+    auto committed = [&]() {
+        int64_t c = S->io_in_use;
+        for (int64_t h : S->held) c += h;
+        return c;
+    };
+    const int64_t grow = t.ws > S->held[slot] ? t.ws - S->held[slot] : 0;
+    bool anyone_busy = false;
+    for (char b : S->busy) anyone_busy = anyone_busy || b;
+    if (committed() + t.io + grow > S->budget) {
+        // release the workspace of the other idle slots, then look again
+        for (size_t k = 0; k < S->held.size(); ++k)
+            if ((int)k != slot && !S->busy[k] && S->held[k] > 0) {
+                ctx_trim(S->ctxs[k]);
+                S->held[k] = ctx_held_bytes(S->ctxs[k]);
+                ++S->trims;
+            }
+        if (committed() + t.io + grow > S->budget) {
+            if (anyone_busy) return false;
+            // nothing else runs: start from this slot's own empty workspace too (the
+            // request fits the budget by itself: kde_server_submit refuses larger ones)
+            ctx_trim(S->ctxs[slot]);
+            S->held[slot] = ctx_held_bytes(S->ctxs[slot]);
+            ++S->trims;
+        }
+    }
+    const int64_t grow2 = t.ws > S->held[slot] ? t.ws - S->held[slot] : 0;
+    S->io_in_use += t.io;
+    S->held[slot] += grow2;
+    const int64_t c = committed();
+    if (c > S->committed_peak) S->committed_peak = c;
+    return true;
 }
 
 static void worker_main(kde_server *S, int slot)
@@ -160,42 +258,55 @@ static void worker_main(kde_server *S, int slot)
     cudaSetDevice(S->device);
     kde_ctx *ctx = S->ctxs[slot];
     cudaStream_t st = S->streams[slot];
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
     for (;;) {
         int64_t id;
+        kde_request req;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             // FIFO admission: the head request starts when its footprint fits the budget
+            // (admit_head commits the accounting when it returns true); a stopping server
+            // still finishes its queue
+            bool admitted = false;
             S->cv_queue.wait(lk, [&] {
-                return S->stop ||
-                       (!S->queue.empty() &&
-                        (S->in_use == 0 || S->in_use + S->tickets[S->queue.front()].footprint <= S->budget));
+                admitted = admit_head(S, slot);
+                return admitted || (S->stop && S->queue.empty());
             });
-            if (S->stop && S->queue.empty()) return;
+            if (!admitted) break;
             id = S->queue.front();
             S->queue.pop_front();
             Ticket &t = S->tickets[id];
-            S->in_use += t.footprint;
+            S->busy[slot] = 1;
             t.t_start = clk::now();
+            req = t.req;
         }
-        kde_request req;
-        {
-            std::lock_guard<std::mutex> lk(S->mu);
-            req = S->tickets[id].req;
+        kde_status rc = run_request(S, ctx, st, req, ev0, ev1);
+        float a = -1.f, b = -1.f;
+        if (cudaEventElapsedTime(&a, S->epoch, ev0) != cudaSuccess || cudaEventElapsedTime(&b, S->epoch, ev1) != cudaSuccess) {
+            cudaGetLastError();
+            a = b = -1.f;
         }
-        kde_status rc = run_request(S, ctx, st, req);
         {
             std::lock_guard<std::mutex> lk(S->mu);
             Ticket &t = S->tickets[id];
             t.status = rc;
             if (rc != KDE_OK) t.err = kde_last_error(ctx);
             t.t_end = clk::now();
+            t.dev_start = a;
+            t.dev_end = b;
             t.done = true;
-            S->in_use -= t.footprint;
+            S->io_in_use -= t.io;
+            S->held[slot] = ctx_held_bytes(ctx);
+            S->busy[slot] = 0;
             ++S->served;
         }
         S->cv_done.notify_all();
         S->cv_queue.notify_all();
     }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
 }
 
 extern "C" kde_status kde_server_create(kde_server **out, int device, int32_t n_slots, int64_t hbm_budget_bytes)
@@ -206,6 +317,10 @@ extern "C" kde_status kde_server_create(kde_server **out, int device, int32_t n_
     kde_server *S = new kde_server();
     S->device = device;
     S->budget = hbm_budget_bytes;
+    if (cudaEventCreate(&S->epoch) != cudaSuccess) {
+        delete S;
+        return KDE_ECUDA;
+    }
     for (int k = 0; k < n_slots; ++k) {
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -220,7 +335,11 @@ extern "C" kde_status kde_server_create(kde_server **out, int device, int32_t n_
         }
         S->streams.push_back(st);
         S->ctxs.push_back(c);
+        S->held.push_back(ctx_held_bytes(c));
+        S->busy.push_back(0);
     }
+    cudaEventRecord(S->epoch, S->streams[0]);
+    cudaEventSynchronize(S->epoch);
     for (int k = 0; k < n_slots; ++k) S->workers.emplace_back(worker_main, S, k);
     *out = S;
     return KDE_OK;
@@ -239,14 +358,15 @@ extern "C" kde_status kde_server_submit(kde_server *S, const kde_request *req, i
     default: ok = false;
     }
     if (!ok) return KDE_EINVAL;
-    const int64_t fp = request_footprint(r);
-    if (fp > S->budget) return KDE_EINVAL;  // could never be admitted
+    const int64_t io = request_io_bytes(r), ws = request_ws_bytes(r);
+    if (io + ws + (1 << 20) > S->budget) return KDE_EINVAL;  // could never be admitted (1 MiB for tables)
     {
         std::lock_guard<std::mutex> lk(S->mu);
         int64_t id = S->next_id++;
         Ticket &t = S->tickets[id];
         t.req = r;
-        t.footprint = fp;
+        t.io = io;
+        t.ws = ws;
         t.t_submit = clk::now();
         S->queue.push_back(id);
         *ticket = id;
@@ -255,7 +375,7 @@ extern "C" kde_status kde_server_submit(kde_server *S, const kde_request *req, i
     return KDE_OK;
 }
 
-extern "C" kde_status kde_server_wait(kde_server *S, int64_t ticket, double *latency_ms, double *service_ms)
+extern "C" kde_status kde_server_wait_times(kde_server *S, int64_t ticket, double *times)
 {
     if (!S) return KDE_EINVAL;
     std::unique_lock<std::mutex> lk(S->mu);
@@ -264,11 +384,63 @@ extern "C" kde_status kde_server_wait(kde_server *S, int64_t ticket, double *lat
     // element references stay valid while other tickets are inserted (iterators may not)
     Ticket &t = it->second;
     S->cv_done.wait(lk, [&] { return t.done; });
-    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(t.t_end - t.t_submit).count();
-    if (service_ms) *service_ms = std::chrono::duration<double, std::milli>(t.t_end - t.t_start).count();
+    if (times) {
+        times[0] = std::chrono::duration<double, std::milli>(t.t_end - t.t_submit).count();
+        times[1] = t.cancelled ? 0.0 : std::chrono::duration<double, std::milli>(t.t_end - t.t_start).count();
+        times[2] = t.dev_start;
+        times[3] = t.dev_end;
+    }
     kde_status rc = t.status;
     S->tickets.erase(ticket);
     return rc;
+}
+
+extern "C" kde_status kde_server_wait(kde_server *S, int64_t ticket, double *latency_ms, double *service_ms)
+{
+    double t[4] = {0, 0, -1, -1};
+    kde_status rc = kde_server_wait_times(S, ticket, t);
+    if (latency_ms) *latency_ms = t[0];
+    if (service_ms) *service_ms = t[1];
+    return rc;
+}
+
+extern "C" kde_status kde_server_cancel(kde_server *S, int64_t ticket)
+{
+    if (!S) return KDE_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->tickets.find(ticket);
+        if (it == S->tickets.end()) return KDE_EINVAL;
+        auto q = std::find(S->queue.begin(), S->queue.end(), ticket);
+        if (q == S->queue.end()) return KDE_EBUSY;  // admitted already (running or done)
+        S->queue.erase(q);
+        Ticket &t = it->second;
+        t.cancelled = true;
+        t.status = KDE_ECANCELED;
+        t.t_start = t.t_end = clk::now();
+        t.done = true;
+        ++S->cancelled;
+    }
+    S->cv_done.notify_all();
+    S->cv_queue.notify_all();  // the next request may now be the head
+    return KDE_OK;
+}
+
+extern "C" kde_status kde_server_stats(kde_server *S, int64_t *stats)
+{
+    if (!S || !stats) return KDE_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    int64_t held = 0;
+    for (int64_t h : S->held) held += h;
+    stats[0] = S->io_in_use + held;
+    stats[1] = S->committed_peak;
+    stats[2] = S->budget;
+    stats[3] = S->served;
+    stats[4] = S->cancelled;
+    stats[5] = (int64_t)S->queue.size();
+    stats[6] = S->trims;
+    stats[7] = held;
+    return KDE_OK;
 }
 
 extern "C" kde_status kde_server_destroy(kde_server *S)
@@ -282,6 +454,7 @@ extern "C" kde_status kde_server_destroy(kde_server *S)
     for (auto &w : S->workers) w.join();
     for (auto *c : S->ctxs) kde_destroy(c);
     for (auto st : S->streams) cudaStreamDestroy(st);
+    if (S->epoch) cudaEventDestroy(S->epoch);
     delete S;
     return KDE_OK;
 }

@@ -7,8 +7,10 @@ takes a stream instead of a context and keeps its scratch in a fixed device
 array inside the library.  Its output must match kde_deposit's within the
 deposit tolerance of the other tests (1e-5 relative L2 in FP32, 1e-10 in
 FP64), on two calls in a row (the shared scratch keeps the previous call's
-contents), for sorted and unsorted particles.  This file is collected last so
-that a stop-at-first-failure run has already run every other test.
+contents), for sorted and unsorted particles; and it must match the FP64 oracle
+within the same tolerances while the device's free memory stays the same across
+calls.  This file is collected last so that a stop-at-first-failure run has
+already run every other test.
 """
 import ctypes
 import math
@@ -71,3 +73,47 @@ def test_noalloc_rejects_oversized_grid_and_bad_arguments(kp):
     assert call(lib, u[:0], 64, 1.0, out, kappa_u=5.0) == 0  # empty input gives zeros
     torch.cuda.synchronize()
     assert torch.all(out[:64] == 0)
+
+
+def test_noalloc_matches_oracle_and_allocates_nothing(kp, oracle):
+    # every buffer exists before the first call; after it (which may load the
+    # module), repeated calls leave the device's free memory exactly where it was
+    lib = kp.load_library()
+    L = 4 * math.pi
+    cases = [
+        dict(N=30_011, Ng=256, kappa_u=120.0, f64=False),
+        dict(N=6_000, Ng=333, per_particle=True, weights=True, f64=False),
+        dict(N=3_000, Ng=64, kappa_u=25.0, f64=True),
+    ]
+    prepared = []
+    for cs in cases:
+        N, Ng, f64 = cs["N"], cs["Ng"], cs["f64"]
+        u, _ = I.landau_load(N + 1, N, L, 0.05, 1.0)
+        u = u[np.argsort(I.uniforms(N, 10, N))]
+        dt = torch.float64 if f64 else torch.float32
+        kap = I.log_uniform(N, I.STREAM_KAPPA, N, 5.0, 5e3) if cs.get("per_particle") else None
+        w = 0.5 + I.uniforms(N, 8, N) if cs.get("weights") else None
+        kap_d = None if kap is None else to_dev(kap, dt)
+        w_d = None if w is None else to_dev(w, dt)
+        # the oracle gets exactly the values the device holds
+        kap_o = None if kap is None else kap_d.double().cpu().numpy()
+        w_o = None if w is None else w_d.double().cpu().numpy()
+        ref = oracle.deposit(I.from_fixed(u, L), Ng, L, kappa=kap_o, kappa_u=cs.get("kappa_u", 0.0), w=w_o)
+        outs = [torch.full((Ng,), float("nan"), dtype=dt, device="cuda:0") for _ in range(3)]
+        prepared.append((cs, to_dev_u(u), kap_d, w_d, ref, outs, 1e-10 if f64 else 1e-5))
+    torch.cuda.synchronize()
+    free0 = None
+    for k in range(3):
+        for cs, ud, kap_d, w_d, ref, outs, tol in prepared:
+            rc = call(lib, ud, cs["Ng"], L, outs[k], kappa=kap_d, kappa_u=cs.get("kappa_u", 0.0), weight=w_d,
+                      f64=cs["f64"])
+            assert rc == 0
+        torch.cuda.synchronize()
+        free = torch.cuda.mem_get_info()[0]
+        if k == 0:
+            free0 = free
+        else:
+            assert free == free0, (free0, free)
+    for cs, ud, kap_d, w_d, ref, outs, tol in prepared:
+        for out in outs:
+            assert rel_l2(out.cpu().numpy(), ref) <= tol, cs
