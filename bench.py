@@ -1,19 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the KDE-PIC hot path on one GB300 (or N independent replicas).
 
-Workload (default, `--workload landau`): the Landau-damping run with particle-
-wise widths -- N = 2^20 electrons, Ng = 256 nodes, L = 4 pi (k = 0.5),
-density 1 + 0.05 cos(kx), Maxwellian v_th = 1, dt = 0.1; every 50 steps the
-width is re-selected by leave-one-out CV over 64 candidates log-spaced in
-[1, 1e4] and Silverman's particle-wise widths (alpha = 0.5) are recomputed.
-One benchmark step is one such 50-step period: CV pair sums + integral term +
-leave-one-out pass + adaptive widths, then 50 x (sort, deposit, Poisson,
-gather + push + field energy).  All of it runs in libkdepic's CUDA kernels.
+Default line (`--workload landau`): the Landau-damping run with particle-wise widths --
+N = 2^20 electrons, Ng = 256 nodes, L = 4 pi (k = 0.5), density 1 + 0.05 cos(kx),
+Maxwellian v_th = 1, dt = 0.1; every 50 steps the width is re-selected by leave-one-out
+CV over 64 candidates log-spaced in [1, 1e4] and Silverman's particle-wise widths
+(alpha = 0.5) are recomputed.  One benchmark step is one such 50-step period on the
+library's production path: the CV in the cheaper of its two exact forms (the library's
+cost rule takes the Fourier form here), the Silverman widths, then 50 x (sort, deposit,
+Poisson, gather + push + field energy).  All of it runs in libkdepic's CUDA kernels.
 
-`value` counts the definition pairs of the deposit and gather, 2 N Ng per PIC
-step, divided by the device time of the whole period (CV included).  The CV
-pair throughput is reported beside it.  `--impl reference` times the FP64 CPU
-oracle on a bounded sample of the same workload (the reference arm).
+`value` = the in-radius (particle, node) pairs of the period's 50 deposits and 50 gathers
+divided by the period's device time.  Sub-records of the same line: the O(N^2) pair-sum
+CV at the CV-sweep configuration (`cv_pairs`), the 256-realisation ensemble
+(`ensemble`), the 10,000-request serving stream (`serve`) and the Sec. II.D schedule
+(`ad_schedule`).  `--impl reference` times the FP64 CPU oracle on a bounded sample of the
+same workload (the reference arm).
 """
 from __future__ import annotations
 
@@ -185,10 +187,75 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_ours(args, rank, world, local_rank):
+def timed(fn, flush, reps):
+    """CUDA-event times (ms) of reps calls of fn on the current stream, L2 flushed before each."""
+    import torch
+    out = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return out
+
+
+def landau_state(kp, dev, w, seed, max_steps, **kw):
     import torch
 
     import kde_inputs as I
+    N, Ng, L, dt, P = w["N"], w["Ng"], w["L"], w["dt"], w["period"]
+    cand = I.log_candidates(w["kmin_c"], w["kmax_c"], w["n_cand"])
+    u0, v0 = I.landau_load(seed, N, L, 0.05, 1.0)
+    st = kp.PicState(torch.from_numpy(u0.view(np.int32)).to(dev), torch.from_numpy(v0.astype(np.float32)).to(dev),
+                     L, Ng, dt, kappa=torch.ones(N, device=dev), ids=torch.arange(N, dtype=torch.int32, device=dev),
+                     width_every=P, cand=cand, alpha=w["alpha"], kappa_min=w["kappa_min"], kappa_max=w["kappa_max"],
+                     max_steps=max_steps, **kw)
+    return st, u0, v0, cand
+
+
+def cv_pairs_record(kp, ctx, dev, ex2_peak, reps=3):
+    """The O(N^2) pair-sum CV of Eq. cv_def at the CV-sweep configuration: N = 2^18 positions
+    from 0.7 U + 0.3 vonMises(pi, 20), 64 candidates in [1, 1e4], forced pair sums (the
+    production path would take the exact Fourier form).  Definition pairs/s and the exp2
+    roofline of the pair kernel."""
+    import torch
+
+    import kde_inputs as I
+    N, L = 1 << 18, 2 * math.pi
+    cand = I.log_candidates(1.0, 1e4, 64)
+    u_np = I.cv_sweep_load(0, N)
+    u = torch.from_numpy(u_np.view(np.int32)).to(dev)
+    loo = torch.empty(N, device=dev)
+    ctx.cv(u, L, cand, loo=loo, pairs=True)
+    ctx.profile_enable(True)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ctx.cv(u, L, cand, loo=loo, pairs=True)
+    wall = (time.perf_counter() - t0) / reps
+    cv_ms, cv_n = ctx.profile_read("cv_pairs")
+    ctx.profile_enable(False)
+    alg = cv_inradius_pairs(u_np, cand)
+    launch_ms = cv_ms / max(cv_n, 1)
+    ach = alg / (launch_ms * 1e-3)
+    return {"workload": "CV width sweep: N=2^18 mixture 0.7U+0.3vM(pi,20) on [0,2pi), 64 candidates in [1,1e4], "
+                        "O(N^2) pair sums (KDE_CV_PAIRS)",
+            "cv_pairs_per_s": 64 * N * (N - 1) / (wall), "unit": "definition pairs/s (64 N (N-1) per call)",
+            "ms_per_call": 1e3 * wall, "pair_kernel_ms": launch_ms,
+            "roofline": {"bound": "alu", "kernel": "cv_pairs_fast_kernel", "achieved": ach / 1e12,
+                         "peak": ex2_peak / 1e12, "unit": "Tex2/s", "frac": ach / ex2_peak,
+                         "algorithmic_units_per_launch": alg,
+                         "unit_def": "one exp2 per (unordered pair inside the candidate's truncation radius, "
+                                     "candidate)"}}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
     import paper_1804_11174_gb300 as kp
     from paper_1804_11174_gb300 import _build
 
@@ -202,28 +269,18 @@ def run_ours(args, rank, world, local_rank):
 
     w = LANDAU
     N, Ng, L, dt, P = w["N"], w["Ng"], w["L"], w["dt"], w["period"]
-    cand = I.log_candidates(w["kmin_c"], w["kmax_c"], w["n_cand"])
     ctx = kp.Context(local_rank)
     ctx.reserve(N, Ng, w["n_cand"])
     ctx.set_autotune(not args.no_autotune)  # gather tile shape tuned in the first warm-up step
     # each rank simulates its own realisation (independent replicas, weak scaling)
-    u0, v0 = I.landau_load(w["seed"] + rank, N, L, 0.05, 1.0)
-    u0_t = torch.from_numpy(u0.view(np.int32)).to(dev)
-    v0_t = torch.from_numpy(v0.astype(np.float32)).to(dev)
-    total_steps = P * (args.warmup + args.steps) + P
-    st = kp.PicState(u0_t.clone(), v0_t.clone(), L, Ng, dt, kappa=torch.ones(N, device=dev),
-                     ids=torch.arange(N, dtype=torch.int32, device=dev), width_every=P, cand=cand,
-                     alpha=w["alpha"], kappa_min=w["kappa_min"], kappa_max=w["kappa_max"], max_steps=total_steps,
-                     cv_spectral=args.cv == "spectral")
+    st, u0, v0, cand = landau_state(kp, dev, w, w["seed"] + rank, P * (args.warmup + args.steps + 1),
+                                    cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
-
     for _ in range(args.warmup):
         ctx.pic_step(st, P)
     torch.cuda.synchronize()
 
-    # algorithmic CV work of each timed period (positions at the start of the period)
-    step_ms = []
-    cv_alg = []
+    # ---- the production width-update period: CV (cost rule) + Silverman + 50 PIC steps ----
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -231,77 +288,47 @@ def run_ours(args, rank, world, local_rank):
     clocks.start()
     ctx.profile_enable(True)
     wall0 = time.perf_counter()
-    grid_alg = []
+    step_ms, pairs = [], []
     for _ in range(args.steps):
-        if rank == 0:
-            cv_alg.append(st.u.cpu().numpy().view(np.uint32).copy())
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        ctx.pic_step(st, P)
-        b.record()
-        b.synchronize()
-        step_ms.append(a.elapsed_time(b))
-        if rank == 0:  # widths in force for the period's steps (set by its first-step update)
-            grid_alg.append(grid_window_pairs(st.kappa.cpu().numpy(), Ng))
+        step_ms += timed(lambda: ctx.pic_step(st, P), flush, 1)
+        # widths in force during the period (set by its first-step update), for the
+        # in-radius pair count of its 50 deposits and 50 gathers
+        pairs.append(2.0 * P * grid_window_pairs(st.kappa.cpu().numpy(), Ng))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    cv_ms, cv_n = ctx.profile_read("cv_pairs")
-    prof = {k: ctx.profile_read(k) for k in ("deposit", "gather", "sort", "poisson", "cv_grid", "cv_loo",
-                                              "spectral")}
+    prof = {k: ctx.profile_read(k) for k in ("deposit", "gather", "sort", "poisson", "spectral", "cv_pairs",
+                                              "cv_grid", "cv_loo")}
     _, launches = ctx.profile_read("all")
     ctx.profile_enable(False)
     clk = clocks.stop()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-
-    t_step = float(np.sum(step_ms)) / args.steps  # ms of device time per period
+    t_step = float(np.mean(step_ms))
     if dist:
         tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step = float(tt.item())
-    pairs_dg = 2.0 * N * Ng * P  # deposit + gather definition pairs per period
-    value = world * pairs_dg / (t_step * 1e-3)
-    cv_def_pairs = w["n_cand"] * N * (N - 1)  # ordered pairs i != j per candidate
-    cv_pairs_per_s = cv_def_pairs / (cv_ms / max(cv_n, 1) * 1e-3) if cv_n else None
+    pairs_period = float(np.mean(pairs))
+    value = world * pairs_period / (t_step * 1e-3)
 
-    # ---- e2e: the same period through the public API from pinned host buffers ----
-    e2e = None
-    if True:
-        hu = torch.from_numpy(u0.view(np.int32)).pin_memory()
-        hv = torch.from_numpy(v0.astype(np.float32)).pin_memory()
-        hk = torch.ones(N).pin_memory()
-        out_u = torch.empty(N, dtype=torch.int32).pin_memory()
-        out_v = torch.empty(N, dtype=torch.float32).pin_memory()
-        out_w = torch.empty(P, dtype=torch.float64).pin_memory()
-        e2e_steps = max(1, min(args.steps, 3))
-        st2 = kp.PicState(torch.empty(N, dtype=torch.int32, device=dev), torch.empty(N, device=dev), L, Ng, dt,
-                          kappa=torch.empty(N, device=dev), width_every=P, cand=cand, alpha=w["alpha"],
-                          kappa_min=w["kappa_min"], kappa_max=w["kappa_max"], max_steps=P,
-                          cv_spectral=args.cv == "spectral")
-        torch.cuda.synchronize()
-        e_ms = []
-        for _ in range(e2e_steps):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            st2.u.copy_(hu, non_blocking=True)
-            st2.v.copy_(hv, non_blocking=True)
-            st2.kappa.copy_(hk, non_blocking=True)
-            st2.c.step = 0
-            ctx.pic_step(st2, P)
-            out_u.copy_(st2.u, non_blocking=True)
-            out_v.copy_(st2.v, non_blocking=True)
-            out_w.copy_(st2.energy[:P], non_blocking=True)
-            b.record()
-            b.synchronize()
-            e_ms.append(a.elapsed_time(b))
-        e_t = float(np.mean(e_ms))
-        e2e = {"value": world * pairs_dg / (e_t * 1e-3), "unit": UNIT, "h2d_bytes_per_step": N * 12,
-               "d2h_bytes_per_step": N * 8 + P * 8, "ms_per_step": e_t}
+    # ---- e2e: the same period through the C ABI from pinned host buffers (pic_step_host:
+    #      host -> device copies of u, v, kappa, id, the period, copies back, inside the call) ----
+    st_h, _, _, _ = landau_state(kp, dev, w, w["seed"] + rank, P * (args.warmup + args.steps + 1),
+                                 cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
+    host = kp.PicState(st_h.u.cpu().pin_memory(), st_h.v.cpu().pin_memory(), L, Ng, dt,
+                       kappa=st_h.kappa.cpu().pin_memory(), ids=st_h.id.cpu().pin_memory(), width_every=P,
+                       cand=cand, alpha=w["alpha"], kappa_min=w["kappa_min"], kappa_max=w["kappa_max"],
+                       max_steps=P * (args.warmup + args.steps + 1),
+                       cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
+    del st_h
+    for _ in range(args.warmup):
+        ctx.pic_step_host(host, P)
+    e_ms = timed(lambda: ctx.pic_step_host(host, P), flush, max(1, min(args.steps, 5)))
+    e_t = float(np.mean(e_ms))
+    e2e = {"value": world * pairs_period / (e_t * 1e-3), "unit": UNIT, "ms_per_step": e_t,
+           "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16 + P * 8 * 2,
+           "path": "pic_step_host (C ABI, pinned host buffers; copies inside the call)"}
 
     if rank != 0:
         if dist:
@@ -311,10 +338,9 @@ def run_ours(args, rank, world, local_rank):
     ms_p, ops_p = ctx.probe_exp2(1 << 14)
     ex2_peak = ops_p / (ms_p * 1e-3)
     fm_ms, fm_ops = ctx.probe_fma(1 << 14)
-    # deposit and gather: in-radius (particle, node) pairs per launch over their mean launch time
-    per_launch = float(np.mean(grid_alg)) if grid_alg else 0.0
     kr = {}
-    for name, key in (("deposit_chunk_x2_kernel", "deposit"), ("gather2_kernel", "gather")):
+    per_launch = pairs_period / (2.0 * P)  # in-radius pairs of one deposit (or one gather)
+    for name, key in (("deposit_persist_kernel", "deposit"), ("gather2_kernel", "gather")):
         ms_k, n_k = prof[key]
         if n_k:
             ach_k = per_launch / (ms_k / n_k * 1e-3)
@@ -322,9 +348,8 @@ def run_ours(args, rank, world, local_rank):
                         "frac": ach_k / ex2_peak, "algorithmic_units_per_launch": per_launch,
                         "avg_launch_ms": ms_k / n_k, "launches": n_k,
                         "unit_def": "one exp2 per (particle, node) pair inside the particle's truncation radius"}
-    # the cell sort of every step (count, scan and scatter kernels), against HBM
     s_ms, s_n = prof["sort"]
-    hbm = measured_peaks().get("hbm_gbs") or 6768.8
+    hbm = measured_peaks().get("hbm_gbs") or 6773.2
     if s_n:
         sort_bytes = N * (4 + 20 + 20)
         ach_s = sort_bytes / (s_ms / s_n * 1e-3) / 1e9
@@ -333,84 +358,30 @@ def run_ours(args, rank, world, local_rank):
             "algorithmic_bytes_per_launch": sort_bytes, "avg_launch_ms": s_ms / s_n, "launches": s_n,
             "unit_def": "per particle: 4 B code read by the count pass, 20 B read and 20 B written by the "
                         "scatter (u, v, kappa, norm, id)"}
+    dom = max(("deposit_persist_kernel", "gather2_kernel"),
+              key=lambda k: kr[k]["avg_launch_ms"] * kr[k]["launches"] if k in kr else -1.0)
+    roof = dict(kr.get(dom, {}), kernel=dom, traffic=PROFILED_TRAFFIC.get(dom),
+                peak_source="measured ex2.approx.ftz.f32 stream on this GPU (kde_probe_exp2)",
+                fma_peak_tflops=2.0 * fm_ops / (fm_ms * 1e-3) / 1e12)
 
-    if args.cv == "spectral":
-        line = spectral_line(args, ctx, world, t_step, value, prof, launches, clk, e2e, wall, w, kr)
-        print(json.dumps(line), flush=True)
-        ctx.close()
-        if dist:
-            dist.destroy_process_group()
-        return
-    # ---- roofline of the dominant kernel (CV pair sums, bound by the exp2 unit) ----
-    alg = [cv_inradius_pairs(u, cand) for u in cv_alg]
-    alg_per_launch = float(np.mean(alg))
-    cv_launch_ms = cv_ms / max(cv_n, 1)
-    achieved = alg_per_launch / (cv_launch_ms * 1e-3)
-    roof = {"bound": "alu", "kernel": "cv_pairs_fast_kernel", "achieved": achieved / 1e12, "peak": ex2_peak / 1e12,
-            "unit": "Tex2/s", "frac": achieved / ex2_peak, "traffic": None,
-            "peak_source": "measured ex2.approx.ftz.f32 stream on this GPU (kde_probe_exp2)",
-            "fma_peak_tflops": 2.0 * fm_ops / (fm_ms * 1e-3) / 1e12,
-            "algorithmic_units_per_launch": alg_per_launch,
-            "unit_def": "one exp2 per (unordered pair inside the candidate's truncation radius, candidate)",
-            "avg_launch_ms": cv_launch_ms, "launches": cv_n}
-
-    # the same period with the width schedule in the exact Fourier form (same run, same state size)
-    variant = None
-    try:
-        st3 = kp.PicState(u0_t.clone(), v0_t.clone(), L, Ng, dt, kappa=torch.ones(N, device=dev),
-                          ids=torch.arange(N, dtype=torch.int32, device=dev), width_every=P, cand=cand,
-                          alpha=w["alpha"], kappa_min=w["kappa_min"], kappa_max=w["kappa_max"],
-                          max_steps=P * (args.warmup + args.steps), cv_spectral=True)
-        for _ in range(args.warmup):
-            ctx.pic_step(st3, P)
-        torch.cuda.synchronize()
-        v_ms = []
-        for _ in range(args.steps):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            ctx.pic_step(st3, P)
-            b.record()
-            b.synchronize()
-            v_ms.append(a.elapsed_time(b))
-        vt = float(np.mean(v_ms))
-        variant = {"cv": "exact Fourier form (kde_cv KDE_CV_SPECTRAL)", "ms_per_step": vt,
-                   "value": world * pairs_dg / (vt * 1e-3), "unit": UNIT}
-    except Exception as e:  # report, do not fail the main line
-        variant = {"error": str(e)}
-
-    # the same load with a uniform width under the Sec. II.D schedule: the Anderson-Darling
-    # test every step, CV (exact Fourier form) when the p-value halves, smoothing rate 0.05
-    ad_variant = None
-    try:
-        st4 = kp.PicState(u0_t.clone(), v0_t.clone(), L, Ng, dt, kappa_uniform=50.0, cand=cand,
-                          max_steps=P * (args.warmup + args.steps), width_ad=True, cv_spectral=True)
-        for _ in range(args.warmup):
-            ctx.pic_step(st4, P)
-        torch.cuda.synchronize()
-        ctx.profile_enable(True)
-        a_ms = []
-        for _ in range(args.steps):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            ctx.pic_step(st4, P)
-            b.record()
-            b.synchronize()
-            a_ms.append(a.elapsed_time(b))
-        ad_ms, ad_n = ctx.profile_read("ad")
-        ctx.profile_enable(False)
-        at = float(np.mean(a_ms))
-        lp = st4.ad_log_p.cpu().numpy()[:st4.c.step]
-        ad_variant = {"schedule": "Anderson-Darling test every step (Sec. II.D), uniform width, CV by the exact "
-                                  "Fourier form", "ms_per_step": at, "value": world * pairs_dg / (at * 1e-3),
-                      "unit": UNIT, "ad_terms_kernel_ms_per_pic_step": ad_ms / max(ad_n, 1),
-                      "optimisations": int(st4.c.n_opt), "kappa_final": float(st4.c.kappa_uniform),
-                      "log_p_first_last": [float(lp[0]), float(lp[-1])]}
-    except Exception as e:  # report, do not fail the main line
-        ad_variant = {"error": str(e)}
+    sub = {}
+    if not args.quick:
+        try:
+            sub["cv_pairs"] = cv_pairs_record(kp, ctx, dev, ex2_peak)
+        except Exception as e:  # report, do not fail the main line
+            sub["cv_pairs"] = {"error": str(e)}
+        try:
+            sub["ensemble"] = ensemble_record(kp, ctx, dev, args)
+        except Exception as e:
+            sub["ensemble"] = {"error": str(e)}
+        try:
+            sub["serve"] = serve_record(kp, args)
+        except Exception as e:
+            sub["serve"] = {"error": str(e)}
+        try:
+            sub["ad_schedule"] = ad_record(kp, ctx, dev, args, flush)
+        except Exception as e:
+            sub["ad_schedule"] = {"error": str(e)}
 
     try:
         # one width-update period (CV + 50 PIC steps) of a 2^18-particle sample: 10-30 s of CPU work
@@ -420,17 +391,20 @@ def run_ours(args, rank, world, local_rank):
     except Exception as e:  # the oracle needs gcc; report its absence instead of failing the bench
         cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "unavailable: %s" % e}
 
+    cv_form = {"auto": "cost rule (exact Fourier form on this load)", "pairs": "O(N^2) pair sums",
+               "spectral": "exact Fourier form"}[args.cv]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(w), "N": N, "Ng": Ng, "dt": dt, "pic_steps_per_step": P,
-                   "n_cand": w["n_cand"], "l2": "flushed before every timed step (256 MB write)",
+                   "n_cand": w["n_cand"], "cv_form": cv_form,
+                   "value_def": "in-radius deposit+gather (particle, node) pairs of the period / period time",
+                   "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "gather_tile_shape": "default" if args.no_autotune else "autotuned"},
-        "cv_pairs_per_s": cv_pairs_per_s,
-        "cv_ms_per_step": cv_launch_ms,
-        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "pairs_per_step": pairs_period,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "wall_s": wall,
         "clocks": clk,
         "e2e": e2e,
@@ -438,13 +412,42 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "kernel_rooflines": kr,
         "cpu_baseline": cpu,
-        "variant_cv_spectral": variant,
-        "variant_ad_schedule": ad_variant,
     }
+    line.update(sub)
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def ad_record(kp, ctx, dev, args, flush):
+    """The Landau load with a uniform width under the Sec. II.D schedule: the Anderson-Darling
+    test every step, CV (exact Fourier form) when the p-value halves, smoothing rate 0.05."""
+    import torch
+    w = LANDAU
+    P = w["period"]
+    st, _, _, cand = landau_state(kp, dev, w, w["seed"], P * 4, cv_spectral=True)
+    st4 = kp.PicState(st.u, st.v, w["L"], w["Ng"], w["dt"], kappa_uniform=50.0, cand=cand, max_steps=P * 4,
+                      width_ad=True, cv_spectral=True)
+    ctx.pic_step(st4, P)
+    torch.cuda.synchronize()
+    ctx.profile_enable(True)
+    a_ms = timed(lambda: ctx.pic_step(st4, P), flush, 2)
+    ad_ms, ad_n = ctx.profile_read("ad")
+    ctx.profile_enable(False)
+    at = float(np.mean(a_ms))
+    lp = st4.ad_log_p.cpu().numpy()[:st4.c.step]
+    return {"schedule": "Anderson-Darling test every step (Sec. II.D), uniform width, CV by the exact Fourier form",
+            "ms_per_step": at, "value": 2.0 * P * w["N"] * w["Ng"] / (at * 1e-3),
+            "value_def": "deposit+gather (particle, node) pairs (whole-grid windows) / period time",
+            "ad_terms_kernel_ms_per_pic_step": ad_ms / max(ad_n, 1), "optimisations": int(st4.c.n_opt),
+            "kappa_final": float(st4.c.kappa_uniform), "log_p_first_last": [float(lp[0]), float(lp[-1])]}
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels as
+# last captured by ncu on the Landau step (see profiles/); None until captured for the
+# current build of the kernel
+PROFILED_TRAFFIC = {"deposit_persist_kernel": None, "gather2_kernel": None}
 
 
 def run_cv_sweep(args, rank, world, local_rank):
@@ -497,34 +500,20 @@ def run_cv_sweep(args, rank, world, local_rank):
     ctx.close()
 
 
-def spectral_line(args, ctx, world, t_step, value, prof, launches, clk, e2e, wall, w, kr):
-    """Bench line for the Landau period with the width schedule in the exact Fourier form.
-    The PIC step is then the bulk of the period; the roofline line reports the slower of the
-    deposit and the gather (both bound by the exp2 unit), the others stay in kernel_rooflines."""
-    N, Ng, P = w["N"], w["Ng"], w["period"]
-    dom = max(("deposit_chunk_x2_kernel", "gather2_kernel"),
-              key=lambda k: kr[k]["avg_launch_ms"] * kr[k]["launches"] if k in kr else -1.0)
-    roof = dict(kr.get(dom, {}), kernel=dom, traffic=None)
-    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(w) + " [CV by the exact Fourier form]", "N": N, "Ng": Ng,
-                       "pic_steps_per_step": P, "l2": "flushed before every timed step (256 MB write)",
-                       "gather_tile_shape": "default" if args.no_autotune else "autotuned"},
-            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}, "wall_s": wall,
-            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernel_rooflines": kr}
+def serve_requests(R, seed=0, nmax_log2=22, cv_nmax_log2=17):
+    """The serving stream: kinds cycle deposit / gather / CV (16 scale factors on kappa_i) /
+    10-step PIC; N = floor(2^(12 + (nmax-12) U)), log-uniform in [2^12, 2^nmax] (CV requests
+    capped at 2^cv_nmax: their pair sums are O(N^2)); Ng log-uniform integer in [64, 4096];
+    kappa_i log-uniform in [5, 5e3]; Maxwellian v_th = 1; uniform positions.  Requests are
+    slices of one shared host pool held in page-locked memory."""
+    import torch
 
-
-def serve_requests(R, seed=0, nmax_log2=20, cv_nmax_log2=16):
-    """Bounded sample of the serving stream: kinds cycle deposit / gather / CV (16 scale
-    factors on kappa_i) / 10-step PIC; N = floor(2^(12 + (nmax-12) U)) (CV requests capped at
-    2^cv_nmax); Ng log-uniform integer in [64, 4096]; kappa_i log-uniform in [5, 5e3];
-    Maxwellian v_th = 1; uniform positions.  Requests are slices of one shared host pool."""
     import kde_inputs as I
     pool = 1 << nmax_log2
-    u = (I.splitmix64(seed, I.STREAM_X, pool) >> np.uint64(32)).astype(np.uint32)
-    kap = I.log_uniform(seed, I.STREAM_KAPPA, pool, 5.0, 5e3).astype(np.float32)
-    v = I.maxwellian(seed, pool, 1.0).astype(np.float32)
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    u = pin((I.splitmix64(seed, I.STREAM_X, pool) >> np.uint64(32)).astype(np.uint32))
+    kap = pin(I.log_uniform(seed, I.STREAM_KAPPA, pool, 5.0, 5e3).astype(np.float32))
+    v = pin(I.maxwellian(seed, pool, 1.0).astype(np.float32))
     U = I.uniforms(seed, I.STREAM_REQ, 3 * R)
     scales = 10.0 ** ((np.arange(16) - 8) / 8.0)
     reqs = []
@@ -545,19 +534,17 @@ def serve_requests(R, seed=0, nmax_log2=20, cv_nmax_log2=16):
     return reqs
 
 
-def serve_stream(kp, reqs, n_slots, arrivals):
+def serve_stream(kp, reqs, n_slots, arrivals, outs):
     """Submit each request at its arrival time (seconds from start) and return latencies (ms)
-    and the makespan (s)."""
+    and the makespan (s).  outs: preallocated page-locked output buffers per request."""
     srv = kp.Server(0, n_slots=n_slots, hbm_budget_bytes=100 << 30)
     L = 4 * math.pi
     tickets = []
     t0 = time.perf_counter()
-    for r, ta in zip(reqs, arrivals):
+    for r, ta, (out, out64) in zip(reqs, arrivals, outs):
         now = time.perf_counter() - t0
         if ta > now:
             time.sleep(ta - now)
-        out = np.empty(r["Ng"] if r["kind"] == 1 else r["N"], np.float32) if r["kind"] in (1, 2, 4) else None
-        out64 = np.empty(16 if r["kind"] == 3 else 10) if r["kind"] in (3, 4) else None
         tickets.append(srv.submit(r["kind"], r["u"], L, Ng=r["Ng"], kappa=r["kappa"], v=r.get("v"),
                                   field=r.get("field"), cand=r.get("cand"), n_steps=10 if r["kind"] == 4 else 0,
                                   dt=0.1, out=out, out64=out64))
@@ -567,64 +554,94 @@ def serve_stream(kp, reqs, n_slots, arrivals):
     return lat, span
 
 
-def run_serve(args, rank, world, local_rank):
+def serve_outputs(reqs):
+    import torch
+    pin = lambda n, dt: torch.empty(n, dtype=dt).pin_memory().numpy()
+    outs = []
+    for r in reqs:
+        out = pin(r["Ng"] if r["kind"] == 1 else r["N"], torch.float32) if r["kind"] in (1, 2, 4) else None
+        out64 = pin(16 if r["kind"] == 3 else 10, torch.float64) if r["kind"] in (3, 4) else None
+        outs.append((out, out64))
+    return outs
+
+
+def serve_record(kp, args):
+    """Continuous batching (args.slots slots) against the plain form (one slot: one request at a
+    time) on the same stream of args.requests requests: saturated throughput (everything
+    submitted at t = 0) and p50/p99 latency under Poisson arrivals at 0.9x the plain
+    throughput, each pair run args.serve_repeats times."""
     import kde_inputs as I
+    R = args.requests
+    t_build = time.perf_counter()
+    reqs = serve_requests(R, nmax_log2=args.serve_nmax_log2, cv_nmax_log2=args.serve_cv_nmax_log2)
+    outs = serve_outputs(reqs)
+    t_build = time.perf_counter() - t_build
+    warm = serve_requests(32, seed=99, nmax_log2=args.serve_nmax_log2, cv_nmax_log2=args.serve_cv_nmax_log2)
+    wouts = serve_outputs(warm)
+    serve_stream(kp, warm, args.slots, np.zeros(len(warm)), wouts)
+    serve_stream(kp, warm, 1, np.zeros(len(warm)), wouts)
+    pct = lambda a, q: float(np.percentile(a, q))
+    runs = []
+    for rep in range(args.serve_repeats):
+        _, span_p = serve_stream(kp, reqs, 1, np.zeros(R), outs)
+        _, span_b = serve_stream(kp, reqs, args.slots, np.zeros(R), outs)
+        mu_plain = R / span_p
+        gaps = -np.log(1.0 - I.uniforms(7 + rep, 7, R)) / (0.9 * mu_plain)
+        arr = np.cumsum(gaps) - gaps[0]
+        lat_p, _ = serve_stream(kp, reqs, 1, arr, outs)
+        lat_b, _ = serve_stream(kp, reqs, args.slots, arr, outs)
+        runs.append({"saturated_rps": {"batched": R / span_b, "plain": mu_plain},
+                     "poisson_rate_rps": 0.9 * mu_plain,
+                     "batched": {"p50_ms": pct(lat_b, 50), "p99_ms": pct(lat_b, 99)},
+                     "plain": {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99)}})
+    Ns = np.array([r["N"] for r in reqs])
+    return {"workload": "serving: %d requests cycling deposit / gather / CV (16 scales of kappa_i) / 10-step "
+                        "pic_step; N log-uniform in [2^12, 2^%d] (CV requests capped at 2^%d); Ng log-uniform in "
+                        "[64, 4096]; kappa_i log-uniform in [5, 5e3]; Maxwellian v; page-locked host buffers; "
+                        "HBM budget 100 GB; batched = %d slots, plain = 1 slot"
+                        % (R, args.serve_nmax_log2, args.serve_cv_nmax_log2, args.slots),
+            "requests": R, "particles_total": int(Ns.sum()), "largest_N": int(Ns.max()),
+            "runs": runs,
+            "batched_over_plain_rps": [r["saturated_rps"]["batched"] / r["saturated_rps"]["plain"] for r in runs],
+            "p99_batched_over_plain": [r["batched"]["p99_ms"] / r["plain"]["p99_ms"] for r in runs],
+            "host_build_s": t_build}
+
+
+def run_serve(args, rank, world, local_rank):
     import paper_1804_11174_gb300 as kp
     from paper_1804_11174_gb300 import _build
     _build.build()
     if rank != 0:
         return
-    R = args.requests
-    reqs = serve_requests(R)
-    warm = serve_requests(16, seed=99)
-    serve_stream(kp, warm, 8, np.zeros(len(warm)))
-    # saturated runs (everything submitted at t = 0): throughput of each server
-    lat_p0, span_p = serve_stream(kp, reqs, 1, np.zeros(R))
-    lat_b0, span_b = serve_stream(kp, reqs, args.slots, np.zeros(R))
-    mu_plain = R / span_p
-    # the same Poisson stream at 0.9 x the plain throughput for both servers
-    gaps = -np.log(1.0 - I.uniforms(7, 7, R)) / (0.9 * mu_plain)
-    arr = np.cumsum(gaps) - gaps[0]
-    lat_p, _ = serve_stream(kp, reqs, 1, arr)
-    lat_b, _ = serve_stream(kp, reqs, args.slots, arr)
-    pct = lambda a, q: float(np.percentile(a, q))
-    line = {"metric": METRIC, "value": R / span_b, "unit": "requests/s", "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": 1e3 * span_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving: %d requests (deposit/gather/CV/10-step PIC), N log-uniform in "
-                                   "[2^12, 2^20] (CV capped at 2^16), Ng in [64, 4096], kappa_i in [5, 5e3], "
-                                   "HBM budget 100 GB, %d slots" % (R, args.slots)},
-            "saturated": {"batched_rps": R / span_b, "plain_rps": mu_plain},
-            "poisson_0.9x_plain": {"rate_rps": 0.9 * mu_plain,
-                                   "batched": {"p50_ms": pct(lat_b, 50), "p99_ms": pct(lat_b, 99)},
-                                   "plain": {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99)}}}
+    rec = serve_record(kp, args)
+    r0 = rec["runs"][0]
+    line = {"metric": METRIC, "value": r0["saturated_rps"]["batched"], "unit": "requests/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * args.requests / r0["saturated_rps"]["batched"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": rec["workload"]}, "serve": rec}
     print(json.dumps(line), flush=True)
 
 
-def run_ensemble(args, rank, world, local_rank):
-    """Ensemble workload: R independent Landau realisations (seeds 0..R-1, alpha = 0.05,
-    v_th = 1, dt = 0.1), N log-uniform in [2^14, 2^20], Ng cycling {128, 256, 512, 1024}, one
-    uniform width per realisation chosen at t = 0 by the exact Fourier form of the CV over 16
-    candidates in [1, 1e3].  One step = one replay of the captured graph over all
-    realisations; compared with the plain form (pic_step per realisation, one after another,
-    on one stream).  value = deposit+gather definition pairs (2 sum_r N_r Ng_r) per second."""
+def ensemble_record(kp, ctx, dev, args):
+    """Ensemble: R independent Landau realisations (seeds 0..R-1, alpha = 0.05, v_th = 1,
+    dt = 0.1), N log-uniform in [2^14, 2^20], Ng cycling {128, 256, 512, 1024}, one uniform width
+    per realisation chosen at t = 0 by the CV (exact Fourier form) over 16 candidates in
+    [1, 1e3].  One step = one replay of the captured graph over all realisations; compared with
+    the same launches issued directly and with the plain form (pic_step per realisation, one
+    after another, on one stream; a 32-realisation sample scaled by particle count)."""
     import torch
 
     import kde_inputs as I
-    import paper_1804_11174_gb300 as kp
-    from paper_1804_11174_gb300 import _build
-    _build.build()
-    torch.cuda.set_device(local_rank)
-    dev = "cuda:%d" % local_rank
     R = args.realisations
     L = 4 * math.pi
     Ns, Ngs = I.ensemble_sizes(R)
     us, vs = [], []
+    t_build = time.perf_counter()
     for r in range(R):
         q = I.uniforms(r, I.STREAM_X, int(Ns[r]))
         us.append(I.to_fixed(I.inverse_cdf_cosine(q, L, 0.05), L))
         vs.append(I.maxwellian(r, int(Ns[r]), 1.0).astype(np.float32))
-    ctx = kp.Context(local_rank)
+    t_build = time.perf_counter() - t_build
     cand = I.log_candidates(1.0, 1e3, 16)
     kap = []
     for r in range(R):
@@ -632,64 +649,65 @@ def run_ensemble(args, rank, world, local_rank):
         kap.append(float(cand[am]))
     u = torch.from_numpy(np.concatenate(us).view(np.int32)).to(dev)
     v = torch.from_numpy(np.concatenate(vs)).to(dev)
-    ctx.set_autotune(not args.no_autotune)  # the lanes tune their gathers in the first (uncaptured) step
     ens = kp.Ensemble(ctx, Ns, Ngs, kap, L, 0.1, u, v)
     mise = ens.mise(0.05, 1).cpu().numpy()
-    steps = args.steps * 10
+    steps = args.ens_steps
     en = torch.zeros(R * steps, dtype=torch.float64, device=dev)
-    ens.run(max(args.warmup, 1), None, use_graph=True)
+    ens.run(1, None, use_graph=True)
     ens.run(steps, en, use_graph=True)  # captures the step for this (energy, steps) pair
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    flush.zero_()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record()
-    ens.run(steps, en, use_graph=True)
-    b.record()
-    b.synchronize()
-    t_graph = a.elapsed_time(b) / steps
-    clk = clocks.stop()
-    flush.zero_()
-    a.record()
-    ens.run(steps, en, use_graph=False)
-    b.record()
-    b.synchronize()
-    t_launch = a.elapsed_time(b) / steps
-    # plain form: one realisation after another through pic_step (a bounded sample)
+    t_graph = timed(lambda: ens.run(steps, en, use_graph=True), flush, 2)
+    t_launch = timed(lambda: ens.run(steps, en, use_graph=False), flush, 1)
+    t_graph, t_launch = min(t_graph) / steps, t_launch[0] / steps
     sample = min(R, 32)
     sts = [kp.PicState(torch.from_numpy(us[r].view(np.int32)).to(dev), torch.from_numpy(vs[r]).to(dev), L,
                        int(Ngs[r]), 0.1, kappa_uniform=kap[r]) for r in range(sample)]
     for s_ in sts:
         ctx.pic_step(s_, 1)
     torch.cuda.synchronize()
-    a.record()
-    for _ in range(3):
-        for s_ in sts:
-            ctx.pic_step(s_, 1)
-    b.record()
-    b.synchronize()
+
+    def plain():
+        for _ in range(3):
+            for s_ in sts:
+                ctx.pic_step(s_, 1)
     frac = float(np.sum(Ns[:sample])) / float(np.sum(Ns))
-    t_plain = a.elapsed_time(b) / 3 / frac
+    t_plain = timed(plain, flush, 1)[0] / 3 / frac
+    ens.close()
     Ntot = float(np.sum(Ns))
-    pairs = 2.0 * float(np.sum(Ns * Ngs))
-    line = {"metric": METRIC, "value": pairs / (t_graph * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": t_graph, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "ensemble of %d Landau realisations, N log-uniform in [2^14, 2^20] (total %d), "
-                                   "Ng in {128,256,512,1024}, one CUDA graph per step" % (R, int(Ntot)),
-                       "l2": "inputs larger than L2 (%.0f MB of particle state)" % (Ntot * 8 / 1e6),
-                       "gather_tile_shape": "default" if args.no_autotune else "autotuned"},
-            "particle_steps_per_s": Ntot / (t_graph * 1e-3),
-            "ms_per_step_graph": t_graph, "ms_per_step_launches": t_launch,
+    return {"workload": "ensemble of %d Landau realisations, N log-uniform in [2^14, 2^20] (total %d), Ng in "
+                        "{128,256,512,1024}, one CUDA graph per step" % (R, int(Ntot)),
+            "particles": int(Ntot), "ms_per_step_graph": t_graph, "ms_per_step_launches": t_launch,
             "ms_per_step_plain_per_realisation": t_plain,
+            "particle_steps_per_s_graph": Ntot / (t_graph * 1e-3),
+            "particle_steps_per_s_plain": Ntot / (t_plain * 1e-3),
+            "graph_over_plain": t_plain / t_graph,
+            "pairs_per_s_graph_definition": 2.0 * float(np.sum(Ns * Ngs)) / (t_graph * 1e-3),
             "mise_t0": {"mean": float(np.mean(mise)), "min": float(np.min(mise)), "max": float(np.max(mise))},
-            "kappa_star": {"min": float(np.min(kap)), "max": float(np.max(kap))}, "clocks": clk}
+            "kappa_star": {"min": float(np.min(kap)), "max": float(np.max(kap))},
+            "l2": "inputs larger than L2 (%.0f MB of particle state)" % (Ntot * 8 / 1e6),
+            "host_build_s": t_build}
+
+
+def run_ensemble(args, rank, world, local_rank):
+    import torch
+
+    import paper_1804_11174_gb300 as kp
+    from paper_1804_11174_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = "cuda:%d" % local_rank
+    ctx = kp.Context(local_rank)
+    ctx.set_autotune(not args.no_autotune)  # the lanes tune their gathers in the first (uncaptured) step
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    rec = ensemble_record(kp, ctx, dev, args)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": rec["pairs_per_s_graph_definition"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.ens_steps, "warmup": 1, "ms_per_step": rec["ms_per_step_graph"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": rec["workload"], "l2": rec["l2"]}, "ensemble": rec, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ens.close()
     ctx.close()
 
 
@@ -913,11 +931,17 @@ def main():
     ap.add_argument("--stat-steps", type=int, default=1500, help="landau_stats: PIC steps per run")
     ap.add_argument("--realisations", type=int, default=256, help="ensemble: realisations")
     ap.add_argument("--loads", type=int, default=8, help="shapes: independent particle loads")
-    ap.add_argument("--requests", type=int, default=1000, help="serving: requests in the sample")
+    ap.add_argument("--requests", type=int, default=10000, help="serving: requests in the stream")
     ap.add_argument("--slots", type=int, default=8, help="serving: slots of the batched server")
+    ap.add_argument("--serve-repeats", type=int, default=2, help="serving: repeats of each comparison")
+    ap.add_argument("--serve-nmax-log2", type=int, default=22, help="serving: largest request size (log2 N)")
+    ap.add_argument("--serve-cv-nmax-log2", type=int, default=17, help="serving: largest CV request (log2 N)")
+    ap.add_argument("--ens-steps", type=int, default=20, help="ensemble: timed steps per replay")
+    ap.add_argument("--quick", action="store_true", help="default line without the sub-records")
     ap.add_argument("--no-autotune", action="store_true", help="keep the gather's default tile shape")
-    ap.add_argument("--cv", default="pairs", choices=["pairs", "spectral"],
-                    help="CV evaluation in the width schedule: O(N^2) pair sums or the exact Fourier form")
+    ap.add_argument("--cv", default="auto", choices=["auto", "pairs", "spectral"],
+                    help="CV evaluation in the width schedule: the library's cost rule (auto), O(N^2) pair "
+                         "sums or the exact Fourier form")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -312,7 +312,7 @@ class Context:
         self._check("pic_step_host", self.lib.pic_step_host(self.h, ctypes.byref(state.c), int(n_steps)))
 
     PROF = {"cv_pairs": 0, "deposit": 1, "gather": 2, "sort": 3, "poisson": 4, "cv_grid": 5, "cv_loo": 6,
-            "spectral": 7, "ad": 8}
+            "spectral": 7, "ad": 8, "deposit_rows": 9}
 
     def set_wait_limit(self, polls: int = -1):
         """kde_set_wait_limit: polls of a bounded device wait (-1: default, 0: give up at once)."""

@@ -85,6 +85,7 @@ enum WsSlot {
     WS_AD_OUT,
     WS_CV_GPAR,
     WS_GREEN,
+    WS_DEP_ROWS,   // persistent FP32 deposit: per-CTA node rows and their headers
     WS_HOST_U,     // device copies of a host-resident PIC state (pic_step_host)
     WS_HOST_V,
     WS_HOST_K,
@@ -96,7 +97,7 @@ enum WsSlot {
 
 // kernels timed by the profiling hook (kde_profile_enable / kde_profile_read)
 enum KdeProfId { PROF_CV_PAIRS = 0, PROF_DEPOSIT, PROF_GATHER, PROF_SORT, PROF_POISSON, PROF_CV_GRID, PROF_CV_LOO,
-                 PROF_SPECTRAL, PROF_AD, PROF_NIDS };
+                 PROF_SPECTRAL, PROF_AD, PROF_DEPOSIT_ROWS, PROF_NIDS };
 
 struct kde_ctx {
     int device = 0;
@@ -380,6 +381,8 @@ kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T
 template <typename T>
 kde_status kde_acc_to_real(kde_ctx *ctx, const long long *acc, int Ng, double bound, const unsigned int *wmax_bits,
                            double wscale, T *out);
+// grows the workspace of the FP32 deposit for N particles on Ng nodes (kde_reserve)
+kde_status kde_deposit_reserve(kde_ctx *ctx, int64_t N, int Ng);
 
 // Poisson solve of rho_total = background + charge * rho, rho given as a real
 // array or as int64 accumulators (value = acc * acc_inv)

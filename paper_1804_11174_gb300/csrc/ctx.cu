@@ -301,6 +301,7 @@ extern "C" kde_status kde_reserve(kde_ctx *ctx, int64_t N, int32_t Ng, int32_t n
     for (auto &b : big)
         if (!kde_ws(ctx, (WsSlot)b[0], b[1])) return KDE_ENOMEM;
     if (!kde_node_table(ctx, Ng, false) || !kde_node_table(ctx, Ng, true)) return KDE_ENOMEM;
+    if (N > 0) KDE_TRY(kde_deposit_reserve(ctx, N, Ng));
     return KDE_OK;
 }
 

@@ -513,6 +513,316 @@ __global__ void __launch_bounds__(DEP_THREADS) deposit_chunk_kernel(DepSrc<T> S)
     deposit_chunk_body<T>(S, blockIdx.x, rec, part, red);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 deposit of cell-sorted particles over a balanced persistent grid, without
+// global atomics.
+//
+// G = min(4 x SMs, ceil(N / 256)) CTAs (one wave); CTA c owns the contiguous
+// particles [c N / G, (c + 1) N / G), so every CTA carries the same number of
+// particles and, since a particle's cost is its window, nearly the same work.
+// The CTA's node window is fixed up front: its first and last cell widened by the
+// window of its smallest width.  Its particles are taken in sub-chunks of
+// DEPP_SUB records (one float4 each: the two angle terms and the weighted norm;
+// a Landau-size run of 2^20 particles has one sub-chunk a CTA), the inputs of a
+// sub-chunk loaded in batches of register loads, and swept by node-owner lanes as
+// in the chunk kernel (f32x2 pairs of nodes, fixed-order combination of particle
+// slices).  After every sub-chunk the FP32 node sums become int64 fixed point in
+// the CTA's row of the workspace (each node always by the same thread: plain
+// loads and stores).  A second kernel sums the rows: one CTA per 32 nodes, its
+// warps taking the rows in turn with all their loads in flight, the warps'
+// integer sums combined in shared memory, every output node written with a plain
+// store.  Integer sums make the result exact and independent of any order.
+// ---------------------------------------------------------------------------
+#define DEPP_THREADS 256
+#define DEPP_WARPS 8
+#define DEPP_MINB 4
+#define DEPP_SUB 2048
+#define DEPP_PART 512
+#define DEPP_RED_THREADS 1024
+#define DEPP_RED_NODES 32
+
+struct DepPlan {
+    int G;            // CTAs
+    long long *rows;  // [G][Ng] per-CTA node sums over its window
+    int2 *hdr;        // [G] (first node, node count) of every row
+    long long *acc;   // [Ng] output accumulators (every node written by the row reduction)
+};
+// node pairs of the persistent deposit: each lane owns P pairs of nodes (64 P
+// consecutive nodes a warp pass) of the window [g_lo, g_lo + R); the n records of
+// the sub-chunk are split into slices when there are fewer node groups than warps.
+// flush(r, a) receives the FP32 sum of window node r over the sub-chunk, once per node.
+template <int P, typename F>
+__device__ __forceinline__ void depp_sweep(const DepSrc<float> &S, int n, int g_lo, int R, bool cosf,
+                                           const float4 *rec, float *part, F &&flush)
+{
+    constexpr int GW = 64 * P;
+    constexpr int U = 4;
+    const int Ng = S.Ng;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ngroups = (R + GW - 1) / GW;
+    kde_f2 SS[P], CC[P], acc[P];
+    auto nodes_of = [&](int gi) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            float sa, ca, sb, cb;
+            const int ra = gi * GW + 64 * q + lane, rb = ra + 32;
+            int ga = g_lo + ra, gb = g_lo + rb;
+            ga = ga < 0 ? ga + Ng : (ga >= Ng ? ga - Ng : ga);
+            gb = gb < 0 ? gb + Ng : (gb >= Ng ? gb - Ng : gb);
+            node_sc(S, ra < R ? ga : 0, sa, ca);
+            node_sc(S, rb < R ? gb : 0, sb, cb);
+            if (cosf) {
+                SS[q] = kde_pk(2.f * sa * ca, 2.f * sb * cb);
+                CC[q] = kde_pk((ca - sa) * (ca + sa), (cb - sb) * (cb + sb));
+            } else {
+                SS[q] = kde_pk(sa, sb);
+                CC[q] = kde_pk(-ca, -cb);
+            }
+        }
+    };
+    // record (a, b, w): cosine form a = K cos x_j, b = K sin x_j, exponent
+    // S_g b + C_g a = K cos(x_j - x_g); half-angle form a = beta sin, b = beta cos of
+    // half the angle, s = S_g b - C_g a and the exponent -s^2
+    auto sweep = [&](int p0, int p1) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) acc[q] = kde_pk(0.f, 0.f);
+        if (cosf) {
+#pragma unroll U
+            for (int p = p0; p < p1; ++p) {
+                const float4 r4 = rec[p];
+                const kde_f2 qa = kde_pk(r4.x, r4.x), qb = kde_pk(r4.y, r4.y), w = kde_pk(r4.z, r4.z);
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    acc[q] = kde_fma2(kde_ex22(kde_fma2(SS[q], qb, kde_mul2(CC[q], qa))), w, acc[q]);
+            }
+        } else {
+#pragma unroll U
+            for (int p = p0; p < p1; ++p) {
+                const float4 r4 = rec[p];
+                const kde_f2 qa = kde_pk(r4.x, r4.x), qb = kde_pk(r4.y, r4.y), w = kde_pk(r4.z, r4.z);
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const kde_f2 sv = kde_fma2(SS[q], qb, kde_mul2(CC[q], qa));
+                    acc[q] = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), w, acc[q]);
+                }
+            }
+        }
+    };
+    if (ngroups >= DEPP_WARPS) {
+        for (int gi = warp; gi < ngroups; gi += DEPP_WARPS) {
+            nodes_of(gi);
+            sweep(0, n);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                float a0, a1;
+                kde_upk(acc[q], a0, a1);
+                const int ra = gi * GW + 64 * q + lane;
+                if (ra < R) flush(ra, a0);
+                if (ra + 32 < R) flush(ra + 32, a1);
+            }
+        }
+        return;
+    }
+    // every warp works: warp w takes node group w mod ngroups and one of that group's
+    // particle slices (slice counts differ by at most one); ngroups GW <= DEPP_PART
+    const int gi = warp % ngroups, sl = warp / ngroups;
+    const int slices = (DEPP_WARPS - gi + ngroups - 1) / ngroups;
+    {
+        const int p0 = (int)((int64_t)n * sl / slices), p1 = (int)((int64_t)n * (sl + 1) / slices);
+        nodes_of(gi);
+        sweep(p0, p1);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            float a0, a1;
+            kde_upk(acc[q], a0, a1);
+            part[sl * DEPP_PART + gi * GW + 64 * q + lane] = a0;
+            part[sl * DEPP_PART + gi * GW + 64 * q + 32 + lane] = a1;
+        }
+    }
+    __syncthreads();
+    for (int r = tid; r < ngroups * GW; r += DEPP_THREADS) {
+        if (r >= R) continue;
+        const int gr = r / GW, sr = (DEPP_WARPS - gr + ngroups - 1) / ngroups;
+        float a = 0.f;
+        for (int k = 0; k < sr; ++k) a += part[k * DEPP_PART + r];
+        flush(r, a);
+    }
+}
+
+// acc[g] = sum over the rows whose window covers node g of that row's entry; CTA b
+// takes nodes [32 b, 32 b + 32), lane l node 32 b + l, warp w rows w, w + 32, ...
+__global__ void __launch_bounds__(DEPP_RED_THREADS) deposit_rows_kernel(const long long *__restrict__ rows,
+                                                                       const int2 *__restrict__ hdr, int G, int Ng,
+                                                                       long long *acc)
+{
+    __shared__ long long wsum[DEPP_RED_THREADS / 32][DEPP_RED_NODES];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = DEPP_RED_THREADS / 32;
+    const int g = blockIdx.x * DEPP_RED_NODES + lane;
+    long long sum = 0;
+    if (g < Ng) {
+        // rows in batches of 8 per warp, every load of a batch issued before any is used
+        for (int k0 = warp; k0 < G; k0 += 8 * NW) {
+            long long v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + q * NW;
+                v[q] = 0;
+                if (k < G) {
+                    const int2 h = hdr[k];
+                    int r = g - h.x;
+                    r = r < 0 ? r + Ng : (r >= Ng ? r - Ng : r);
+                    if (r < h.y) v[q] = rows[(size_t)k * Ng + r];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sum += v[q];
+        }
+    }
+    wsum[warp][lane] = sum;
+    __syncthreads();
+    if (warp == 0 && g < Ng) {
+        long long t = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t += wsum[w][lane];
+        acc[g] = t;
+    }
+}
+
+__global__ void __launch_bounds__(DEPP_THREADS, DEPP_MINB) deposit_persist_kernel(DepSrc<float> S, DepPlan Pl)
+{
+    __shared__ __align__(16) unsigned char smraw[DEPP_SUB * 16 + DEPP_WARPS * DEPP_PART * 4];
+    __shared__ float sred[2 * DEPP_WARPS];
+    __shared__ int s_es, s_last;
+    static_assert(DEPP_SUB * 16 + DEPP_WARPS * DEPP_PART * 4 >= KDE_MAX_NG * 8, "reduction buffer");
+    constexpr int PER = DEPP_SUB / DEPP_THREADS;  // particles of a sub-chunk per thread
+    float4 *rec = (float4 *)smraw;
+    float *part = (float *)(smraw + DEPP_SUB * 16);
+    long long *red = (long long *)smraw;
+    const int Ng = S.Ng;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = blockIdx.x;
+    const int64_t i0 = S.N * c / Pl.G, i1 = S.N * (c + 1) / Pl.G;  // non-empty: G <= N
+
+    // smallest and largest width of the CTA's particles (the window and the form): a pass
+    // over the widths, PER loads in flight per thread
+    float kmin = (float)KDE_KAPPA_MAX, kmax = 0.f;
+    for (int64_t j0 = i0; j0 < i1; j0 += (int64_t)PER * DEPP_THREADS) {
+        float kk[PER];
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            const int64_t j = j0 + tid + p * DEPP_THREADS;
+            kk[p] = j < i1 ? (S.kappa ? S.kscale * S.kappa[j] : S.kappa_u) : -1.f;
+        }
+#pragma unroll
+        for (int p = 0; p < PER; ++p)
+            if (kk[p] != -1.f) {
+                const float k = (kk[p] > 0.f && kk[p] <= (float)KDE_KAPPA_MAX) ? kk[p] : (float)KDE_KAPPA_MAX;
+                kmin = fminf(kmin, k);
+                kmax = fmaxf(kmax, k);
+            }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    if (lane == 0) {
+        sred[warp] = kmin;
+        sred[DEPP_WARPS + warp] = kmax;
+    }
+    if (tid == 0) {
+        int es = S.scale_exp;
+        if (es == KDE_ES_FROM_BOUND) {
+            double bound = S.bound;
+            if (S.wmax_bits)
+                bound = (double)S.N * (double)S.coef * S.norm_bound * (double)__uint_as_float(*S.wmax_bits);
+            es = acc_scale_exp(bound);
+        }
+        s_es = es;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < DEPP_WARPS; ++k) {
+        kmin = fminf(kmin, sred[k]);
+        kmax = fmaxf(kmax, sred[DEPP_WARPS + k]);
+    }
+    const int es = s_es;
+    const bool cosf = kmax <= KDE_COSFORM_KMAX;
+    const int W = window_nodes_f(kmin, Ng, (float)KDE_XCUT);
+    const int c_first = kde_cell(S.u[i0], Ng), c_last = kde_cell(S.u[i1 - 1], Ng);
+    int g_lo = c_first - W;
+    int R = c_last + W - g_lo + 1;
+    if (R >= Ng || R < 1 || c_last < c_first) {
+        g_lo = 0;
+        R = Ng;
+    }
+    // 4, 2 or 1 node pairs a lane: the widest that computes no extra nodes and whose
+    // slice sums fit the buffer
+    const int n64 = (R + 63) >> 6, n128 = (R + 127) >> 7, n256 = (R + 255) >> 8;
+    const int P = (4 * n256 == n64 && (n256 >= DEPP_WARPS || n256 * 256 <= DEPP_PART))   ? 4
+                  : (2 * n128 == n64 && (n128 >= DEPP_WARPS || n128 * 128 <= DEPP_PART)) ? 2
+                                                                                          : 1;
+    long long *row = Pl.rows + (size_t)c * Ng;
+
+    for (int64_t b0 = i0; b0 < i1; b0 += DEPP_SUB) {
+        const int n = (int)(i1 - b0 < DEPP_SUB ? i1 - b0 : DEPP_SUB);
+        const bool first = b0 == i0;
+        if (!first) __syncthreads();  // the previous sub-chunk's readers of rec and part are done
+        // the particle records (a, b, w n) of the form in use, in groups of four particles a
+        // thread whose inputs are loaded together (one global-load latency per group)
+        constexpr int QB = 4;
+#pragma unroll
+        for (int p0 = 0; p0 < PER; p0 += QB) {
+            uint32_t ru[QB];
+            float rk[QB], rn[QB], rw[QB];
+#pragma unroll
+            for (int q = 0; q < QB; ++q) {
+                const int t = tid + (p0 + q) * DEPP_THREADS;
+                const int64_t j = b0 + (t < n ? t : 0);
+                ru[q] = S.u[j];
+                rk[q] = S.kappa ? S.kscale * S.kappa[j] : S.kappa_u;
+                rn[q] = S.norm ? S.norm[j] : 0.f;
+                rw[q] = S.w ? S.w[j] : S.w_u;
+            }
+#pragma unroll
+            for (int q = 0; q < QB; ++q) {
+                const int t = tid + (p0 + q) * DEPP_THREADS;
+                if (t >= n) break;
+                float k = rk[q];
+                if (!(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
+                    kde_flag(S.status, KDE_DEV_KAPPA_RANGE, (unsigned)(b0 + t));
+                    k = (float)KDE_KAPPA_MAX;
+                }
+                float nm;
+                if (S.norm) nm = rn[q];
+                else if (S.kappa) nm = S.ntab ? kde_norm_tab(S.ntab, k) : (float)kde_norm((double)k);
+                else nm = S.norm_u;
+                const float wn = rw[q] * S.coef * nm;
+                float sh, ch;
+                kde_half_sincos(ru[q], sh, ch);
+                if (cosf) {
+                    const float K = (float)KDE_LOG2E * k;
+                    rec[t] = make_float4(K * ((ch - sh) * (ch + sh)), K * (2.f * sh * ch), wn * kde_ex2(-K), 0.f);
+                } else {
+                    const float beta = sqrtf((float)(2.0 * KDE_LOG2E) * k);
+                    rec[t] = make_float4(beta * sh, beta * ch, wn, 0.f);
+                }
+            }
+        }
+        __syncthreads();
+        auto flush = [&](int r, float a) {
+            // x 2^es in integer arithmetic; the FP64 product only for extreme bounds
+            const long long v = (es >= -100 && es <= 100) ? fix_pow2(a, es) : __double2ll_rn(ldexp((double)a, es));
+            row[r] = first ? v : __ldcg(&row[r]) + v;
+        };
+        if (P == 4) depp_sweep<4>(S, n, g_lo, R, cosf, rec, part, flush);
+        else if (P == 2) depp_sweep<2>(S, n, g_lo, R, cosf, rec, part, flush);
+        else depp_sweep<1>(S, n, g_lo, R, cosf, rec, part, flush);
+    }
+    if (tid == 0) Pl.hdr[c] = make_int2(g_lo, R);
+}
+
 // acc -> real values
 template <typename T>
 __global__ void acc_to_real_kernel(const long long *acc, int Ng, double bound, const unsigned int *wmax_bits,
@@ -542,12 +852,36 @@ __global__ void wmax_kernel(const T *w, int64_t N, unsigned int *wmax_bits, unsi
 }
 
 // ---------------------------------------------------------------------------
+// workspace of the persistent FP32 deposit for N particles on Ng nodes: the CTAs'
+// rows and their headers
+static kde_status depp_plan(kde_ctx *ctx, int64_t N, int Ng, long long *acc, DepPlan &Pl)
+{
+    const int64_t gmax = (int64_t)DEPP_MINB * ctx->sm_count;
+    const int64_t gn = (N + 255) / 256;
+    Pl.G = (int)(gn < gmax ? gn : gmax);
+    const size_t rows_b = (size_t)Pl.G * Ng * 8;
+    unsigned char *w = (unsigned char *)kde_ws(ctx, WS_DEP_ROWS, rows_b + (size_t)Pl.G * 8);
+    if (!w) return KDE_ENOMEM;
+    Pl.rows = (long long *)w;
+    Pl.hdr = (int2 *)(w + rows_b);
+    Pl.acc = acc;
+    return KDE_OK;
+}
+
+kde_status kde_deposit_reserve(kde_ctx *ctx, int64_t N, int Ng)
+{
+    DepPlan Pl{};
+    return depp_plan(ctx, N, Ng, nullptr, Pl);
+}
+
 template <typename T>
 kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,
                               const T *w, T w_u, int64_t N, int Ng, double coef, long long *acc, double bound,
                               const unsigned int *wmax_bits, double norm_bound)
 {
-    KDE_CUDA(ctx, cudaMemsetAsync(acc, 0, (size_t)Ng * sizeof(long long), ctx->stream), "acc memset");
+    // the persistent FP32 kernel writes every node; the others add into zeroed accumulators
+    if (!(sizeof(T) == 4 && N > 0))
+        KDE_CUDA(ctx, cudaMemsetAsync(acc, 0, (size_t)Ng * sizeof(long long), ctx->stream), "acc memset");
     if (N == 0) return KDE_OK;
     const void *nodes = kde_node_table(ctx, Ng, sizeof(T) == 8);
     if (!nodes) return KDE_ENOMEM;
@@ -578,13 +912,28 @@ kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T
         S.scale_exp = 62 - e;
     }
     S.ntab = ctx->norm_tab;
-    unsigned grid = (unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK);
-    {
-        KdeProfScope _ps(ctx, PROF_DEPOSIT);
-        if constexpr (sizeof(T) == 4) deposit_chunk_x2_kernel<<<grid, DEP_THREADS, 0, ctx->stream>>>(S);
-        else deposit_chunk_kernel<T><<<grid, DEP_THREADS, 0, ctx->stream>>>(S);
+    if constexpr (sizeof(T) == 4) {
+        DepPlan Pl{};
+        KDE_TRY(depp_plan(ctx, N, Ng, acc, Pl));
+        {
+            KdeProfScope _ps(ctx, PROF_DEPOSIT);
+            deposit_persist_kernel<<<Pl.G, DEPP_THREADS, 0, ctx->stream>>>(S, Pl);
+        }
+        KDE_LAUNCHED(ctx, "deposit_persist_kernel");
+        {
+            KdeProfScope _ps(ctx, PROF_DEPOSIT_ROWS);
+            deposit_rows_kernel<<<(Ng + DEPP_RED_NODES - 1) / DEPP_RED_NODES, DEPP_RED_THREADS, 0, ctx->stream>>>(
+                Pl.rows, Pl.hdr, Pl.G, Ng, acc);
+        }
+        KDE_LAUNCHED(ctx, "deposit_rows_kernel");
+    } else {
+        unsigned grid = (unsigned)((N + DEP_CHUNK - 1) / DEP_CHUNK);
+        {
+            KdeProfScope _ps(ctx, PROF_DEPOSIT);
+            deposit_chunk_kernel<T><<<grid, DEP_THREADS, 0, ctx->stream>>>(S);
+        }
+        KDE_LAUNCHED(ctx, "deposit_chunk_kernel");
     }
-    KDE_LAUNCHED(ctx, "deposit_chunk_kernel");
     return KDE_OK;
 }
 

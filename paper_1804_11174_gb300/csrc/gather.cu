@@ -228,28 +228,26 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherAr
     float2 *FF = (float2 *)(SC + Ng);  // (E, E)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = ((int64_t)blockIdx.x * GAT2_WARPS + warp) * GAT2_ITEM;
-    float nm[GAT2_NP], kap[GAT2_NP], vin[GAT2_NP], nin[GAT2_NP];
-    uint32_t uu[GAT2_NP], idin[GAT2_NP];
-    bool valid[GAT2_NP];
+    // held across the node loop: positions and norms; widths until the particle terms
+    // are formed; the push's other inputs are loaded after the loop (registers are the
+    // limit with eight particles a lane, and other warps cover the load latency)
+    float nm[GAT2_NP], kap[GAT2_NP];
+    uint32_t uu[GAT2_NP];
     int lo = 0x3fffffff, hi = -0x3fffffff;
     float kmax = 0.f;
 #pragma unroll
     for (int h = 0; h < GAT2_NP; ++h) {
         const int64_t j = base + h * 32 + lane;
-        valid[h] = j < A.N;
-        uu[h] = valid[h] ? A.u[j] : 0u;
-        // the push's inputs are loaded now, so that their latency hides behind the node loop
-        vin[h] = (A.u_out && valid[h]) ? A.v_in[j] : 0.f;
-        nin[h] = (A.norm_out && valid[h]) ? A.norm_in[j] : 0.f;
-        idin[h] = (A.id_out && valid[h]) ? A.id_in[j] : 0u;
-        float k = A.kappa ? (valid[h] ? A.kappa[j] : 1.0f) : A.kappa_u;
-        if (valid[h] && !(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
+        const bool valid = j < A.N;
+        uu[h] = valid ? A.u[j] : 0u;
+        float k = A.kappa ? (valid ? A.kappa[j] : 1.0f) : A.kappa_u;
+        if (valid && !(k > 0.f && k <= (float)KDE_KAPPA_MAX)) {
             kde_flag(A.status, KDE_DEV_KAPPA_RANGE, (unsigned)j);
             k = (float)KDE_KAPPA_MAX;
         }
         kap[h] = k;
-        nm[h] = A.norm ? (valid[h] ? A.norm[j] : 0.f) : (A.kappa ? kde_norm_tab(A.ntab, k) : A.norm_u);
-        if (valid[h]) {
+        nm[h] = A.norm ? (valid ? A.norm[j] : 0.f) : (A.kappa ? kde_norm_tab(A.ntab, k) : A.norm_u);
+        if (valid) {
             kmax = fmaxf(kmax, k);
             const int cell = kde_cell(uu[h], Ng);
             const int W = window_nodes_g(k, Ng, (float)KDE_XCUT);
@@ -345,20 +343,45 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherAr
     float ea[GAT2_NP];
 #pragma unroll
     for (int q = 0; q < NPP; ++q) kde_upk(acc[q], ea[2 * q], ea[2 * q + 1]);
+    if (A.u_out) {
+        // the push's inputs of four particles at a time first (one load latency per group;
+        // the stores below alias nothing the loads read, but the compiler cannot know
+        // that), then the stores
+        constexpr int HB = GAT2_NP < 4 ? GAT2_NP : 4;
 #pragma unroll
-    for (int h = 0; h < GAT2_NP; ++h) {
-        if (!valid[h]) continue;
-        const int64_t j = base + h * 32 + lane;
-        const float Ei = ea[h] * nm[h] * A.coef;
-        if (A.u_out) {
-            const float v = vin[h] + A.kick_qm_dt * Ei;
+        for (int h0 = 0; h0 < GAT2_NP; h0 += HB) {
+        float vin[HB], kin[HB], nin[HB];
+        uint32_t idin[HB];
+#pragma unroll
+        for (int hh = 0; hh < HB; ++hh) {
+            const int64_t j = base + (h0 + hh) * 32 + lane;
+            const bool ok = j < A.N;
+            vin[hh] = ok ? A.v_in[j] : 0.f;
+            kin[hh] = (ok && A.kappa_out) ? (A.kappa ? A.kappa[j] : A.kappa_u) : 0.f;
+            nin[hh] = (ok && A.norm_out) ? A.norm_in[j] : 0.f;
+            idin[hh] = (ok && A.id_out) ? A.id_in[j] : 0u;
+        }
+#pragma unroll
+        for (int hh = 0; hh < HB; ++hh) {
+            const int h = h0 + hh;
+            const int64_t j = base + h * 32 + lane;
+            if (j >= A.N) continue;
+            const float v = vin[hh] + A.kick_qm_dt * (ea[h] * nm[h] * A.coef);
             A.v_out[j] = v;
             A.u_out[j] = advance_position(uu[h], v * A.dt_scale);
-            if (A.kappa_out) A.kappa_out[j] = kap[h];
-            if (A.norm_out) A.norm_out[j] = nin[h];
-            if (A.id_out) A.id_out[j] = idin[h];
-        } else {
-            A.out[A.perm ? A.perm[j] : j] = Ei;
+            if (A.kappa_out) {
+                const float k = kin[hh];
+                A.kappa_out[j] = (k > 0.f && k <= (float)KDE_KAPPA_MAX) ? k : (float)KDE_KAPPA_MAX;
+            }
+            if (A.norm_out) A.norm_out[j] = nin[hh];
+            if (A.id_out) A.id_out[j] = idin[hh];
+        }
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < GAT2_NP; ++h) {
+            const int64_t j = base + h * 32 + lane;
+            if (j < A.N) A.out[A.perm ? A.perm[j] : j] = ea[h] * nm[h] * A.coef;
         }
     }
 }
@@ -388,12 +411,14 @@ static kde_status gat2_launch(kde_ctx *ctx, const GatherArgs<float> &A)
 
 static kde_status gat2_variant(kde_ctx *ctx, const GatherArgs<float> &A, int v)
 {
-    // all with four particles a lane: the warps' particle sets, and so their node windows
-    // and kernel forms, are the same in every variant
+    // all with eight particles a lane (a block of four warps takes 1024 consecutive
+    // particles, so a Landau-size run of 2^20 particles is one wave of 1024 blocks):
+    // the warps' particle sets, and so their node windows and kernel forms, are the
+    // same in every variant
     switch (v) {
-    case 1: return gat2_launch<4, 4, 4, 8>(ctx, A);
-    case 2: return gat2_launch<4, 8, 4, 6>(ctx, A);
-    default: return gat2_launch<4, 8, 4, 5>(ctx, A);
+    case 1: return gat2_launch<8, 4, 4, 6>(ctx, A);
+    case 2: return gat2_launch<8, 8, 4, 4>(ctx, A);
+    default: return gat2_launch<8, 4, 4, 8>(ctx, A);
     }
 }
 

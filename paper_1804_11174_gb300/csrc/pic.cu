@@ -190,7 +190,11 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
         pa.qm_dt = st->qm * st->dt;
         pa.dt_scale = st->dt * 4294967296.0 / L;
         pa.energy = st->energy ? st->energy + step : nullptr;
-        pa.kstar_in = update || sched ? ks_dev : nullptr;
+        // the CV width in force: this step's update, else the previous step's history entry
+        // (the state's own record; the context's copy may belong to another state), else the
+        // context's copy (no history kept, so the value is not reported anywhere)
+        pa.kstar_in = update ? ks_dev
+                             : (sched && st->kappa_star && step > 0 ? st->kappa_star + step - 1 : (sched ? ks_dev : nullptr));
         pa.kstar_out = st->kappa_star ? st->kappa_star + step : nullptr;
         pa.dx = L / Ng;
         {
@@ -287,6 +291,10 @@ extern "C" kde_status pic_step_host(kde_ctx *ctx, pic_state *st, int32_t n_steps
     KDE_CUDA(ctx, cudaMemcpyAsync(d.v, st->v, N * el, cudaMemcpyHostToDevice, s), "state copy in");
     if (st->kappa) KDE_CUDA(ctx, cudaMemcpyAsync(d.kappa, st->kappa, N * el, cudaMemcpyHostToDevice, s), "state copy in");
     if (st->id) KDE_CUDA(ctx, cudaMemcpyAsync(d.id, st->id, N * 4, cudaMemcpyHostToDevice, s), "state copy in");
+    // the width in force before this call is the previous step's history entry
+    if (st->kappa_star && st->step > 0)
+        KDE_CUDA(ctx, cudaMemcpyAsync(d.kappa_star + st->step - 1, st->kappa_star + st->step - 1, 8,
+                                      cudaMemcpyHostToDevice, s), "history copy in");
     KDE_TRY(pic_step(ctx, &d, n_steps));
     KDE_CUDA(ctx, cudaMemcpyAsync(st->u, d.u, N * 4, cudaMemcpyDeviceToHost, s), "state copy out");
     KDE_CUDA(ctx, cudaMemcpyAsync(st->v, d.v, N * el, cudaMemcpyDeviceToHost, s), "state copy out");
