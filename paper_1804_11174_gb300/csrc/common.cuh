@@ -109,7 +109,7 @@ struct kde_ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     std::string err;
-    unsigned int *d_status = nullptr;  // [0] code, [1] detail, [2] sort-scan ticket (zero between calls), [3] spare
+    unsigned int *d_status = nullptr;  // [0] code, [1] detail, [2], [3] spare
     void *ws[WS_NSLOTS] = {};
     size_t ws_bytes[WS_NSLOTS] = {};
     // cached tables keyed by (Ng, precision): half-angle sines/cosines of the nodes
@@ -120,6 +120,7 @@ struct kde_ctx {
     void *ad_tab = nullptr;
     float2 *norm_tab = nullptr;  // FP32 width-normalisation table (kde_norm_tab), built at creation
     unsigned wait_polls = 1u << 26;         // polls of a bounded device wait (kde_set_wait_limit)
+    bool count_flip = false;                // which sort count table the next counted sort reads (sort.cu)
     bool autotune = false;                  // kde_set_autotune
     std::map<uint64_t, int> gat2_tuned;     // packed-gather tile shape per key (gather.cu)
     void *sp_atab = nullptr;                // workspace holding the Bessel ratios of sp_atab_cands (spectral.cu)
@@ -357,7 +358,16 @@ struct SortPayload {
     int elem;
 };
 kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, uint32_t *u_out,
-                           const SortPayload *pl, int npl, uint32_t *perm_out);
+                           const SortPayload *pl, int npl, uint32_t *perm_out, bool counted = false);
+// the count table of such a sort (bin-major: entry bin * nblk + tile, tile = index >>
+// tile_shift), for a kernel that adds the counts of the keys it writes; with
+// counted = true kde_sort_by_bin uses the table as it stands (every sort leaves it zero)
+struct SortCounts {
+    unsigned int *counts;
+    int nblk;
+    int tile_shift;
+};
+kde_status kde_sort_counts_table(kde_ctx *ctx, int64_t N, int nbins, SortCounts *out);
 // standard-PIC shapes inside pic_step: deposit of the B-spline shape (degree
 // order, width h) into int64 accumulators acc[Ng] (zeroed here; *bound_out = the
 // largest possible node value), and gather + leap-frog push in place
@@ -383,6 +393,21 @@ kde_status kde_acc_to_real(kde_ctx *ctx, const long long *acc, int Ng, double bo
                            double wscale, T *out);
 // grows the workspace of the FP32 deposit for N particles on Ng nodes (kde_reserve)
 kde_status kde_deposit_reserve(kde_ctx *ctx, int64_t N, int Ng);
+// the FP32 deposit of cell-sorted particles (uniform weight w_u, N >= 1) left as its
+// per-CTA int64 rows (workspace, valid until the next deposit on the context):
+// node g of row k is rows[k Ng + ((g - hdr[k].x) mod Ng)] when that index is below
+// hdr[k].y, else 0; fixed-point scale kde_acc_scale(bound)
+struct DepRows {
+    const long long *rows;
+    const int2 *hdr;
+    int G;
+};
+kde_status kde_deposit_rows_f32(kde_ctx *ctx, const uint32_t *u, const float *kappa, float kappa_u, const float *norm,
+                                float norm_u, int64_t N, int Ng, double coef, float w_u, double bound, DepRows *out);
+// the PIC step's field from those rows: rho_total = background + charge * rho with its
+// mean removed, E by the spectral or finite-difference Green's function (FP32 output)
+kde_status kde_field_from_rows(kde_ctx *ctx, const long long *rows, const int2 *hdr, int G, int Ng, double L,
+                               double acc_inv, double charge, double background, bool fd, float *E_out);
 
 // Poisson solve of rho_total = background + charge * rho, rho given as a real
 // array or as int64 accumulators (value = acc * acc_inv)
@@ -408,6 +433,8 @@ struct PushArgs {
     const double *kstar_in;  // CV width in force (device), or null for the uniform width
     double *kstar_out;
     double dx;
+    unsigned int *counts;    // FP32 gather: count table of the next cell sort (kde_sort_counts_table), or null
+    int cnt_nblk, cnt_shift;
 };
 template <typename T>
 kde_status kde_gather_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,

@@ -691,14 +691,11 @@ __global__ void __launch_bounds__(DEPP_RED_THREADS) deposit_rows_kernel(const lo
 
 __global__ void __launch_bounds__(DEPP_THREADS, DEPP_MINB) deposit_persist_kernel(DepSrc<float> S, DepPlan Pl)
 {
-    __shared__ __align__(16) unsigned char smraw[DEPP_SUB * 16 + DEPP_WARPS * DEPP_PART * 4];
+    __shared__ float4 rec[DEPP_SUB];
+    __shared__ float part[DEPP_WARPS * DEPP_PART];
     __shared__ float sred[2 * DEPP_WARPS];
-    __shared__ int s_es, s_last;
-    static_assert(DEPP_SUB * 16 + DEPP_WARPS * DEPP_PART * 4 >= KDE_MAX_NG * 8, "reduction buffer");
+    __shared__ int s_es;
     constexpr int PER = DEPP_SUB / DEPP_THREADS;  // particles of a sub-chunk per thread
-    float4 *rec = (float4 *)smraw;
-    float *part = (float *)(smraw + DEPP_SUB * 16);
-    long long *red = (long long *)smraw;
     const int Ng = S.Ng;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c = blockIdx.x;
@@ -875,9 +872,9 @@ kde_status kde_deposit_reserve(kde_ctx *ctx, int64_t N, int Ng)
 }
 
 template <typename T>
-kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,
-                              const T *w, T w_u, int64_t N, int Ng, double coef, long long *acc, double bound,
-                              const unsigned int *wmax_bits, double norm_bound)
+static kde_status deposit_sorted_impl(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm,
+                                      T norm_u, const T *w, T w_u, int64_t N, int Ng, double coef, long long *acc,
+                                      double bound, const unsigned int *wmax_bits, double norm_bound, DepRows *rows_out)
 {
     // the persistent FP32 kernel writes every node; the others add into zeroed accumulators
     if (!(sizeof(T) == 4 && N > 0))
@@ -920,6 +917,13 @@ kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T
             deposit_persist_kernel<<<Pl.G, DEPP_THREADS, 0, ctx->stream>>>(S, Pl);
         }
         KDE_LAUNCHED(ctx, "deposit_persist_kernel");
+        if (rows_out) {
+            // the caller sums the rows itself (the PIC step's field kernel)
+            rows_out->rows = Pl.rows;
+            rows_out->hdr = Pl.hdr;
+            rows_out->G = Pl.G;
+            return KDE_OK;
+        }
         {
             KdeProfScope _ps(ctx, PROF_DEPOSIT_ROWS);
             deposit_rows_kernel<<<(Ng + DEPP_RED_NODES - 1) / DEPP_RED_NODES, DEPP_RED_THREADS, 0, ctx->stream>>>(
@@ -935,6 +939,23 @@ kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T
         KDE_LAUNCHED(ctx, "deposit_chunk_kernel");
     }
     return KDE_OK;
+}
+
+template <typename T>
+kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,
+                              const T *w, T w_u, int64_t N, int Ng, double coef, long long *acc, double bound,
+                              const unsigned int *wmax_bits, double norm_bound)
+{
+    return deposit_sorted_impl<T>(ctx, u, kappa, kappa_u, norm, norm_u, w, w_u, N, Ng, coef, acc, bound, wmax_bits,
+                                  norm_bound, nullptr);
+}
+
+kde_status kde_deposit_rows_f32(kde_ctx *ctx, const uint32_t *u, const float *kappa, float kappa_u, const float *norm,
+                                float norm_u, int64_t N, int Ng, double coef, float w_u, double bound, DepRows *out)
+{
+    if (N < 1) return kde_fail(ctx, KDE_EINVAL, "deposit rows: need N >= 1");
+    return deposit_sorted_impl<float>(ctx, u, kappa, kappa_u, norm, norm_u, nullptr, w_u, N, Ng, coef, nullptr, bound,
+                                      nullptr, 0.0, out);
 }
 
 template <typename T>

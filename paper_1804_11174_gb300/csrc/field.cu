@@ -7,6 +7,8 @@
 // mean first keeps the FP32 sum free of cancellation).  Ng <= 4096, so the
 // whole grid lives in shared memory; each warp owns one output node, its lanes
 // take every 32nd term and a shuffle tree adds them (Ng / 8 blocks of 8 warps).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 #define POI_THREADS 256
@@ -49,6 +51,123 @@ __global__ void __launch_bounds__(POI_THREADS)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) E[j] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Field of the PIC step straight from the FP32 deposit's per-CTA rows: one
+// cluster of FIELD_C CTAs.  CTA q owns the node slice [q Ng / C, (q + 1) Ng / C):
+// its warps take the rows in turn (headers staged in shared memory), add every
+// row entry that falls in the slice into the slice's int64 sums (shared-memory
+// atomics: exact), then the CTAs read each other's slices through distributed
+// shared memory, so every CTA holds the whole charge density; the mean is removed
+// in FP64 (same order in every CTA) and each CTA solves the circular convolution
+// for its slice as poisson_kernel does.  Replaces the row reduction, the
+// accumulator round trip and the Poisson launch of the step.
+// ---------------------------------------------------------------------------
+#define FIELD_C 8
+#define FIELD_THREADS 1024
+#define FIELD_MAXG 1024
+#define FIELD_MAXS ((KDE_MAX_NG + FIELD_C - 1) / FIELD_C)
+
+__global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
+    field_rows_kernel(const long long *__restrict__ rows, const int2 *__restrict__ hdr, int G, int Ng, double acc_inv,
+                      double charge, double background, const float *__restrict__ Gf, float *E)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ int2 sh[FIELD_MAXG];
+    __shared__ long long sacc[FIELD_MAXS];
+    __shared__ float rt[KDE_MAX_NG];
+    __shared__ float gs[KDE_MAX_NG];
+    __shared__ double red[FIELD_THREADS / 32];
+    __shared__ double s_mean;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = FIELD_THREADS / 32;
+    constexpr int RB = 16;  // rows of a warp whose loads are in flight together
+    const int q = (int)cluster.block_rank();
+    const int a = (int)((int64_t)Ng * q / FIELD_C), b = (int)((int64_t)Ng * (q + 1) / FIELD_C);
+    for (int k = tid; k < G; k += FIELD_THREADS) sh[k] = hdr[k];
+    for (int g = tid; g < Ng; g += FIELD_THREADS) gs[g] = Gf[g];  // used after the row sums
+    for (int g = tid; g < b - a; g += FIELD_THREADS) sacc[g] = 0;
+    __syncthreads();
+    // rows of warp w: w, w + 32, ...; for each row the slice nodes its window covers
+    for (int k0 = warp; k0 < G; k0 += RB * NW) {
+        for (int g0 = a; g0 < b; g0 += 32) {
+            const int g = g0 + lane;
+            long long v[RB];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                const int k = k0 + i * NW;
+                v[i] = 0;
+                if (k < G && g < b) {
+                    const int2 h = sh[k];
+                    int r = g - h.x;
+                    r = r < 0 ? r + Ng : (r >= Ng ? r - Ng : r);
+                    if (r < h.y) v[i] = rows[(size_t)k * Ng + r];
+                }
+            }
+            long long t = 0;
+#pragma unroll
+            for (int i = 0; i < RB; ++i) t += v[i];
+            if (t) atomicAdd((unsigned long long *)&sacc[g - a], (unsigned long long)t);
+        }
+    }
+    cluster.sync();
+    // the whole density from every CTA's slice, the total charge density with its mean
+    // removed (FP64, the same order in every CTA)
+    auto total = [&](int g) -> double {
+        // the CTA whose slice [Ng o / C, Ng (o + 1) / C) holds node g
+        int o = (int)((int64_t)g * FIELD_C / Ng);
+        while (o > 0 && (int)((int64_t)Ng * o / FIELD_C) > g) --o;
+        while (o < FIELD_C - 1 && (int)((int64_t)Ng * (o + 1) / FIELD_C) <= g) ++o;
+        const long long *remote = cluster.map_shared_rank(sacc, o);
+        return background + charge * ((double)remote[g - (int)((int64_t)Ng * o / FIELD_C)] * acc_inv);
+    };
+    // FP64 is slow on this part: the sum runs on the warps that hold nodes, the mean on one warp
+    double local = 0.0;
+    for (int g = tid; g < Ng; g += FIELD_THREADS) local += total(g);
+    if (warp * 32 < Ng) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    }
+    if (lane == 0) red[warp] = local;
+    __syncthreads();
+    if (warp == 0) {
+        double v = red[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_mean = v / Ng;
+    }
+    __syncthreads();
+    const double mean = s_mean;
+    for (int g = tid; g < Ng; g += FIELD_THREADS) rt[g] = (float)(total(g) - mean);
+    cluster.sync();  // every remote read is done before any CTA moves on (and may exit)
+    // E_j = sum_l G[(j - l) mod Ng] rho'_l for the slice: one node a warp at a time
+    for (int j = a + warp; j < b; j += NW) {
+        float s2 = 0.f;
+        for (int l = lane; l < Ng; l += 32) {
+            const int d = j - l;
+            s2 += gs[d < 0 ? d + Ng : d] * rt[l];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) E[j] = s2;
+    }
+}
+
+kde_status kde_field_from_rows(kde_ctx *ctx, const long long *rows, const int2 *hdr, int G, int Ng, double L,
+                               double acc_inv, double charge, double background, bool fd, float *E_out)
+{
+    if (G > FIELD_MAXG) return kde_fail(ctx, KDE_ENOTSUP, "field: %d deposit rows exceed %d", G, FIELD_MAXG);
+    const float *Gf = (const float *)kde_green_table(ctx, Ng, L, fd, false);
+    if (!Gf) return KDE_ENOMEM;
+    {
+        KdeProfScope _ps(ctx, PROF_POISSON);
+        field_rows_kernel<<<FIELD_C, FIELD_THREADS, 0, ctx->stream>>>(rows, hdr, G, Ng, acc_inv, charge, background,
+                                                                       Gf, E_out);
+    }
+    KDE_LAUNCHED(ctx, "field_rows_kernel");
+    return KDE_OK;
 }
 
 template <typename T>

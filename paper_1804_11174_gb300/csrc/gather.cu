@@ -54,6 +54,10 @@ template <typename T> struct GatherArgs {
     double dx;
     unsigned int *status;
     const float2 *ntab;  // FP32 norm table (kde_norm_tab): per-particle widths without norms
+    // push only: count table of the next step's cell sort, or null (counts of the new
+    // positions are added with one atomic per warp and distinct cell)
+    unsigned int *counts;
+    int cnt_nblk, cnt_shift;
 };
 
 __device__ __forceinline__ int window_nodes_g(float kappa, int Ng, float xcut)
@@ -365,16 +369,26 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherAr
         for (int hh = 0; hh < HB; ++hh) {
             const int h = h0 + hh;
             const int64_t j = base + h * 32 + lane;
-            if (j >= A.N) continue;
-            const float v = vin[hh] + A.kick_qm_dt * (ea[h] * nm[h] * A.coef);
-            A.v_out[j] = v;
-            A.u_out[j] = advance_position(uu[h], v * A.dt_scale);
-            if (A.kappa_out) {
-                const float k = kin[hh];
-                A.kappa_out[j] = (k > 0.f && k <= (float)KDE_KAPPA_MAX) ? k : (float)KDE_KAPPA_MAX;
+            int key = -1;
+            if (j < A.N) {
+                const float v = vin[hh] + A.kick_qm_dt * (ea[h] * nm[h] * A.coef);
+                A.v_out[j] = v;
+                const uint32_t nu = advance_position(uu[h], v * A.dt_scale);
+                A.u_out[j] = nu;
+                if (A.kappa_out) {
+                    const float k = kin[hh];
+                    A.kappa_out[j] = (k > 0.f && k <= (float)KDE_KAPPA_MAX) ? k : (float)KDE_KAPPA_MAX;
+                }
+                if (A.norm_out) A.norm_out[j] = nin[hh];
+                if (A.id_out) A.id_out[j] = idin[hh];
+                key = kde_cell(nu, Ng);
             }
-            if (A.norm_out) A.norm_out[j] = nin[hh];
-            if (A.id_out) A.id_out[j] = idin[hh];
+            if (A.counts) {  // warp-uniform; the 32 particles of a round share one sort tile
+                const unsigned int peers = __match_any_sync(0xffffffffu, key);
+                if (key >= 0 && lane == __ffs(peers) - 1)
+                    atomicAdd(&A.counts[(size_t)key * A.cnt_nblk + (size_t)(j >> A.cnt_shift)],
+                              (unsigned int)__popc(peers));
+            }
         }
         }
     } else {
@@ -411,14 +425,14 @@ static kde_status gat2_launch(kde_ctx *ctx, const GatherArgs<float> &A)
 
 static kde_status gat2_variant(kde_ctx *ctx, const GatherArgs<float> &A, int v)
 {
-    // all with eight particles a lane (a block of four warps takes 1024 consecutive
-    // particles, so a Landau-size run of 2^20 particles is one wave of 1024 blocks):
-    // the warps' particle sets, and so their node windows and kernel forms, are the
-    // same in every variant
+    // all with four particles a lane: the warps' particle sets, and so their node windows
+    // and kernel forms, are the same in every variant.  (Eight particles a lane, which
+    // makes a Landau-size run one wave, measured 10% slower: the 64-register bound leaves
+    // the node loop less room.)
     switch (v) {
-    case 1: return gat2_launch<8, 4, 4, 6>(ctx, A);
-    case 2: return gat2_launch<8, 8, 4, 4>(ctx, A);
-    default: return gat2_launch<8, 4, 4, 8>(ctx, A);
+    case 1: return gat2_launch<4, 4, 4, 8>(ctx, A);
+    case 2: return gat2_launch<4, 8, 4, 6>(ctx, A);
+    default: return gat2_launch<4, 8, 4, 5>(ctx, A);
     }
 }
 
@@ -467,9 +481,13 @@ static kde_status launch_gather2(kde_ctx *ctx, GatherArgs<float> &A)
     cudaEvent_t ev[2 * GAT2_NVARIANTS + 1];
     for (auto &e : ev) KDE_CUDA(ctx, cudaEventCreate(&e), "autotune event");
     KDE_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream), "autotune event");
+    // the timed runs add no sort counts (they repeat the gather); the chosen shape runs
+    // once more below with the caller's arguments
+    GatherArgs<float> T = A;
+    T.counts = nullptr;
     for (int r = 0; r < 2; ++r)
         for (int k = 0; k < GAT2_NVARIANTS; ++k) {
-            KDE_TRY(gat2_variant(ctx, A, k));
+            KDE_TRY(gat2_variant(ctx, T, k));
             KDE_CUDA(ctx, cudaEventRecord(ev[1 + r * GAT2_NVARIANTS + k], ctx->stream), "autotune event");
         }
     KDE_CUDA(ctx, cudaEventSynchronize(ev[2 * GAT2_NVARIANTS]), "autotune wait");
@@ -484,6 +502,10 @@ static kde_status launch_gather2(kde_ctx *ctx, GatherArgs<float> &A)
     }
     for (auto &e : ev) cudaEventDestroy(e);
     ctx->gat2_tuned[key] = v;
+    if (A.counts) {
+        KdeProfScope _ps(ctx, PROF_GATHER);
+        return gat2_variant(ctx, A, v);
+    }
     return KDE_OK;
 }
 
@@ -543,6 +565,9 @@ kde_status kde_gather_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T 
         A.kstar_in = push->kstar_in;
         A.kstar_out = push->kstar_out;
         A.dx = push->dx;
+        A.counts = push->counts;
+        A.cnt_nblk = push->cnt_nblk;
+        A.cnt_shift = push->cnt_shift;
     }
     if constexpr (sizeof(T) == 4) return launch_gather2(ctx, A);
     else return launch_gather<T>(ctx, A);

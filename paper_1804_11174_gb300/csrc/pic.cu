@@ -102,10 +102,14 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
     }
     const double coef = KDE_TWO_PI / L;
     const double w_u = L / (double)N;
+    // the FP32 gather + push adds the next step's sort counts; a step whose table was
+    // overwritten since (first step of the call, CV or AD sorts) counts afresh
+    bool counted = false;
     for (int s = 0; s < n_steps; ++s) {
         const int64_t step = st->step;
         const bool update = sched && step % st->width_every == 0;
         if (update) {
+            counted = false;  // the CV's own sort reuses the count table
             KdeRange r_("kdepic width update (CV + Silverman)");
             if (cv_spec)
                 KDE_TRY(kde_cv_spectral_device(ctx, st->u, N, L, st->cand, st->n_cand, cv_dev, amin_dev, loo, ks_dev));
@@ -117,6 +121,7 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
             if (!fetch_ws()) return KDE_ENOMEM;
         }
         if (adsched) {
+            counted = false;  // the AD test's radix sort reuses the count table
             KdeRange r_("kdepic Anderson-Darling schedule");
             KDE_TRY(kde_ad_device(ctx, st->u, N, ad_out, st->ad_log_p ? st->ad_log_p + step : nullptr));
             double ad_h[2];
@@ -160,21 +165,36 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
         if (st->id) pl[npl++] = SortPayload{st->id, ids, 4};
         {
             KdeRange r_("kdepic sort by cell");
-            KDE_TRY(kde_sort_by_bin(ctx, st->u, N, Ng, us, pl, npl, nullptr));
+            KDE_TRY(kde_sort_by_bin(ctx, st->u, N, Ng, us, pl, npl, nullptr, counted));
         }
 
         const double norm_u = per ? 0.0 : kde_norm(st->kappa_uniform);
         const double norm_bound = per ? kde_norm(KDE_KAPPA_MAX) : norm_u;
         const double bound = (double)N * w_u * coef * norm_bound;
-        {
-            KdeRange r_("kdepic deposit");
-            KDE_TRY(kde_deposit_sorted<T>(ctx, us, ks, (T)st->kappa_uniform, ns, (T)norm_u, nullptr, (T)w_u, N, Ng,
-                                          coef, acc, bound, nullptr, norm_bound));
-        }
-        {
-            KdeRange r_("kdepic Poisson");
-            KDE_TRY(kde_poisson_impl<T>(ctx, nullptr, acc, 1.0 / kde_acc_scale(bound), Ng, L, st->charge,
-                                        st->background, fd, E));
+        if constexpr (sizeof(T) == 4) {
+            // FP32: per-CTA rows, summed inside the field kernel (no accumulator round trip)
+            DepRows dr{};
+            {
+                KdeRange r_("kdepic deposit");
+                KDE_TRY(kde_deposit_rows_f32(ctx, us, ks, (float)st->kappa_uniform, ns, (float)norm_u, N, Ng, coef,
+                                             (float)w_u, bound, &dr));
+            }
+            {
+                KdeRange r_("kdepic field (row sums + Poisson)");
+                KDE_TRY(kde_field_from_rows(ctx, dr.rows, dr.hdr, dr.G, Ng, L, 1.0 / kde_acc_scale(bound), st->charge,
+                                            st->background, fd, (float *)E));
+            }
+        } else {
+            {
+                KdeRange r_("kdepic deposit");
+                KDE_TRY(kde_deposit_sorted<T>(ctx, us, ks, (T)st->kappa_uniform, ns, (T)norm_u, nullptr, (T)w_u, N,
+                                              Ng, coef, acc, bound, nullptr, norm_bound));
+            }
+            {
+                KdeRange r_("kdepic Poisson");
+                KDE_TRY(kde_poisson_impl<T>(ctx, nullptr, acc, 1.0 / kde_acc_scale(bound), Ng, L, st->charge,
+                                            st->background, fd, E));
+            }
         }
 
         PushArgs pa{};
@@ -197,11 +217,19 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
                              : (sched && st->kappa_star && step > 0 ? st->kappa_star + step - 1 : (sched ? ks_dev : nullptr));
         pa.kstar_out = st->kappa_star ? st->kappa_star + step : nullptr;
         pa.dx = L / Ng;
+        SortCounts sc{};
+        if constexpr (sizeof(T) == 4) {
+            KDE_TRY(kde_sort_counts_table(ctx, N, Ng, &sc));
+            pa.counts = sc.counts;
+            pa.cnt_nblk = sc.nblk;
+            pa.cnt_shift = sc.tile_shift;
+        }
         {
             KdeRange r_("kdepic gather + push");
             KDE_TRY(kde_gather_sorted<T>(ctx, us, ks, (T)st->kappa_uniform, ns, (T)norm_u, N, E, Ng,
                                          KDE_TWO_PI / Ng, nullptr, nullptr, &pa));
         }
+        counted = pa.counts != nullptr;
         st->step = step + 1;
     }
     return KDE_OK;

@@ -6,16 +6,17 @@
 //             warp are added once, by their leader) -> counts[bin][block]
 //             (bin-major, so that the destination order of the tiles' segments is
 //             the flat index bin * nblocks + block)
-//   scan    : exclusive scan of the flat counts array in one kernel: tiles of 2048
-//             scanned in place, then the block that finishes last (a ticket in the
-//             context's status words, put back to zero) scans the tile totals.  A
-//             context's calls must not overlap on the GPU (they share the ticket as
-//             they share the workspace).
+//   scan    : exclusive scan of each 2048-entry tile of the flat counts array in place,
+//             plus the tile totals; every scatter block scans the (few) tile totals
+//             itself, so no block waits for another.
 //   scatter : each warp histograms its unit in shared memory, the block turns the
 //             warps' histograms into destination starts (its segment start plus the
-//             counts of the earlier warps), then every warp ranks equal keys in each
-//             32-particle step with __match_any_sync and writes every particle
-//             (position and payloads) to its start + rank.
+//             counts of the earlier warps) and zeroes the count entries it consumed,
+//             then every warp ranks equal keys in each 32-particle step with
+//             __match_any_sync and writes every particle (position and payloads) to
+//             its start + rank.
+// In the PIC step the count pass is skipped when the previous step's gather + push
+// kernel has already added the new positions' counts into the (zeroed) table.
 // The order inside a bin is the input order (stable), so results are
 // deterministic.  The count table has one entry per (bin, block) rather than per
 // (bin, warp), so it stays small next to the particle data.
@@ -74,15 +75,13 @@ __global__ void sort_count_kernel(const uint32_t *__restrict__ u, int64_t N, int
 }
 
 // exclusive scan of each SCAN_TILE-element tile in place (coalesced rounds of
-// SCAN_THREADS elements, all loads issued first); the tile totals go to tot, and the
-// block that finishes last (a ticket taken after a fence) scans them in place and
-// puts the ticket back to zero
+// SCAN_THREADS elements, all loads issued first); the tile totals go to tot.  The
+// scatter scans the (few) tile totals itself, so no block waits for another.
 __global__ void __launch_bounds__(SCAN_THREADS) sort_scan_kernel(unsigned int *a, int64_t n, unsigned int *tot,
-                                                                 unsigned int *ticket)
+                                                                 unsigned int *zero_out)
 {
     constexpr int R = SCAN_TILE / SCAN_THREADS;
     __shared__ unsigned int wsum[SCAN_THREADS / 32];
-    __shared__ bool last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // block-wide exclusive scan of one value a thread; returns the prefix, adds the total to carry
     auto block_scan = [&](unsigned int v, unsigned int &carry) -> unsigned int {
@@ -119,23 +118,15 @@ __global__ void __launch_bounds__(SCAN_THREADS) sort_scan_kernel(unsigned int *a
         const unsigned int x = block_scan(v[r], carry);
         if (i < n) a[i] = x;
     }
-    if (tid == 0) {
-        tot[blockIdx.x] = carry;
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (tid == 0) tot[blockIdx.x] = carry;
+    // the next step's count table (added to by the PIC gather) starts from zero
+    if (zero_out) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t i = t0 + (int64_t)r * SCAN_THREADS + tid;
+            if (i < n) zero_out[i] = 0u;
+        }
     }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    const int nt = (int)gridDim.x;
-    unsigned int c2 = 0;
-    for (int r0 = 0; r0 < nt; r0 += SCAN_THREADS) {
-        const int i = r0 + tid;
-        const unsigned int x = i < nt ? ((volatile unsigned int *)tot)[i] : 0u;
-        const unsigned int y = block_scan(x, c2);
-        if (i < nt) tot[i] = y;
-    }
-    if (tid == 0) *ticket = 0u;
 }
 
 struct ScatterPl {
@@ -150,14 +141,30 @@ struct ScatterPl {
 template <bool DIGIT, int NPL>
 __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int shift, int unit,
                                     int nblk, const unsigned int *__restrict__ seg,
-                                    const unsigned int *__restrict__ tiles, uint32_t *u_out, ScatterPl pl,
+                                    const unsigned int *__restrict__ tot, int ntiles, uint32_t *u_out, ScatterPl pl,
                                     uint32_t *perm_out)
 {
     extern __shared__ unsigned int hist[];
     const int wpb = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned int *h = hist + (size_t)warp * nbins;
+    unsigned int *tpre = hist + (size_t)wpb * nbins;  // exclusive prefix of the scan's tile totals
     for (int b = threadIdx.x; b < wpb * nbins; b += blockDim.x) hist[b] = 0;
+    // the tile totals' exclusive prefix, by warp 0 (a few hundred values at most)
+    if (warp == 0) {
+        unsigned int carry = 0;
+        for (int t0 = 0; t0 < ntiles; t0 += 32) {
+            const unsigned int x = t0 + lane < ntiles ? tot[t0 + lane] : 0u;
+            unsigned int inc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (t0 + lane < ntiles) tpre[t0 + lane] = carry + inc - x;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+    }
     __syncthreads();
     const int64_t i0 = ((int64_t)blockIdx.x * wpb + warp) * unit;
     const int64_t i1 = i0 + unit < N ? i0 + unit : N;  // empty when i0 >= N
@@ -180,10 +187,12 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
         }
     }
     __syncthreads();
-    // destination starts: the block's segment start of each bin plus the earlier warps' counts
+    // destination starts: the block's segment start of each bin plus the earlier warps'
+    // counts; the consumed count entry is put back to zero (the PIC step's gather adds the
+    // next step's counts into a zeroed table)
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
         const size_t flat = (size_t)b * nblk + blockIdx.x;
-        unsigned int run = seg[flat] + tiles[flat / SCAN_TILE];
+        unsigned int run = seg[flat] + tpre[flat / SCAN_TILE];
         for (int w = 0; w < wpb; ++w) {
             const unsigned int t = hist[(size_t)w * nbins + b];
             hist[(size_t)w * nbins + b] = run;
@@ -223,8 +232,9 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
             __syncwarp();
             if (valid && rank == 0) h[key] = before + __popc(peers);
             __syncwarp();
+            // a count table that disagreed with the keys could not send a write past the arrays
+            const unsigned int dst = min(before + rank, (unsigned int)(N - 1));
             if (valid) {
-                const unsigned int dst = before + rank;
                 u_out[dst] = uu[r];
 #pragma unroll
                 for (int k = 0; k < NPL; ++k) {
@@ -240,25 +250,68 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
 template <bool DIGIT, int NPL>
 static void set_scatter_attr(kde_ctx *ctx)
 {
-    cudaFuncSetAttribute(sort_scatter_kernel<DIGIT, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(sort_scatter_kernel<DIGIT, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+}
+
+// tile geometry of a sort of N keys into nbins bins: wpb warps of `unit` keys a block
+static void sort_geometry(int64_t N, int nbins, int &wpb, int &unit, int &nblk)
+{
+    // warps per block: the scatter's warp-private histograms must fit the shared-memory budget
+    wpb = 8;
+    while (wpb > 1 && (size_t)wpb * nbins * 4 > 96 * 1024) wpb >>= 1;
+    unit = 256;
+    while ((int64_t)nbins * ((N + (int64_t)wpb * unit - 1) / ((int64_t)wpb * unit)) > SORT_MAX_COUNTS) unit *= 2;
+    nblk = (int)((N + (int64_t)wpb * unit - 1) / ((int64_t)wpb * unit));
+}
+
+// the two count tables of the PIC step (one consumed by this step's sort while the
+// gather adds the next step's into the other), in one workspace slot
+static unsigned int *count_tables(kde_ctx *ctx, int64_t ncounts)
+{
+    return (unsigned int *)kde_ws(ctx, WS_SORT_COUNTS, (size_t)ncounts * 8);
+}
+
+kde_status kde_sort_counts_table(kde_ctx *ctx, int64_t N, int nbins, SortCounts *out)
+{
+    int wpb, unit, nblk;
+    sort_geometry(N, nbins, wpb, unit, nblk);
+    int sh = 0;
+    while ((1LL << sh) < (int64_t)wpb * unit) ++sh;
+    const int64_t ncounts = (int64_t)nbins * nblk;
+    unsigned int *counts = count_tables(ctx, ncounts);
+    if (!counts) return KDE_ENOMEM;
+    out->counts = counts + (ctx->count_flip ? ncounts : 0);  // the table the next sort reads
+    out->nblk = nblk;
+    out->tile_shift = sh;
+    return KDE_OK;
 }
 
 template <bool DIGIT>
 static kde_status sort_pass(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, int shift, uint32_t *u_out,
-                            const SortPayload *pl, int npl, uint32_t *perm_out)
+                            const SortPayload *pl, int npl, uint32_t *perm_out, bool counted = false)
 {
-    // warps per block: the scatter's warp-private histograms must fit the shared-memory budget
-    int wpb = 8;
-    while (wpb > 1 && (size_t)wpb * nbins * 4 > 96 * 1024) wpb >>= 1;
-    int unit = 256;
-    while ((int64_t)nbins * ((N + (int64_t)wpb * unit - 1) / ((int64_t)wpb * unit)) > SORT_MAX_COUNTS) unit *= 2;
-    const int nblk = (int)((N + (int64_t)wpb * unit - 1) / ((int64_t)wpb * unit));
+    int wpb, unit, nblk;
+    sort_geometry(N, nbins, wpb, unit, nblk);
     const int64_t ncounts = (int64_t)nbins * nblk;
     const int ntiles = (int)((ncounts + SCAN_TILE - 1) / SCAN_TILE);
-    unsigned int *counts = (unsigned int *)kde_ws(ctx, WS_SORT_COUNTS, (size_t)ncounts * 4);
+    unsigned int *tables = count_tables(ctx, ncounts);
     unsigned int *tiles = (unsigned int *)kde_ws(ctx, WS_SORT_STARTS, (size_t)ntiles * 4);
-    if (!counts || !tiles) return KDE_ENOMEM;
-    const size_t smem = (size_t)wpb * nbins * 4;
+    if (!tables || !tiles) return KDE_ENOMEM;
+    // a counted sort reads the table the gather filled and zeroes the other for the next
+    // step; an uncounted one counts into the first table and zeroes the second.
+    // count_flip names the table the next counted sort reads (false: first, true: second)
+    unsigned int *const t0 = tables, *const t1 = tables + ncounts;
+    unsigned int *counts, *other;
+    if (counted) {
+        counts = ctx->count_flip ? t1 : t0;
+        other = ctx->count_flip ? t0 : t1;
+        ctx->count_flip = !ctx->count_flip;
+    } else {
+        counts = t0;
+        other = t1;
+        ctx->count_flip = true;  // the gather that follows adds into the second table
+    }
+    const size_t smem = (size_t)wpb * nbins * 4 + (size_t)ntiles * 4;
     static bool attr_set = false;
     if (!attr_set) {
         KDE_CUDA(ctx,
@@ -272,11 +325,14 @@ static kde_status sort_pass(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbin
         KDE_CUDA(ctx, cudaGetLastError(), "sort attribute");
         attr_set = true;
     }
+    if (smem > 100 * 1024) return kde_fail(ctx, KDE_ENOTSUP, "sort: %d tiles of counts exceed shared memory", ntiles);
     KdeProfScope _ps(ctx, PROF_SORT);  // the whole pass: count, scan and scatter
-    sort_count_kernel<DIGIT><<<nblk, wpb * 32, (size_t)nbins * 4, ctx->stream>>>(u, N, nbins, shift, unit, nblk,
-                                                                                counts);
-    KDE_LAUNCHED(ctx, "sort_count_kernel");
-    sort_scan_kernel<<<ntiles, SCAN_THREADS, 0, ctx->stream>>>(counts, ncounts, tiles, ctx->d_status + 2);
+    if (!counted) {
+        sort_count_kernel<DIGIT><<<nblk, wpb * 32, (size_t)nbins * 4, ctx->stream>>>(u, N, nbins, shift, unit, nblk,
+                                                                                    counts);
+        KDE_LAUNCHED(ctx, "sort_count_kernel");
+    }
+    sort_scan_kernel<<<ntiles, SCAN_THREADS, 0, ctx->stream>>>(counts, ncounts, tiles, DIGIT ? nullptr : other);
     KDE_LAUNCHED(ctx, "sort_scan_kernel");
     ScatterPl sp{};
     sp.n = npl;
@@ -287,27 +343,27 @@ static kde_status sort_pass(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbin
     }
     switch (npl) {
     case 0: sort_scatter_kernel<DIGIT, 0><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                tiles, u_out, sp, perm_out); break;
+                                                                                tiles, ntiles, u_out, sp, perm_out); break;
     case 1: sort_scatter_kernel<DIGIT, 1><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                tiles, u_out, sp, perm_out); break;
+                                                                                tiles, ntiles, u_out, sp, perm_out); break;
     case 2: sort_scatter_kernel<DIGIT, 2><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                tiles, u_out, sp, perm_out); break;
+                                                                                tiles, ntiles, u_out, sp, perm_out); break;
     case 3: sort_scatter_kernel<DIGIT, 3><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                tiles, u_out, sp, perm_out); break;
+                                                                                tiles, ntiles, u_out, sp, perm_out); break;
     default: sort_scatter_kernel<DIGIT, 4><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                 tiles, u_out, sp, perm_out); break;
+                                                                                 tiles, ntiles, u_out, sp, perm_out); break;
     }
     KDE_LAUNCHED(ctx, "sort_scatter_kernel");
     return KDE_OK;
 }
 
 kde_status kde_sort_by_bin(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbins, uint32_t *u_out,
-                           const SortPayload *pl, int npl, uint32_t *perm_out)
+                           const SortPayload *pl, int npl, uint32_t *perm_out, bool counted)
 {
     if (N <= 0) return KDE_OK;
     if (nbins < 1 || nbins > 8192 || npl > 4 || N > 0xFFFFFFFFll)
         return kde_fail(ctx, KDE_EINVAL, "sort: unsupported sizes");
-    return sort_pass<false>(ctx, u, N, nbins, 0, u_out, pl, npl, perm_out);
+    return sort_pass<false>(ctx, u, N, nbins, 0, u_out, pl, npl, perm_out, counted);
 }
 
 kde_status kde_radix_sort_u32(kde_ctx *ctx, const uint32_t *u, int64_t N, uint32_t *out, uint32_t *tmp)
