@@ -273,7 +273,7 @@ def run_ours(args, rank, world, local_rank):
     ctx.reserve(N, Ng, w["n_cand"])
     ctx.set_autotune(not args.no_autotune)  # gather tile shape tuned in the first warm-up step
     # each rank simulates its own realisation (independent replicas, weak scaling)
-    st, u0, v0, cand = landau_state(kp, dev, w, w["seed"] + rank, P * (args.warmup + args.steps + 1),
+    st, u0, v0, cand = landau_state(kp, dev, w, w["seed"] + rank, P * (args.warmup + 2 * args.steps + 1),
                                     cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
     for _ in range(args.warmup):
@@ -286,7 +286,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    ctx.profile_enable(True)
+    ctx.profile_enable(False)  # no events between the kernels (they would serialise the launch overlap);
+    #                            this also zeroes the launch counter
     wall0 = time.perf_counter()
     step_ms, pairs = [], []
     for _ in range(args.steps):
@@ -296,9 +297,13 @@ def run_ours(args, rank, world, local_rank):
         pairs.append(2.0 * P * grid_window_pairs(st.kappa.cpu().numpy(), Ng))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    _, launches = ctx.profile_read("all")
+    # per-kernel durations: CUDA events around every kernel over the same number of
+    # periods, run right after the timed ones on the same state
+    ctx.profile_enable(True)
+    prof_ms = timed(lambda: ctx.pic_step(st, P), flush, args.steps)
     prof = {k: ctx.profile_read(k) for k in ("deposit", "gather", "sort", "poisson", "spectral", "cv_pairs",
                                               "cv_grid", "cv_loo")}
-    _, launches = ctx.profile_read("all")
     ctx.profile_enable(False)
     clk = clocks.stop()
     if dist:
@@ -314,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- e2e: the same period through the C ABI from pinned host buffers (pic_step_host:
     #      host -> device copies of u, v, kappa, id, the period, copies back, inside the call) ----
-    st_h, _, _, _ = landau_state(kp, dev, w, w["seed"] + rank, P * (args.warmup + args.steps + 1),
+    st_h, _, _, _ = landau_state(kp, dev, w, w["seed"] + rank, P * (args.warmup + 2 * args.steps + 1),
                                  cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
     host = kp.PicState(st_h.u.cpu().pin_memory(), st_h.v.cpu().pin_memory(), L, Ng, dt,
                        kappa=st_h.kappa.cpu().pin_memory(), ids=st_h.id.cpu().pin_memory(), width_every=P,
@@ -351,13 +356,15 @@ def run_ours(args, rank, world, local_rank):
     s_ms, s_n = prof["sort"]
     hbm = measured_peaks().get("hbm_gbs") or 6773.2
     if s_n:
-        sort_bytes = N * (4 + 20 + 20)
+        ncounts = Ng * -(-N // 2048)  # (bin, tile) count entries: tiles of 2048 particles
+        sort_bytes = N * (20 + 20) + 12 * ncounts
         ach_s = sort_bytes / (s_ms / s_n * 1e-3) / 1e9
-        kr["sort_count+scan+scatter"] = {
+        kr["sort_scan+scatter"] = {
             "bound": "hbm", "achieved": ach_s, "peak": hbm, "unit": "GB/s", "frac": ach_s / hbm,
             "algorithmic_bytes_per_launch": sort_bytes, "avg_launch_ms": s_ms / s_n, "launches": s_n,
-            "unit_def": "per particle: 4 B code read by the count pass, 20 B read and 20 B written by the "
-                        "scatter (u, v, kappa, norm, id)"}
+            "unit_def": "per particle 20 B read and 20 B written by the scatter (u, v, kappa, norm, id); per "
+                        "(bin, tile) count entry 12 B (the scan's read and write, and the zeroing of the other "
+                        "table); the counts themselves are added by the gather + push of the step before"}
     dom = max(("deposit_persist_kernel", "gather2_kernel"),
               key=lambda k: kr[k]["avg_launch_ms"] * kr[k]["launches"] if k in kr else -1.0)
     roof = dict(kr.get(dom, {}), kernel=dom, traffic=PROFILED_TRAFFIC.get(dom),
@@ -405,6 +412,9 @@ def run_ours(args, rank, world, local_rank):
                    "gather_tile_shape": "default" if args.no_autotune else "autotuned"},
         "pairs_per_step": pairs_period,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "kernel_timing": "CUDA events around each kernel on the library's stream over %d further periods "
+                         "right after the timed ones (%.3f ms a period with the events, which serialise the "
+                         "launch overlap)" % (args.steps, float(np.mean(prof_ms))),
         "wall_s": wall,
         "clocks": clk,
         "e2e": e2e,

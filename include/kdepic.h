@@ -107,6 +107,16 @@ kde_status kde_sync(kde_ctx *ctx);
 kde_status kde_set_autotune(kde_ctx *ctx, int32_t enable);
 kde_status kde_autotune_entries(const kde_ctx *ctx, int32_t *n_out);
 
+/* Launch overlap (no counterpart in the paper: a speed facility of this library).
+ * With enable != 0 (the default) the kernels of the FP32 step chain -- the sort's scan
+ * and scatter, the deposit, the field kernel and the gather with push -- are launched
+ * as programmatic dependents: each may begin its independent prologue (loading its own
+ * particles, building node tables) while the kernel before it in the stream finishes,
+ * and waits on the device for that kernel's results before it reads them or writes
+ * anything.  Results are bitwise identical with the setting on or off.  Launches that
+ * follow a profiling event or another stream's work are ordered as usual. */
+kde_status kde_set_launch_overlap(kde_ctx *ctx, int32_t enable);
+
 /* Limit of the bounded device-side waits (no counterpart in the paper: a
  * robustness facility of this library).  The CV kernels stage column tiles with
  * bulk copies and wait for each on an mbarrier; a wait that has not seen its copy

@@ -123,6 +123,7 @@ def load_library(path: str | None = None):
         "kde_server_destroy": (S, [_P]),
         "kde_profile_read": (S, [_P, ctypes.c_int, _P, _P]),
         "kde_set_autotune": (S, [_P, ctypes.c_int32]),
+        "kde_set_launch_overlap": (S, [_P, ctypes.c_int32]),
         "kde_set_wait_limit": (S, [_P, _I64]),
         "kde_autotune_entries": (S, [_P, _P]),
     }
@@ -321,6 +322,10 @@ class Context:
     def set_autotune(self, on: bool = True):
         """kde_set_autotune: tune the FP32 gather's tile shape per key on first use."""
         self._check("kde_set_autotune", self.lib.kde_set_autotune(self.h, int(on)))
+
+    def set_launch_overlap(self, on: bool = True):
+        """kde_set_launch_overlap: programmatic dependent launches in the FP32 step chain."""
+        self._check("kde_set_launch_overlap", self.lib.kde_set_launch_overlap(self.h, int(on)))
 
     def autotune_entries(self) -> int:
         """kde_autotune_entries: number of keys tuned so far."""

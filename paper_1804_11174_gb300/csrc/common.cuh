@@ -122,6 +122,7 @@ struct kde_ctx {
     unsigned wait_polls = 1u << 26;         // polls of a bounded device wait (kde_set_wait_limit)
     bool count_flip = false;                // which sort count table the next counted sort reads (sort.cu)
     bool autotune = false;                  // kde_set_autotune
+    bool overlap = true;                    // kde_set_launch_overlap: PDL launches in the step chain
     std::map<uint64_t, int> gat2_tuned;     // packed-gather tile shape per key (gather.cu)
     void *sp_atab = nullptr;                // workspace holding the Bessel ratios of sp_atab_cands (spectral.cu)
     std::vector<double> sp_atab_cands;
@@ -152,6 +153,25 @@ double kde_host_i0e(double x);  // scaled Bessel I0e in FP64 on the host (unifor
         ++(ctx)->launches;                             \
         KDE_CUDA(ctx, cudaGetLastError(), what);       \
     } while (0)
+
+// launch on the context's stream; with `pdl` and the context's overlap setting on, the
+// kernel may begin while the previous kernel in the stream runs (see kde_pdl_wait)
+template <typename... KArgs, typename... Args>
+inline cudaError_t kde_launch(kde_ctx *ctx, bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = (pdl && ctx->overlap) ? 1u : 0u;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 // profiling hook: when enabled, records an event pair around a launch on the
 // context's stream
@@ -260,6 +280,20 @@ __device__ __forceinline__ void kde_flag(unsigned int *status, unsigned code, un
 {
     if (status && atomicCAS(status, 0u, code) == 0u) status[1] = detail;
 }
+
+// Programmatic dependent launch.  A kernel launched by kde_launch with overlap on may
+// start while the kernel before it in the stream is still running.  Every kernel so
+// launched keeps two rules:
+//  * every CTA executes kde_pdl_wait() before it reads anything the previous kernel
+//    writes, before its first global write (the device status word, which only ever
+//    goes from zero to an error code, excepted) and before it exits; the wait returns
+//    once the previous grid has completed and its writes are visible (at once without
+//    PDL);
+//  * kde_pdl_trigger(), which lets the next kernel start, comes after kde_pdl_wait().
+// So when a kernel starts, the kernel two places before it has completed, and data
+// written two or more kernels back may be read before the wait.
+__device__ __forceinline__ void kde_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void kde_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // half-angle sine and cosine of the position code: theta / 2 = pi u / 2^32.
 // FP32: the code is split as u = hi 2^16 + lo so that both arguments of

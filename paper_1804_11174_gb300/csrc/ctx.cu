@@ -247,6 +247,13 @@ extern "C" kde_status kde_set_autotune(kde_ctx *ctx, int32_t enable)
     return KDE_OK;
 }
 
+extern "C" kde_status kde_set_launch_overlap(kde_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return KDE_EINVAL;
+    ctx->overlap = enable != 0;
+    return KDE_OK;
+}
+
 extern "C" kde_status kde_set_wait_limit(kde_ctx *ctx, int64_t polls)
 {
     if (!ctx) return KDE_EINVAL;

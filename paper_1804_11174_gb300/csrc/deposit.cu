@@ -700,6 +700,8 @@ __global__ void __launch_bounds__(DEPP_THREADS, DEPP_MINB) deposit_persist_kerne
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c = blockIdx.x;
     const int64_t i0 = S.N * c / Pl.G, i1 = S.N * (c + 1) / Pl.G;  // non-empty: G <= N
+    kde_pdl_wait();  // everything read below comes from the sort before
+    kde_pdl_trigger();
 
     // smallest and largest width of the CTA's particles (the window and the form): a pass
     // over the widths, PER loads in flight per thread
@@ -914,7 +916,8 @@ static kde_status deposit_sorted_impl(kde_ctx *ctx, const uint32_t *u, const T *
         KDE_TRY(depp_plan(ctx, N, Ng, acc, Pl));
         {
             KdeProfScope _ps(ctx, PROF_DEPOSIT);
-            deposit_persist_kernel<<<Pl.G, DEPP_THREADS, 0, ctx->stream>>>(S, Pl);
+            KDE_CUDA(ctx, kde_launch(ctx, true, deposit_persist_kernel, dim3(Pl.G), dim3(DEPP_THREADS), 0, S, Pl),
+                     "deposit_persist_kernel");
         }
         KDE_LAUNCHED(ctx, "deposit_persist_kernel");
         if (rows_out) {

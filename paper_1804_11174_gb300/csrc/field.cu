@@ -86,6 +86,8 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
     constexpr int RB = 16;  // rows of a warp whose loads are in flight together
     const int q = (int)cluster.block_rank();
     const int a = (int)((int64_t)Ng * q / FIELD_C), b = (int)((int64_t)Ng * (q + 1) / FIELD_C);
+    kde_pdl_wait();  // the rows come from the deposit before
+    kde_pdl_trigger();
     for (int k = tid; k < G; k += FIELD_THREADS) sh[k] = hdr[k];
     for (int g = tid; g < Ng; g += FIELD_THREADS) gs[g] = Gf[g];  // used after the row sums
     for (int g = tid; g < b - a; g += FIELD_THREADS) sacc[g] = 0;
@@ -163,8 +165,9 @@ kde_status kde_field_from_rows(kde_ctx *ctx, const long long *rows, const int2 *
     if (!Gf) return KDE_ENOMEM;
     {
         KdeProfScope _ps(ctx, PROF_POISSON);
-        field_rows_kernel<<<FIELD_C, FIELD_THREADS, 0, ctx->stream>>>(rows, hdr, G, Ng, acc_inv, charge, background,
-                                                                       Gf, E_out);
+        KDE_CUDA(ctx, kde_launch(ctx, true, field_rows_kernel, dim3(FIELD_C), dim3(FIELD_THREADS), 0, rows, hdr, G, Ng,
+                                 acc_inv, charge, background, Gf, E_out),
+                 "field_rows_kernel");
     }
     KDE_LAUNCHED(ctx, "field_rows_kernel");
     return KDE_OK;

@@ -278,6 +278,12 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherAr
         } else {
             SC[g] = make_float4(sc.x, sc.x, -sc.y, -sc.y);
         }
+    }
+    // the field is the previous kernel's output; so far only the sorted particles (two or
+    // more kernels back) and the node table have been read
+    kde_pdl_wait();
+    kde_pdl_trigger();
+    for (int g = threadIdx.x; g < Ng; g += GAT2_WARPS * 32) {
         const float f = A.field[g];
         FF[g] = make_float2(f, f);
     }
@@ -418,7 +424,11 @@ static kde_status gat2_launch(kde_ctx *ctx, const GatherArgs<float> &A)
     const size_t smem = (size_t)A.Ng * (sizeof(float4) + sizeof(float2));
     unsigned grid = (unsigned)((A.N + GAT2_WARPS * 32 * NP - 1) / (GAT2_WARPS * 32 * NP));
     if (grid == 0) grid = 1;
-    kern<<<grid, GAT2_WARPS * 32, smem, ctx->stream>>>(A);
+    // with the push (the PIC step) the kernel before is the field kernel, which writes
+    // none of the sorted particle arrays the prologue reads before its wait; a plain
+    // gather may follow the sort that wrote them, so it starts after it as usual
+    KDE_CUDA(ctx, kde_launch(ctx, A.u_out != nullptr, kern, dim3(grid), dim3(GAT2_WARPS * 32), smem, A),
+             "gather2_kernel");
     KDE_LAUNCHED(ctx, "gather2_kernel");
     return KDE_OK;
 }

@@ -7,16 +7,18 @@
 //             (bin-major, so that the destination order of the tiles' segments is
 //             the flat index bin * nblocks + block)
 //   scan    : exclusive scan of each 2048-entry tile of the flat counts array in place,
-//             plus the tile totals; every scatter block scans the (few) tile totals
-//             itself, so no block waits for another.
+//             plus the tile totals, and zeroing of the second count table; every
+//             scatter block scans the (few) tile totals itself, so no block waits for
+//             another.
 //   scatter : each warp histograms its unit in shared memory, the block turns the
 //             warps' histograms into destination starts (its segment start plus the
-//             counts of the earlier warps) and zeroes the count entries it consumed,
-//             then every warp ranks equal keys in each 32-particle step with
-//             __match_any_sync and writes every particle (position and payloads) to
-//             its start + rank.
+//             counts of the earlier warps), then every warp ranks equal keys in each
+//             32-particle step with __match_any_sync and writes every particle
+//             (position and payloads) to its start + rank.
 // In the PIC step the count pass is skipped when the previous step's gather + push
-// kernel has already added the new positions' counts into the (zeroed) table.
+// kernel has already added the new positions' counts into the table the previous
+// scan zeroed (two tables, used in turn).  The scan and the scatter are launched as
+// programmatic dependents: the scatter's key loads and histograms overlap the scan.
 // The order inside a bin is the input order (stable), so results are
 // deterministic.  The count table has one entry per (bin, block) rather than per
 // (bin, warp), so it stays small next to the particle data.
@@ -40,7 +42,8 @@ __device__ __forceinline__ int sort_key(uint32_t u, int nbins, int shift)
     return bin_of(u, nbins);
 }
 
-#define SORT_MAXR 4  // 32-particle steps whose loads are issued together
+#define SORT_MAXR 4  // 32-particle steps whose loads are issued together (8-byte payloads)
+#define SORT_MAXR_N 8  // the same with 4-byte payloads only
 #define COUNT_MAXR 8  // the same for the count kernel
 
 // the block's histogram of its tile; each thread issues the loads of COUNT_MAXR
@@ -82,6 +85,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) sort_scan_kernel(unsigned int *a
 {
     constexpr int R = SCAN_TILE / SCAN_THREADS;
     __shared__ unsigned int wsum[SCAN_THREADS / 32];
+    kde_pdl_wait();  // the counts come from the kernel before
+    kde_pdl_trigger();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // block-wide exclusive scan of one value a thread; returns the prefix, adds the total to carry
     auto block_scan = [&](unsigned int v, unsigned int &carry) -> unsigned int {
@@ -136,21 +141,73 @@ struct ScatterPl {
     int n;
 };
 
-// NPL payload arrays (4- or 8-byte elements) move with the keys; every load of a
-// chunk of SORT_MAXR steps is issued before the chunk is ranked and written
-template <bool DIGIT, int NPL>
-__global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins, int shift, int unit,
-                                    int nblk, const unsigned int *__restrict__ seg,
-                                    const unsigned int *__restrict__ tot, int ntiles, uint32_t *u_out, ScatterPl pl,
-                                    uint32_t *perm_out)
+// NPL payload arrays (4- or 8-byte elements) move with the keys.  NARROW (every payload
+// 4 bytes) takes SORT_MAXR_N steps of 32 particles a chunk, else SORT_MAXR.  A warp
+// whose unit fits one chunk loads its keys and payloads once, at the start, and keeps
+// them in registers through the ranking: every load of the kernel is then in flight
+// before the first dependent step, and the whole pass is one round of loads, the
+// block's offsets and one round of stores.  With a larger unit the payloads are
+// loaded chunk by chunk in the write phase.  The keys are the sort's input, which
+// the scan does not write, so they are read before kde_pdl_wait(); the scan's
+// offsets and tile totals after it.
+template <bool DIGIT, int NPL, bool NARROW>
+__global__ void __launch_bounds__(256, NARROW ? 4 : 1) sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, int nbins,
+                                                           int shift, int unit, int nblk,
+                                                           const unsigned int *__restrict__ seg,
+                                                           const unsigned int *__restrict__ tot, int ntiles,
+                                                           uint32_t *u_out, ScatterPl pl, uint32_t *perm_out)
 {
+    constexpr int SR = NARROW ? SORT_MAXR_N : SORT_MAXR;
+    constexpr int NP1 = NPL > 0 ? NPL : 1;
     extern __shared__ unsigned int hist[];
     const int wpb = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned int *h = hist + (size_t)warp * nbins;
     unsigned int *tpre = hist + (size_t)wpb * nbins;  // exclusive prefix of the scan's tile totals
     for (int b = threadIdx.x; b < wpb * nbins; b += blockDim.x) hist[b] = 0;
-    // the tile totals' exclusive prefix, by warp 0 (a few hundred values at most)
+    const int64_t i0 = ((int64_t)blockIdx.x * wpb + warp) * unit;
+    const int64_t i1 = i0 + unit < N ? i0 + unit : N;  // empty when i0 >= N
+    const bool one = i1 - i0 <= 32 * SR;               // the unit is a single chunk
+    const unsigned int lt = (1u << lane) - 1u;
+    uint32_t uu[SR];
+    uint32_t lo[NP1][SR], hi[NARROW ? 1 : NP1][SR];
+    auto load_payload = [&](int64_t c0) {
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+            const int64_t i = c0 + r * 32 + lane;
+            const bool ok = i < i1;
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                if (!NARROW && pl.elem[k] == 8) {
+                    const uint2 w = ok ? ((const uint2 *)pl.src[k])[i] : make_uint2(0u, 0u);
+                    lo[k][r] = w.x;
+                    hi[NARROW ? 0 : k][r] = w.y;
+                } else {
+                    lo[k][r] = ok ? ((const uint32_t *)pl.src[k])[i] : 0u;
+                }
+            }
+        }
+    };
+    __syncthreads();
+    // per-warp histograms of the keys
+    for (int64_t c0 = i0; c0 < i1; c0 += 32 * SR) {
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+            const int64_t i = c0 + r * 32 + lane;
+            uu[r] = i < i1 ? u[i] : 0u;
+        }
+        if (one) load_payload(c0);
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+            const int64_t i = c0 + r * 32 + lane;
+            const int key = i < i1 ? sort_key<DIGIT>(uu[r], nbins, shift) : -1;
+            const unsigned int peers = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && lane == __ffs(peers) - 1) h[key] += __popc(peers);
+            __syncwarp();
+        }
+    }
+    kde_pdl_wait();  // the scan's results from here on
+    kde_pdl_trigger();
     if (warp == 0) {
         unsigned int carry = 0;
         for (int t0 = 0; t0 < ntiles; t0 += 32) {
@@ -166,30 +223,8 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
         }
     }
     __syncthreads();
-    const int64_t i0 = ((int64_t)blockIdx.x * wpb + warp) * unit;
-    const int64_t i1 = i0 + unit < N ? i0 + unit : N;  // empty when i0 >= N
-    const unsigned int lt = (1u << lane) - 1u;
-    // the warp's histogram of its unit (one leader per key and step; steps ordered by __syncwarp)
-    for (int64_t c0 = i0; c0 < i1; c0 += 32 * SORT_MAXR) {
-        uint32_t uu[SORT_MAXR];
-#pragma unroll
-        for (int r = 0; r < SORT_MAXR; ++r) {
-            const int64_t i = c0 + r * 32 + lane;
-            uu[r] = i < i1 ? u[i] : 0u;
-        }
-#pragma unroll
-        for (int r = 0; r < SORT_MAXR; ++r) {
-            const int64_t i = c0 + r * 32 + lane;
-            const int key = i < i1 ? sort_key<DIGIT>(uu[r], nbins, shift) : -1;
-            const unsigned int peers = __match_any_sync(0xffffffffu, key);
-            if (key >= 0 && lane == __ffs(peers) - 1) h[key] += __popc(peers);
-            __syncwarp();
-        }
-    }
-    __syncthreads();
     // destination starts: the block's segment start of each bin plus the earlier warps'
-    // counts; the consumed count entry is put back to zero (the PIC step's gather adds the
-    // next step's counts into a zeroed table)
+    // counts
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
         const size_t flat = (size_t)b * nblk + blockIdx.x;
         unsigned int run = seg[flat] + tpre[flat / SCAN_TILE];
@@ -200,28 +235,17 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
         }
     }
     __syncthreads();
-    for (int64_t c0 = i0; c0 < i1; c0 += 32 * SORT_MAXR) {
-        uint32_t uu[SORT_MAXR];
-        uint32_t lo[NPL > 0 ? NPL : 1][SORT_MAXR], hi[NPL > 0 ? NPL : 1][SORT_MAXR];
+    for (int64_t c0 = i0; c0 < i1; c0 += 32 * SR) {
+        if (!one) {
 #pragma unroll
-        for (int r = 0; r < SORT_MAXR; ++r) {
-            const int64_t i = c0 + r * 32 + lane;
-            const bool ok = i < i1;
-            uu[r] = ok ? u[i] : 0u;
-#pragma unroll
-            for (int k = 0; k < NPL; ++k) {
-                if (pl.elem[k] == 8) {
-                    const uint2 w = ok ? ((const uint2 *)pl.src[k])[i] : make_uint2(0u, 0u);
-                    lo[k][r] = w.x;
-                    hi[k][r] = w.y;
-                } else {
-                    lo[k][r] = ok ? ((const uint32_t *)pl.src[k])[i] : 0u;
-                    hi[k][r] = 0u;
-                }
+            for (int r = 0; r < SR; ++r) {
+                const int64_t i = c0 + r * 32 + lane;
+                uu[r] = i < i1 ? u[i] : 0u;
             }
+            load_payload(c0);
         }
 #pragma unroll
-        for (int r = 0; r < SORT_MAXR; ++r) {
+        for (int r = 0; r < SR; ++r) {
             const int64_t i = c0 + r * 32 + lane;
             if (c0 + r * 32 >= i1) break;
             const bool valid = i < i1;
@@ -238,7 +262,7 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
                 u_out[dst] = uu[r];
 #pragma unroll
                 for (int k = 0; k < NPL; ++k) {
-                    if (pl.elem[k] == 8) ((uint2 *)pl.dst[k])[dst] = make_uint2(lo[k][r], hi[k][r]);
+                    if (!NARROW && pl.elem[k] == 8) ((uint2 *)pl.dst[k])[dst] = make_uint2(lo[k][r], hi[NARROW ? 0 : k][r]);
                     else ((uint32_t *)pl.dst[k])[dst] = lo[k][r];
                 }
                 if (perm_out) perm_out[dst] = (uint32_t)i;
@@ -247,10 +271,20 @@ __global__ void sort_scatter_kernel(const uint32_t *__restrict__ u, int64_t N, i
     }
 }
 
-template <bool DIGIT, int NPL>
-static void set_scatter_attr(kde_ctx *ctx)
+template <bool DIGIT, int NPL, bool NARROW>
+static cudaError_t scatter_launch(kde_ctx *ctx, int nblk, int threads, size_t smem, const uint32_t *u, int64_t N,
+                                  int nbins, int shift, int unit, const unsigned int *seg, const unsigned int *tot,
+                                  int ntiles, uint32_t *u_out, const ScatterPl &sp, uint32_t *perm_out)
 {
-    cudaFuncSetAttribute(sort_scatter_kernel<DIGIT, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    auto kern = sort_scatter_kernel<DIGIT, NPL, NARROW>;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return kde_launch(ctx, true, kern, dim3(nblk), dim3(threads), smem, u, N, nbins, shift, unit, nblk, seg, tot,
+                      ntiles, u_out, sp, perm_out);
 }
 
 // tile geometry of a sort of N keys into nbins bins: wpb warps of `unit` keys a block
@@ -317,12 +351,6 @@ static kde_status sort_pass(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbin
         KDE_CUDA(ctx,
                  cudaFuncSetAttribute(sort_count_kernel<DIGIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024),
                  "sort attribute");
-        set_scatter_attr<DIGIT, 0>(ctx);
-        set_scatter_attr<DIGIT, 1>(ctx);
-        set_scatter_attr<DIGIT, 2>(ctx);
-        set_scatter_attr<DIGIT, 3>(ctx);
-        set_scatter_attr<DIGIT, 4>(ctx);
-        KDE_CUDA(ctx, cudaGetLastError(), "sort attribute");
         attr_set = true;
     }
     if (smem > 100 * 1024) return kde_fail(ctx, KDE_ENOTSUP, "sort: %d tiles of counts exceed shared memory", ntiles);
@@ -332,27 +360,42 @@ static kde_status sort_pass(kde_ctx *ctx, const uint32_t *u, int64_t N, int nbin
                                                                                     counts);
         KDE_LAUNCHED(ctx, "sort_count_kernel");
     }
-    sort_scan_kernel<<<ntiles, SCAN_THREADS, 0, ctx->stream>>>(counts, ncounts, tiles, DIGIT ? nullptr : other);
+    KDE_CUDA(ctx, kde_launch(ctx, true, sort_scan_kernel, dim3(ntiles), dim3(SCAN_THREADS), 0, counts, ncounts, tiles,
+                             DIGIT ? nullptr : other),
+             "sort_scan_kernel");
     KDE_LAUNCHED(ctx, "sort_scan_kernel");
     ScatterPl sp{};
     sp.n = npl;
+    bool narrow = true;
     for (int k = 0; k < npl; ++k) {
         sp.src[k] = pl[k].src;
         sp.dst[k] = pl[k].dst;
         sp.elem[k] = pl[k].elem;
+        narrow = narrow && pl[k].elem == 4;
     }
-    switch (npl) {
-    case 0: sort_scatter_kernel<DIGIT, 0><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                tiles, ntiles, u_out, sp, perm_out); break;
-    case 1: sort_scatter_kernel<DIGIT, 1><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                tiles, ntiles, u_out, sp, perm_out); break;
-    case 2: sort_scatter_kernel<DIGIT, 2><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                tiles, ntiles, u_out, sp, perm_out); break;
-    case 3: sort_scatter_kernel<DIGIT, 3><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                tiles, ntiles, u_out, sp, perm_out); break;
-    default: sort_scatter_kernel<DIGIT, 4><<<nblk, wpb * 32, smem, ctx->stream>>>(u, N, nbins, shift, unit, nblk, counts,
-                                                                                 tiles, ntiles, u_out, sp, perm_out); break;
+    cudaError_t le;
+#define KDE_SCATTER(NPL_, NARROW_)                                                                                  \
+    scatter_launch<DIGIT, NPL_, NARROW_>(ctx, nblk, wpb * 32, smem, u, N, nbins, shift, unit, counts, tiles, ntiles, \
+                                         u_out, sp, perm_out)
+    if constexpr (DIGIT) le = KDE_SCATTER(0, true);
+    else if (npl == 0) le = KDE_SCATTER(0, true);
+    else if (narrow) {
+        switch (npl) {
+        case 1: le = KDE_SCATTER(1, true); break;
+        case 2: le = KDE_SCATTER(2, true); break;
+        case 3: le = KDE_SCATTER(3, true); break;
+        default: le = KDE_SCATTER(4, true); break;
+        }
+    } else {
+        switch (npl) {
+        case 1: le = KDE_SCATTER(1, false); break;
+        case 2: le = KDE_SCATTER(2, false); break;
+        case 3: le = KDE_SCATTER(3, false); break;
+        default: le = KDE_SCATTER(4, false); break;
+        }
     }
+#undef KDE_SCATTER
+    KDE_CUDA(ctx, le, "sort_scatter_kernel");
     KDE_LAUNCHED(ctx, "sort_scatter_kernel");
     return KDE_OK;
 }

@@ -229,3 +229,31 @@ def test_pic_step_host_equals_device_run(ctx, kp):
     assert torch.equal(host.u, dev.u.cpu()) and torch.equal(host.v, dev.v.cpu())
     assert torch.equal(host.kappa, dev.kappa.cpu()) and torch.equal(host.id, dev.id.cpu())
     assert torch.equal(host.energy, dev.energy.cpu()) and torch.equal(host.kappa_star, dev.kappa_star.cpu())
+
+
+@pytest.mark.parametrize("N, Ng, per_particle", [(1 << 20, 256, True), (3 * 7919, 1024, False)])
+def test_launch_overlap_is_bitwise_neutral(ctx, kp, N, Ng, per_particle):
+    # the step chain launched as programmatic dependents (the default) and launched in
+    # plain stream order give bitwise the same state, with and without profiling events
+    # between the kernels
+    L, dt = 4 * math.pi, 0.1
+    u, v = I.landau_load(44, N, L, 0.05, 1.0)
+    kw = dict(kappa=np.ones(N), width_every=4, cand=I.log_candidates(1.0, 1e4, 16), alpha=0.5, kappa_min=1.0,
+              kappa_max=1e5) if per_particle else dict(kappa_uniform=3.0)
+    states = [make_state(kp, u, v.astype(np.float32), L, Ng, dt, 9, **kw) for _ in range(3)]
+    try:
+        ctx.set_launch_overlap(True)
+        ctx.pic_step(states[0], 9)
+        ctx.profile_enable(True)
+        ctx.pic_step(states[1], 9)
+        ctx.profile_enable(False)
+        ctx.set_launch_overlap(False)
+        ctx.pic_step(states[2], 9)
+        ctx.sync()
+    finally:
+        ctx.set_launch_overlap(True)
+        ctx.profile_enable(False)
+    names = ("u", "v", "id", "energy") + (("kappa", "kappa_star") if per_particle else ())
+    for s in states[1:]:
+        for t in names:
+            assert torch.equal(getattr(states[0], t), getattr(s, t)), t
