@@ -683,6 +683,20 @@ def ensemble_record(kp, ctx, dev, args):
     frac = float(np.sum(Ns[:sample])) / float(np.sum(Ns))
     t_plain = timed(plain, flush, 1)[0] / 3 / frac
     ens.close()
+    # the autotuner's choice per key of the realisations (grid size, log2 N, width class)
+    keys = {}
+    for r in range(R):
+        wc = min(255, max(1, int(4.0 * math.log2(kap[r]) + 128.0)))
+        keys[(int(Ngs[r]), int(Ns[r]).bit_length() - 1, wc)] = kap[r]
+    tuned = {}
+    for e in ctx.autotune_table():
+        kk = (e["Ng"], e["log2_N"], e["width_class"])
+        if kk in keys:
+            tuned.setdefault(kk, {"Ng": kk[0], "log2_N": kk[1], "kappa": keys[kk]})[e["kind"]] = e["value"]
+    cut_hist = {}
+    for t in tuned.values():
+        if "cut_log2" in t:
+            cut_hist[str(t["cut_log2"])] = cut_hist.get(str(t["cut_log2"]), 0) + 1
     Ntot = float(np.sum(Ns))
     return {"workload": "ensemble of %d Landau realisations, N log-uniform in [2^14, 2^20] (total %d), Ng in "
                         "{128,256,512,1024}, one CUDA graph per step" % (R, int(Ntot)),
@@ -694,6 +708,9 @@ def ensemble_record(kp, ctx, dev, args):
             "pairs_per_s_graph_definition": 2.0 * float(np.sum(Ns * Ngs)) / (t_graph * 1e-3),
             "mise_t0": {"mean": float(np.mean(mise)), "min": float(np.min(mise)), "max": float(np.max(mise))},
             "kappa_star": {"min": float(np.min(kap)), "max": float(np.max(kap))},
+            "autotune": {"keys": len(keys), "tuned": sorted(tuned.values(), key=lambda t: (t["Ng"], t["log2_N"],
+                                                                                          t["kappa"])),
+                         "cut_log2_histogram": cut_hist},
             "l2": "inputs larger than L2 (%.0f MB of particle state)" % (Ntot * 8 / 1e6),
             "host_build_s": t_build}
 

@@ -94,18 +94,42 @@ const char *kde_last_error(const kde_ctx *ctx);
  * cleared by this call). */
 kde_status kde_sync(kde_ctx *ctx);
 
-/* Tile-shape autotuner of the FP32 gather (no counterpart in the paper: a speed
- * facility of this library).  The packed gather has several tile shapes (particles a
- * lane, node-loop unrolling, launch bound) that give bitwise-identical results.  With
- * enable != 0, the first FP32 gather (kde_gather, or the gather and push of pic_step
- * and of the ensemble) of each key (grid size, log2 N, uniform width to a quarter
- * octave, or "per-particle widths") runs every shape twice on its own data, timed by
- * CUDA events, and keeps the fastest for that key; later calls with the key use it.
- * Tuning synchronises the stream once per new key and is skipped while the stream is
- * being captured or when an output aliases an input.  Off by default (the default
- * shape is used).  kde_autotune_entries reports how many keys have been tuned. */
+/* Autotuner (no counterpart in the paper: a speed facility of this library).  Keys are
+ * (grid size, log2 N, uniform width to a quarter octave, or "per-particle widths").
+ *  - Tile shape of the FP32 gather.  The packed gather has several tile shapes
+ *    (particles a lane, node-loop unrolling, launch bound) that give bitwise-identical
+ *    results.  The first FP32 gather (kde_gather, or the gather and push of pic_step
+ *    and of the ensemble) of each key runs every shape twice on its own data, timed by
+ *    CUDA events, and keeps the fastest for that key.
+ *  - Truncation radius of the FP32 PIC step (see kde_set_truncation).  Unless a cut is
+ *    fixed, the first FP32 pic_step of each key runs the deposit + field and a gather
+ *    on the step's own sorted particles at the cuts 2^-24, 2^-20 and 2^-18 of each
+ *    kernel's peak, timed by CUDA events; a cut is admitted when the node field and the
+ *    particle fields match those of 2^-24 within 2.5e-6 relative L2, and is chosen when
+ *    it is at least 3% faster than the best admitted cut so far.  Later steps with the
+ *    key use it in their deposit and gather alike.
+ * Later calls with a tuned key use the stored choice.  Tuning synchronises the stream
+ * once per new key and is skipped while the stream is being captured (and, for the
+ * gather, when an output aliases an input).  Off by default.  kde_autotune_entries
+ * reports how many gather keys have been tuned; kde_autotune_table lists every stored
+ * choice: keys[i] (bits 0-15 grid size, 16-23 log2 N, 24-31 width class: 0 for
+ * per-particle widths, else 4 log2(kappa) + 128), kinds[i] (0: gather tile shape,
+ * values[i] its index; 1: truncation, values[i] the cut exponent c of 2^-c), at most
+ * cap entries written, *n_out = the number stored. */
 kde_status kde_set_autotune(kde_ctx *ctx, int32_t enable);
 kde_status kde_autotune_entries(const kde_ctx *ctx, int32_t *n_out);
+kde_status kde_autotune_table(const kde_ctx *ctx, int32_t cap, uint64_t *keys, int32_t *kinds, double *values,
+                              int32_t *n_out);
+
+/* Truncation of the FP32 deposit and gather (Eq. kde, evaluated over a finite window;
+ * no counterpart in the paper, whose sums run over all nodes).  Every FP32 deposit and
+ * gather evaluates each particle's kernel at least over the nodes where its weight is
+ * 2^-c of its peak or more, c = log2_cut.  The kernel mass left outside is at most
+ * 3.6e-8 (c = 24, the default), 5.8e-7 (20), 2.3e-6 (18) and 9.2e-6 (16) of the total,
+ * over all widths (worst near kappa = 6-9; von Mises tail integrals).  log2_cut = 0
+ * returns to the default, with pic_step's cut chosen by the autotuner when it is on.
+ * KDE_EINVAL unless log2_cut is 0 or in [16, 40].  FP64 paths always cut at 2^-64. */
+kde_status kde_set_truncation(kde_ctx *ctx, double log2_cut);
 
 /* Launch overlap (no counterpart in the paper: a speed facility of this library).
  * With enable != 0 (the default) the kernels of the FP32 step chain -- the sort's scan

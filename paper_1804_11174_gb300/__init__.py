@@ -124,6 +124,8 @@ def load_library(path: str | None = None):
         "kde_profile_read": (S, [_P, ctypes.c_int, _P, _P]),
         "kde_set_autotune": (S, [_P, ctypes.c_int32]),
         "kde_set_launch_overlap": (S, [_P, ctypes.c_int32]),
+        "kde_set_truncation": (S, [_P, ctypes.c_double]),
+        "kde_autotune_table": (S, [_P, ctypes.c_int32, _P, _P, _P, _P]),
         "kde_set_wait_limit": (S, [_P, _I64]),
         "kde_autotune_entries": (S, [_P, _P]),
     }
@@ -322,6 +324,31 @@ class Context:
     def set_autotune(self, on: bool = True):
         """kde_set_autotune: tune the FP32 gather's tile shape per key on first use."""
         self._check("kde_set_autotune", self.lib.kde_set_autotune(self.h, int(on)))
+
+    def set_truncation(self, log2_cut: float = 0.0):
+        """kde_set_truncation: FP32 kernels cut at 2^-log2_cut of their peak (0: default / tuned)."""
+        self._check("kde_set_truncation", self.lib.kde_set_truncation(self.h, float(log2_cut)))
+
+    def autotune_table(self):
+        """kde_autotune_table: every stored autotuner choice as a dict with the key's grid
+        size, log2 N and width class (0: per-particle widths, else 4 log2(kappa) + 128),
+        the kind ("gather_shape" or "cut_log2") and its value."""
+        n = ctypes.c_int32()
+        self._check("kde_autotune_table", self.lib.kde_autotune_table(self.h, 0, None, None, None,
+                                                                      ctypes.addressof(n)))
+        cap = n.value
+        keys = np.zeros(max(cap, 1), dtype=np.uint64)
+        kinds = np.zeros(max(cap, 1), dtype=np.int32)
+        vals = np.zeros(max(cap, 1), dtype=np.float64)
+        self._check("kde_autotune_table", self.lib.kde_autotune_table(self.h, cap, keys.ctypes.data, kinds.ctypes.data,
+                                                                      vals.ctypes.data, ctypes.addressof(n)))
+        out = []
+        for k, t, v in zip(keys[:cap], kinds[:cap], vals[:cap]):
+            k = int(k)
+            out.append({"Ng": k & 0xFFFF, "log2_N": (k >> 16) & 0xFF, "width_class": (k >> 24) & 0xFF,
+                        "kind": "gather_shape" if t == 0 else "cut_log2",
+                        "value": int(v) if t == 0 else float(v)})
+        return out
 
     def set_launch_overlap(self, on: bool = True):
         """kde_set_launch_overlap: programmatic dependent launches in the FP32 step chain."""

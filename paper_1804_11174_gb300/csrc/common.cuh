@@ -92,6 +92,7 @@ enum WsSlot {
     WS_HOST_NORM,
     WS_HOST_ID,
     WS_HOST_HIST,  // energy, kappa* and ln p histories
+    WS_TUNE,       // truncation tuner: reference and candidate fields and their error sums
     WS_NSLOTS
 };
 
@@ -124,6 +125,8 @@ struct kde_ctx {
     bool autotune = false;                  // kde_set_autotune
     bool overlap = true;                    // kde_set_launch_overlap: PDL launches in the step chain
     std::map<uint64_t, int> gat2_tuned;     // packed-gather tile shape per key (gather.cu)
+    double cut_fixed = 0.0;                 // kde_set_truncation: FP32 cut exponent, 0 = automatic
+    std::map<uint64_t, float> cut_tuned;    // FP32 PIC truncation cut exponent per key (pic.cu)
     void *sp_atab = nullptr;                // workspace holding the Bessel ratios of sp_atab_cands (spectral.cu)
     std::vector<double> sp_atab_cands;
 };
@@ -206,6 +209,28 @@ struct KdeRange {
     KdeRange(const KdeRange &) = delete;
     KdeRange &operator=(const KdeRange &) = delete;
 };
+
+// FP32 truncation: each kernel is evaluated over at least the nodes where its weight is
+// 2^-xcut of its peak or more.  xcut = 24 unless fixed by kde_set_truncation (or, for
+// the PIC step, chosen by the truncation tuner); FP64 paths always use KDE_XCUT64.
+inline float kde_fp32_cut(const kde_ctx *ctx)
+{
+    return ctx->cut_fixed > 0.0 ? (float)ctx->cut_fixed : (float)KDE_XCUT;
+}
+
+// autotuner key: grid size, log2 of N, and the uniform width in quarter octaves (0 for
+// per-particle widths, whose values the host does not see)
+inline uint64_t kde_width_key(int64_t N, int Ng, bool per_particle, double kappa_u)
+{
+    int lg = 0;
+    while (lg < 40 && (1LL << (lg + 1)) <= N) ++lg;
+    int kc = 0;
+    if (!per_particle) {
+        const double q = 4.0 * log2(kappa_u) + 128.0;
+        kc = q < 1.0 ? 1 : (q > 255.0 ? 255 : (int)q);
+    }
+    return (uint64_t)Ng | ((uint64_t)lg << 16) | ((uint64_t)kc << 24);
+}
 
 // number of nodes on each side of a particle's cell that its truncated kernel
 // can reach: ceil(r / dtheta), r = 2 asin(sqrt(XCUT ln2 / (2 kappa))), or Ng
@@ -437,7 +462,8 @@ struct DepRows {
     int G;
 };
 kde_status kde_deposit_rows_f32(kde_ctx *ctx, const uint32_t *u, const float *kappa, float kappa_u, const float *norm,
-                                float norm_u, int64_t N, int Ng, double coef, float w_u, double bound, DepRows *out);
+                                float norm_u, int64_t N, int Ng, double coef, float w_u, double bound, DepRows *out,
+                                float xcut = 0.f);
 // the PIC step's field from those rows: rho_total = background + charge * rho with its
 // mean removed, E by the spectral or finite-difference Green's function (FP32 output)
 kde_status kde_field_from_rows(kde_ctx *ctx, const long long *rows, const int2 *hdr, int G, int Ng, double L,
@@ -469,11 +495,12 @@ struct PushArgs {
     double dx;
     unsigned int *counts;    // FP32 gather: count table of the next cell sort (kde_sort_counts_table), or null
     int cnt_nblk, cnt_shift;
+    float xcut;              // FP32 truncation cut exponent (kde_fp32_cut), 0: the context's default
 };
 template <typename T>
 kde_status kde_gather_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,
                              int64_t N, const T *field, int Ng, double coef, T *out, const uint32_t *perm,
-                             const PushArgs *push);
+                             const PushArgs *push, float xcut = 0.f);
 
 // candidate widths (or scale factors) for the CV kernels, passed by value
 struct CandList {

@@ -247,6 +247,40 @@ extern "C" kde_status kde_set_autotune(kde_ctx *ctx, int32_t enable)
     return KDE_OK;
 }
 
+extern "C" kde_status kde_set_truncation(kde_ctx *ctx, double log2_cut)
+{
+    if (!ctx) return KDE_EINVAL;
+    if (!(log2_cut == 0.0 || (log2_cut >= 16.0 && log2_cut <= 40.0)))
+        return kde_fail(ctx, KDE_EINVAL, "kde_set_truncation: 0 (automatic) or a cut exponent in [16, 40]");
+    ctx->cut_fixed = log2_cut;
+    return KDE_OK;
+}
+
+extern "C" kde_status kde_autotune_table(const kde_ctx *ctx, int32_t cap, uint64_t *keys, int32_t *kinds,
+                                         double *values, int32_t *n_out)
+{
+    if (!ctx || !n_out || cap < 0 || (cap > 0 && (!keys || !kinds || !values))) return KDE_EINVAL;
+    int32_t n = 0;
+    for (const auto &e : ctx->gat2_tuned) {
+        if (n < cap) {
+            keys[n] = e.first;
+            kinds[n] = 0;
+            values[n] = (double)e.second;
+        }
+        ++n;
+    }
+    for (const auto &e : ctx->cut_tuned) {
+        if (n < cap) {
+            keys[n] = e.first;
+            kinds[n] = 1;
+            values[n] = (double)e.second;
+        }
+        ++n;
+    }
+    *n_out = n;
+    return KDE_OK;
+}
+
 extern "C" kde_status kde_set_launch_overlap(kde_ctx *ctx, int32_t enable)
 {
     if (!ctx) return KDE_EINVAL;

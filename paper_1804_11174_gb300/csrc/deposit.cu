@@ -49,6 +49,7 @@ template <typename T> struct DepSrc {
     unsigned int *status;
     int scale_exp;  // KDE_ES_FROM_BOUND, or the exponent es of the fixed-point scale 2^es
     const float2 *ntab;  // FP32 norm table (kde_norm_tab) for per-particle widths without norms, or nullptr
+    float xcut = (float)KDE_XCUT;  // FP32 packed kernels: truncation cut exponent (kde_fp32_cut)
 };
 
 #define KDE_ES_FROM_BOUND (-100000)
@@ -449,7 +450,7 @@ __device__ void deposit_chunk_body_x2(const DepSrc<float> &S, int64_t chunk, flo
         kmax = fmaxf(kmax, __int_as_float(red[DEP_WARPS + k]));
     }
     // the window shrinks as the width grows: the smallest width's window covers all
-    const int W = window_nodes_f(kmin, Ng, (float)KDE_XCUT);
+    const int W = window_nodes_f(kmin, Ng, S.xcut);
     const bool cosf = allow_cos && kmax <= KDE_COSFORM_KMAX;
     // the particle records
 #pragma unroll
@@ -748,7 +749,7 @@ __global__ void __launch_bounds__(DEPP_THREADS, DEPP_MINB) deposit_persist_kerne
     }
     const int es = s_es;
     const bool cosf = kmax <= KDE_COSFORM_KMAX;
-    const int W = window_nodes_f(kmin, Ng, (float)KDE_XCUT);
+    const int W = window_nodes_f(kmin, Ng, S.xcut);
     const int c_first = kde_cell(S.u[i0], Ng), c_last = kde_cell(S.u[i1 - 1], Ng);
     int g_lo = c_first - W;
     int R = c_last + W - g_lo + 1;
@@ -876,7 +877,8 @@ kde_status kde_deposit_reserve(kde_ctx *ctx, int64_t N, int Ng)
 template <typename T>
 static kde_status deposit_sorted_impl(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm,
                                       T norm_u, const T *w, T w_u, int64_t N, int Ng, double coef, long long *acc,
-                                      double bound, const unsigned int *wmax_bits, double norm_bound, DepRows *rows_out)
+                                      double bound, const unsigned int *wmax_bits, double norm_bound, DepRows *rows_out,
+                                      float xcut = 0.f)
 {
     // the persistent FP32 kernel writes every node; the others add into zeroed accumulators
     if (!(sizeof(T) == 4 && N > 0))
@@ -911,6 +913,7 @@ static kde_status deposit_sorted_impl(kde_ctx *ctx, const uint32_t *u, const T *
         S.scale_exp = 62 - e;
     }
     S.ntab = ctx->norm_tab;
+    S.xcut = xcut > 0.f ? xcut : kde_fp32_cut(ctx);
     if constexpr (sizeof(T) == 4) {
         DepPlan Pl{};
         KDE_TRY(depp_plan(ctx, N, Ng, acc, Pl));
@@ -954,11 +957,12 @@ kde_status kde_deposit_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T
 }
 
 kde_status kde_deposit_rows_f32(kde_ctx *ctx, const uint32_t *u, const float *kappa, float kappa_u, const float *norm,
-                                float norm_u, int64_t N, int Ng, double coef, float w_u, double bound, DepRows *out)
+                                float norm_u, int64_t N, int Ng, double coef, float w_u, double bound, DepRows *out,
+                                float xcut)
 {
     if (N < 1) return kde_fail(ctx, KDE_EINVAL, "deposit rows: need N >= 1");
     return deposit_sorted_impl<float>(ctx, u, kappa, kappa_u, norm, norm_u, nullptr, w_u, N, Ng, coef, nullptr, bound,
-                                      nullptr, 0.0, out);
+                                      nullptr, 0.0, out, xcut);
 }
 
 template <typename T>

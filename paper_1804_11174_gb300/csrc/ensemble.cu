@@ -92,9 +92,20 @@ static kde_status ens_enqueue_step(kde_ensemble *e, double *energy, int nmax, bo
         kde_ctx *lc = e->lane_ctx[r % e->nl];
         s.step = 0;  // energy slot W[r]; the kick is set by the flag
         s.flags = first ? 0u : PIC_NO_BACKSTEP;
+        if (first) {
+            // one autotuner table for the whole ensemble: a key tuned on one lane is reused
+            // by the others (the host issues the realisations in order, and tuning waits
+            // for its own runs); the caller's context keeps the union
+            lc->gat2_tuned.insert(e->ctx->gat2_tuned.begin(), e->ctx->gat2_tuned.end());
+            lc->cut_tuned.insert(e->ctx->cut_tuned.begin(), e->ctx->cut_tuned.end());
+        }
         kde_status st = pic_step(lc, &s, 1);
         s.step = 0;
         if (st != KDE_OK) return kde_fail(e->ctx, st, "ensemble realisation %d: %s", r, kde_last_error(lc));
+        if (first) {
+            e->ctx->gat2_tuned.insert(lc->gat2_tuned.begin(), lc->gat2_tuned.end());
+            e->ctx->cut_tuned.insert(lc->cut_tuned.begin(), lc->cut_tuned.end());
+        }
     }
     KDE_TRY(ens_join(e));
     ens_record_kernel<<<(e->R + 255) / 256, 256, 0, e->stream>>>(e->W, e->R, energy, nmax, e->d_step);
@@ -143,7 +154,9 @@ extern "C" kde_status kde_ensemble_create(kde_ctx *ctx, kde_ensemble **out, int3
         kde_ctx *lc = nullptr;
         if (err == cudaSuccess && kde_create(&lc, ctx->device, st) != KDE_OK) err = cudaErrorMemoryAllocation;
         if (err == cudaSuccess) {
-            lc->autotune = ctx->autotune;  // lanes tune their gathers in the uncaptured first step
+            lc->autotune = ctx->autotune;  // lanes tune in the uncaptured first step
+            lc->cut_fixed = ctx->cut_fixed;
+            lc->overlap = ctx->overlap;
             e->lane_ctx.push_back(lc);
         }
     }

@@ -58,6 +58,7 @@ template <typename T> struct GatherArgs {
     // positions are added with one atomic per warp and distinct cell)
     unsigned int *counts;
     int cnt_nblk, cnt_shift;
+    float xcut = (float)KDE_XCUT;  // FP32 packed gather: truncation cut exponent
 };
 
 __device__ __forceinline__ int window_nodes_g(float kappa, int Ng, float xcut)
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherAr
         if (valid) {
             kmax = fmaxf(kmax, k);
             const int cell = kde_cell(uu[h], Ng);
-            const int W = window_nodes_g(k, Ng, (float)KDE_XCUT);
+            const int W = window_nodes_g(k, Ng, A.xcut);
             lo = min(lo, cell - W);
             hi = max(hi, cell + W);
         }
@@ -446,18 +447,9 @@ static kde_status gat2_variant(kde_ctx *ctx, const GatherArgs<float> &A, int v)
     }
 }
 
-// autotuner key: grid size, log2 of N, and the uniform width in quarter octaves
-// (0 for per-particle widths, whose windows the host does not see)
 static uint64_t gat2_key(const GatherArgs<float> &A)
 {
-    int lg = 0;
-    while (lg < 40 && (1LL << (lg + 1)) <= A.N) ++lg;
-    int kc = 0;
-    if (!A.kappa) {
-        const double q = 4.0 * log2((double)A.kappa_u) + 128.0;
-        kc = q < 1.0 ? 1 : (q > 255.0 ? 255 : (int)q);
-    }
-    return (uint64_t)A.Ng | ((uint64_t)lg << 16) | ((uint64_t)kc << 24);
+    return kde_width_key(A.N, A.Ng, A.kappa != nullptr, (double)A.kappa_u);
 }
 
 // the variant for this call: the tuned one for its key; with autotuning on and no stream
@@ -546,7 +538,7 @@ static kde_status launch_gather(kde_ctx *ctx, GatherArgs<T> &A)
 template <typename T>
 kde_status kde_gather_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T kappa_u, const T *norm, T norm_u,
                              int64_t N, const T *field, int Ng, double coef, T *out, const uint32_t *perm,
-                             const PushArgs *push)
+                             const PushArgs *push, float xcut)
 {
     GatherArgs<T> A{};
     A.u = u;
@@ -560,6 +552,7 @@ kde_status kde_gather_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T 
     A.coef = (T)coef;
     A.out = out;
     A.perm = perm;
+    A.xcut = xcut > 0.f ? xcut : (push && push->xcut > 0.f ? push->xcut : kde_fp32_cut(ctx));
     if (push) {
         A.v_in = (const T *)push->v_in;
         A.u_out = push->u_out;
@@ -585,10 +578,10 @@ kde_status kde_gather_sorted(kde_ctx *ctx, const uint32_t *u, const T *kappa, T 
 
 template kde_status kde_gather_sorted<float>(kde_ctx *, const uint32_t *, const float *, float, const float *, float,
                                              int64_t, const float *, int, double, float *, const uint32_t *,
-                                             const PushArgs *);
+                                             const PushArgs *, float);
 template kde_status kde_gather_sorted<double>(kde_ctx *, const uint32_t *, const double *, double, const double *,
                                               double, int64_t, const double *, int, double, double *,
-                                              const uint32_t *, const PushArgs *);
+                                              const uint32_t *, const PushArgs *, float);
 
 // ---------------------------------------------------------------------------
 template <typename T>

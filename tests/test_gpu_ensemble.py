@@ -24,27 +24,46 @@ def loads(Ns, seed0=0):
     return us, vs
 
 
-def test_ensemble_equals_pic_step_bitwise(ctx, kp):
+@pytest.mark.parametrize("cut", [0.0, 20.0, 18.0, "tuned"])
+def test_ensemble_equals_pic_step_bitwise(ctx, kp, cut):
+    # under each truncation choice (the default 2^-24, fixed cuts, and the autotuner's
+    # per-key choice, which the lanes share) the ensemble gives bitwise the per-realisation
+    # pic_step runs on the same context
     Ns = [3000, 7000, 20000, 5000, 12000]
     Ngs = [128, 256, 512, 1024, 128]
     kap = [20.0, 50.0, 200.0, 30.0, 100.0]
     us, vs = loads(Ns)
     u = to_dev_u(np.concatenate(us))
     v = to_dev(np.concatenate(vs))
-    ens = kp.Ensemble(ctx, Ns, Ngs, kap, L, 0.1, u, v)
-    steps = 10
-    en = torch.zeros(len(Ns) * steps, dtype=torch.float64, device=DEV)
-    ens.run(steps, en, use_graph=True)
-    ctx.sync()
-    en = en.cpu().numpy().reshape(len(Ns), steps)
-    off = np.concatenate([[0], np.cumsum(Ns)])
-    for r in range(len(Ns)):
-        st = kp.PicState(to_dev_u(us[r]), to_dev(vs[r]), L, Ngs[r], 0.1, kappa_uniform=kap[r], max_steps=steps)
-        ctx.pic_step(st, steps)
-        ctx.sync()
-        np.testing.assert_array_equal(en[r], st.energy.cpu().numpy())
-        assert torch.equal(u[off[r]:off[r + 1]], st.u) and torch.equal(v[off[r]:off[r + 1]], st.v)
-    ens.close()
+    c = kp.Context(0) if cut == "tuned" else ctx
+    try:
+        if cut == "tuned":
+            c.set_autotune(True)
+        else:
+            c.set_truncation(cut)
+        ens = kp.Ensemble(c, Ns, Ngs, kap, L, 0.1, u, v)
+        steps = 10
+        en = torch.zeros(len(Ns) * steps, dtype=torch.float64, device=DEV)
+        ens.run(steps, en, use_graph=True)
+        c.sync()
+        if cut == "tuned":
+            cuts = [e for e in c.autotune_table() if e["kind"] == "cut_log2"]
+            assert len(cuts) == len(set(zip(Ngs, kap)))  # one choice per key, shared by the lanes
+            assert all(e["value"] in (24.0, 20.0, 18.0) for e in cuts)
+        en = en.cpu().numpy().reshape(len(Ns), steps)
+        off = np.concatenate([[0], np.cumsum(Ns)])
+        for r in range(len(Ns)):
+            st = kp.PicState(to_dev_u(us[r]), to_dev(vs[r]), L, Ngs[r], 0.1, kappa_uniform=kap[r], max_steps=steps)
+            c.pic_step(st, steps)
+            c.sync()
+            np.testing.assert_array_equal(en[r], st.energy.cpu().numpy())
+            assert torch.equal(u[off[r]:off[r + 1]], st.u) and torch.equal(v[off[r]:off[r + 1]], st.v)
+        ens.close()
+    finally:
+        if cut == "tuned":
+            c.close()
+        else:
+            c.set_truncation(0.0)
 
 
 def test_graph_replay_equals_plain_launches_and_resume(ctx, kp):

@@ -247,7 +247,9 @@ def test_gather_autotune_keeps_results(ctx, kp):
             for a, b in zip(outs, refs):
                 np.testing.assert_array_equal(a, b)
         assert c2.autotune_entries() == 3
-        # pic_step with the tuner on gives the same run bit for bit
+        # pic_step with the tile-shape tuner on gives the same run bit for bit (the
+        # truncation cut held at the default, which the other tuner could change)
+        c2.set_truncation(24.0)
         uu, vv = I.landau_load(32, 20000, L, 0.05, 1.0)
         kk = I.log_uniform(32, I.STREAM_KAPPA, 20000, 5.0, 50.0).astype(np.float32)
         runs = []
@@ -261,3 +263,42 @@ def test_gather_autotune_keeps_results(ctx, kp):
         assert c2.autotune_entries() == 4
     finally:
         c2.close()
+
+
+@pytest.mark.parametrize("cut", [24.0, 20.0, 18.0, 16.0])
+def test_truncation_cut_within_tolerance(ctx, oracle, cut):
+    # every cut kde_set_truncation accepts keeps the FP32 deposit and gather within the
+    # 1e-5 tolerance of the untruncated oracle; kappa = 7.3 sits near the width whose
+    # kernel mass beyond the cut is largest, kappa = 300 has a window well inside the grid
+    L, N = 4 * math.pi, 30001
+    u, x, _ = landau(77, N, L)
+    k = I.log_uniform(77, I.STREAM_KAPPA, N, 5.0, 5e3)
+    ud = to_dev_u(u)
+    base = {}
+    try:
+        for c in (24.0, cut):
+            ctx.set_truncation(c)
+            for Ng, kw, okw in ((256, dict(kappa_uniform=7.3), dict(kappa_u=7.3)),
+                                (512, dict(kappa_uniform=300.0), dict(kappa_u=300.0)),
+                                (512, dict(kappa=to_dev(k)), dict(kappa=k.astype(np.float32)))):
+                rho = ctx.deposit(ud, Ng, L, **kw).cpu().numpy()
+                assert rel_l2(rho, oracle.deposit(x, Ng, L, **okw)) <= TOL32
+                f = np.sin(2 * math.pi * np.arange(Ng) / Ng) + 0.3
+                out = ctx.gather(ud, to_dev(f), L, **kw).cpu().numpy()
+                assert rel_l2(out, oracle.gather(x, f.astype(np.float32), L, **okw)) <= TOL32
+                key = (Ng, str(sorted(okw)), float(okw.get("kappa_u", 0)))
+                if c == 24.0:
+                    base[key] = (rho, out)
+                elif key[2] == 300.0:
+                    # the cut reaches the kernels: a narrower window changes the sums
+                    assert not np.array_equal(rho, base[key][0])
+                    assert not np.array_equal(out, base[key][1])
+    finally:
+        ctx.set_truncation(0.0)
+
+
+def test_truncation_setting_is_checked(ctx, kp):
+    for bad in (15.0, 41.0, -1.0, float("nan")):
+        with pytest.raises(kp.KdeError):
+            ctx.set_truncation(bad)
+    ctx.set_truncation(0.0)

@@ -257,3 +257,29 @@ def test_launch_overlap_is_bitwise_neutral(ctx, kp, N, Ng, per_particle):
     for s in states[1:]:
         for t in names:
             assert torch.equal(getattr(states[0], t), getattr(s, t)), t
+
+
+def test_truncation_tuner_choice_is_used_by_the_step(kp):
+    # the tuner picks one cut per key on the key's first step; the run equals, bit for bit,
+    # a run with that cut fixed, and the choice is one of the candidates
+    L, Ng, dt, N = 4 * math.pi, 512, 0.1, 50_000
+    u, v = I.landau_load(45, N, L, 0.05, 1.0)
+    k = I.log_uniform(45, I.STREAM_KAPPA, N, 5.0, 5e3)
+    a, b = kp.Context(0), kp.Context(0)
+    try:
+        a.set_autotune(True)
+        sa = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 4, kappa=k)
+        a.pic_step(sa, 4)
+        a.sync()
+        cuts = [e for e in a.autotune_table() if e["kind"] == "cut_log2"]
+        assert len(cuts) == 1 and cuts[0]["Ng"] == Ng and cuts[0]["log2_N"] == 15 and cuts[0]["width_class"] == 0
+        assert cuts[0]["value"] in (24.0, 20.0, 18.0)
+        b.set_truncation(cuts[0]["value"])
+        sb = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 4, kappa=k)
+        b.pic_step(sb, 4)
+        b.sync()
+        for t in ("u", "v", "id", "energy", "kappa"):
+            assert torch.equal(getattr(sa, t), getattr(sb, t)), t
+    finally:
+        a.close()
+        b.close()
