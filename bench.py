@@ -122,12 +122,12 @@ def cv_inradius_pairs(u_np, cands):
     return total
 
 
-def grid_window_pairs(kappa_np, Ng):
-    """(particle, node) pairs inside the truncation radius (kernel >= 2^-24 of its peak) for
-    one deposit or one gather: per particle the nodes within r = 2 asin(sqrt(12 ln2 / kappa))
+def grid_window_pairs(kappa_np, Ng, cut=24.0):
+    """(particle, node) pairs inside the truncation radius (kernel >= 2^-cut of its peak) for
+    one deposit or one gather: per particle the nodes within r = 2 asin(sqrt(cut ln2 / (2 kappa)))
     of it, 2 r Ng / (2 pi) on average over positions, at most Ng."""
     k = np.asarray(kappa_np, dtype=np.float64)
-    s2 = np.minimum(24.0 * math.log(2.0) / (2.0 * k), 1.0)
+    s2 = np.minimum(cut * math.log(2.0) / (2.0 * k), 1.0)
     r = 2.0 * np.arcsin(np.sqrt(s2))
     return float(np.minimum(Ng, r * Ng / math.pi).sum())
 
@@ -279,6 +279,11 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         ctx.pic_step(st, P)
     torch.cuda.synchronize()
+    # the truncation cut in force (the autotuner's choice for this key, else 2^-24)
+    cut = 24.0
+    for e in ctx.autotune_table():
+        if e["kind"] == "cut_log2" and (e["Ng"], e["log2_N"], e["width_class"]) == (Ng, N.bit_length() - 1, 0):
+            cut = e["value"]
 
     # ---- the production width-update period: CV (cost rule) + Silverman + 50 PIC steps ----
     if dist:
@@ -294,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
         step_ms += timed(lambda: ctx.pic_step(st, P), flush, 1)
         # widths in force during the period (set by its first-step update), for the
         # in-radius pair count of its 50 deposits and 50 gathers
-        pairs.append(2.0 * P * grid_window_pairs(st.kappa.cpu().numpy(), Ng))
+        pairs.append(2.0 * P * grid_window_pairs(st.kappa.cpu().numpy(), Ng, cut))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     _, launches = ctx.profile_read("all")
@@ -409,7 +414,8 @@ def run_ours(args, rank, world, local_rank):
                    "value_def": "in-radius deposit+gather (particle, node) pairs of the period / period time",
                    "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "gather_tile_shape": "default" if args.no_autotune else "autotuned"},
+                   "gather_tile_shape": "default" if args.no_autotune else "autotuned",
+                   "truncation_cut_log2": cut},
         "pairs_per_step": pairs_period,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "kernel_timing": "CUDA events around each kernel on the library's stream over %d further periods "

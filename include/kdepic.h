@@ -104,10 +104,11 @@ kde_status kde_sync(kde_ctx *ctx);
  *  - Truncation radius of the FP32 PIC step (see kde_set_truncation).  Unless a cut is
  *    fixed, the first FP32 pic_step of each key runs the deposit + field and a gather
  *    on the step's own sorted particles at the cuts 2^-24, 2^-20 and 2^-18 of each
- *    kernel's peak, timed by CUDA events; a cut is admitted when the node field and the
- *    particle fields match those of 2^-24 within 2.5e-6 relative L2, and is chosen when
- *    it is at least 3% faster than the best admitted cut so far.  Later steps with the
- *    key use it in their deposit and gather alike.
+ *    kernel's peak, in rounds timed by CUDA events; a cut is admitted when it changes
+ *    the results (a narrower window somewhere) and the node field and the particle
+ *    fields match those of 2^-24 within 2.5e-6 relative L2, and is chosen when it is at
+ *    least 3% faster than the best admitted cut so far.  Later steps with the key use
+ *    it in their deposit and gather alike.
  * Later calls with a tuned key use the stored choice.  Tuning synchronises the stream
  * once per new key and is skipped while the stream is being captured (and, for the
  * gather, when an output aliases an input).  Off by default.  kde_autotune_entries
@@ -479,6 +480,10 @@ kde_status kde_server_wait(kde_server *srv, int64_t ticket, double *latency_ms, 
  * when not available, e.g. for a cancelled request).  Intervals of requests
  * served by different slots that intersect show their work overlapping. */
 kde_status kde_server_wait_times(kde_server *srv, int64_t ticket, double *times);
+/* Like kde_server_wait_times (times may be null), and for a failed request the
+ * library's error message, NUL-terminated and truncated to msg_cap bytes, in msg
+ * (an empty string for a request that succeeded; msg may be null when msg_cap is 0). */
+kde_status kde_server_wait_msg(kde_server *srv, int64_t ticket, double *times, char *msg, int32_t msg_cap);
 /* Cancel a request that is still queued: it never runs and its wait returns
  * KDE_ECANCELED.  KDE_EBUSY once it has been admitted (running or done);
  * KDE_EINVAL for an unknown ticket. */

@@ -118,6 +118,7 @@ def load_library(path: str | None = None):
         "kde_server_submit": (S, [_P, ctypes.POINTER(_Request), ctypes.POINTER(_I64)]),
         "kde_server_wait": (S, [_P, _I64, _P, _P]),
         "kde_server_wait_times": (S, [_P, _I64, _P]),
+        "kde_server_wait_msg": (S, [_P, _I64, _P, ctypes.c_char_p, ctypes.c_int32]),
         "kde_server_cancel": (S, [_P, _I64]),
         "kde_server_stats": (S, [_P, _P]),
         "kde_server_destroy": (S, [_P]),
@@ -586,10 +587,11 @@ class Server:
         """kde_server_wait_times: (latency ms, service ms, argmin), plus the device-clock
         interval (start, end) in ms since the server started when times=True."""
         t = (ctypes.c_double * 4)()
-        rc = self.lib.kde_server_wait_times(self.h, int(ticket), ctypes.addressof(t))
+        msg = ctypes.create_string_buffer(512)
+        rc = self.lib.kde_server_wait_msg(self.h, int(ticket), ctypes.addressof(t), msg, 512)
         arrs, am = self.keep.pop(ticket)
         if rc != 0:
-            raise KdeError("kde_server_wait", rc, "request failed")
+            raise KdeError("kde_server_wait", rc, msg.value.decode(errors="replace") or "request failed")
         if times:
             return t[0], t[1], int(am[0]), (t[2], t[3])
         return t[0], t[1], int(am[0])

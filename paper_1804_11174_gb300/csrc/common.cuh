@@ -321,15 +321,18 @@ __device__ __forceinline__ void kde_pdl_wait() { asm volatile("griddepcontrol.wa
 __device__ __forceinline__ void kde_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // half-angle sine and cosine of the position code: theta / 2 = pi u / 2^32.
-// FP32: the code is split as u = hi 2^16 + lo so that both arguments of
-// sincospif are exact floats, then recombined by the angle-sum identity.
+// FP32: the code is split as u = hi 2^16 + lo; sincospif of the exact float
+// hi 2^-16 gives the angle of hi, and the angle-sum identity adds that of lo.
 __device__ __forceinline__ void kde_half_sincos(uint32_t u, float &s, float &c)
 {
-    float sh, ch, sl, cl;
+    // the low part is an angle d = pi lo 2^-32 < 4.8e-5: sin d = d (1 - d^2 / 6) and
+    // cos d = 1 - d^2 / 2 round to d and 1 in FP32 (d^2 / 2 < 1.2e-9 is below half an
+    // ulp of 1), so the angle sum needs no second sine/cosine evaluation
+    float sh, ch;
     sincospif((float)(u >> 16) * (1.0f / 65536.0f), &sh, &ch);
-    sincospif((float)(u & 0xFFFFu) * (1.0f / 4294967296.0f), &sl, &cl);
-    s = fmaf(sh, cl, ch * sl);
-    c = fmaf(ch, cl, -sh * sl);
+    const float d = (float)(u & 0xFFFFu) * (float)(KDE_PI / 4294967296.0);
+    s = fmaf(ch, d, sh);
+    c = fmaf(-sh, d, ch);
 }
 __device__ __forceinline__ void kde_half_sincos(uint32_t u, double &s, double &c)
 {

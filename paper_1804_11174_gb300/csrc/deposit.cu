@@ -650,6 +650,81 @@ __device__ __forceinline__ void depp_sweep(const DepSrc<float> &S, int n, int g_
     }
 }
 
+// narrow windows (R <= 32 NPL nodes): the records are kept in particle pairs, recAB[k] =
+// (a_2k, a_2k+1, b_2k, b_2k+1) and recW[k] = (w_2k, w_2k+1), so that one packed operation
+// serves two particles of the same node.  A lane owns NPL nodes (j, j + LG, ...) of its
+// group of LG lanes; the 32 / LG groups of a warp (slices) and the eight warps take
+// interleaved particle pairs.  Slice sums are combined by a fixed butterfly over the lane
+// bits above LG, warp sums in warp order; flush(r, a) receives each node's sum once.
+template <int LG, int NPL, typename F>
+__device__ __forceinline__ void depp_sweep_pairs(const DepSrc<float> &S, int n, int g_lo, int R, bool cosf,
+                                                 const float4 *recAB, const float2 *recW, float *part, F &&flush)
+{
+    constexpr int SL = 32 / LG;
+    constexpr int U = 4;
+    const int Ng = S.Ng;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j = lane & (LG - 1), sl = lane / LG;
+    kde_f2 SS[NPL], CC[NPL], acc[NPL];
+#pragma unroll
+    for (int t = 0; t < NPL; ++t) {
+        const int r = j + LG * t;
+        int g = g_lo + r;
+        g = g < 0 ? g + Ng : (g >= Ng ? g - Ng : g);
+        float sg, cg;
+        node_sc(S, r < R ? g : 0, sg, cg);
+        if (cosf) {
+            const float sf = 2.f * sg * cg, cf = (cg - sg) * (cg + sg);
+            SS[t] = kde_pk(sf, sf);
+            CC[t] = kde_pk(cf, cf);
+        } else {
+            SS[t] = kde_pk(sg, sg);
+            CC[t] = kde_pk(-cg, -cg);
+        }
+        acc[t] = kde_pk(0.f, 0.f);
+    }
+    const int np = (n + 1) >> 1;
+    const int k0 = (int)((int64_t)np * warp / DEPP_WARPS), k1 = (int)((int64_t)np * (warp + 1) / DEPP_WARPS);
+    if (cosf) {
+#pragma unroll U
+        for (int k = k0 + sl; k < k1; k += SL) {
+            const float4 ab = recAB[k];
+            const float2 w = recW[k];
+            const kde_f2 A = kde_pk(ab.x, ab.y), B = kde_pk(ab.z, ab.w), W2 = kde_pk(w.x, w.y);
+#pragma unroll
+            for (int t = 0; t < NPL; ++t) acc[t] = kde_fma2(kde_ex22(kde_fma2(SS[t], B, kde_mul2(CC[t], A))), W2, acc[t]);
+        }
+    } else {
+#pragma unroll U
+        for (int k = k0 + sl; k < k1; k += SL) {
+            const float4 ab = recAB[k];
+            const float2 w = recW[k];
+            const kde_f2 A = kde_pk(ab.x, ab.y), B = kde_pk(ab.z, ab.w), W2 = kde_pk(w.x, w.y);
+#pragma unroll
+            for (int t = 0; t < NPL; ++t) {
+                const kde_f2 sv = kde_fma2(SS[t], B, kde_mul2(CC[t], A));
+                acc[t] = kde_fma2(kde_ex2neg2(kde_mul2(sv, sv)), W2, acc[t]);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NPL; ++t) {
+        float a0, a1;
+        kde_upk(acc[t], a0, a1);
+        float a = a0 + a1;
+#pragma unroll
+        for (int o = LG; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (sl == 0) part[warp * DEPP_PART + j + LG * t] = a;
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += DEPP_THREADS) {
+        float a = 0.f;
+#pragma unroll
+        for (int w = 0; w < DEPP_WARPS; ++w) a += part[w * DEPP_PART + r];
+        flush(r, a);
+    }
+}
+
 // acc[g] = sum over the rows whose window covers node g of that row's entry; CTA b
 // takes nodes [32 b, 32 b + 32), lane l node 32 b + l, warp w rows w, w + 32, ...
 __global__ void __launch_bounds__(DEPP_RED_THREADS) deposit_rows_kernel(const long long *__restrict__ rows,
@@ -757,8 +832,12 @@ __global__ void __launch_bounds__(DEPP_THREADS, DEPP_MINB) deposit_persist_kerne
         g_lo = 0;
         R = Ng;
     }
-    // 4, 2 or 1 node pairs a lane: the widest that computes no extra nodes and whose
-    // slice sums fit the buffer
+    // windows of up to 128 nodes: records in particle pairs (depp_sweep_pairs); wider ones:
+    // 4, 2 or 1 node pairs a lane, the widest that computes no extra nodes and whose slice
+    // sums fit the buffer
+    const bool pairs = R <= 128;
+    float4 *recAB = rec;
+    float2 *recW = (float2 *)(rec + DEPP_SUB / 2);
     const int n64 = (R + 63) >> 6, n128 = (R + 127) >> 7, n256 = (R + 255) >> 8;
     const int P = (4 * n256 == n64 && (n256 >= DEPP_WARPS || n256 * 256 <= DEPP_PART))   ? 4
                   : (2 * n128 == n64 && (n128 >= DEPP_WARPS || n128 * 128 <= DEPP_PART)) ? 2
@@ -772,7 +851,7 @@ __global__ void __launch_bounds__(DEPP_THREADS, DEPP_MINB) deposit_persist_kerne
         // the particle records (a, b, w n) of the form in use, in groups of four particles a
         // thread whose inputs are loaded together (one global-load latency per group)
         constexpr int QB = 4;
-#pragma unroll
+#pragma unroll 1
         for (int p0 = 0; p0 < PER; p0 += QB) {
             uint32_t ru[QB];
             float rk[QB], rn[QB], rw[QB];
@@ -801,14 +880,34 @@ __global__ void __launch_bounds__(DEPP_THREADS, DEPP_MINB) deposit_persist_kerne
                 const float wn = rw[q] * S.coef * nm;
                 float sh, ch;
                 kde_half_sincos(ru[q], sh, ch);
+                float ra, rb, rw2;
                 if (cosf) {
                     const float K = (float)KDE_LOG2E * k;
-                    rec[t] = make_float4(K * ((ch - sh) * (ch + sh)), K * (2.f * sh * ch), wn * kde_ex2(-K), 0.f);
+                    ra = K * ((ch - sh) * (ch + sh));
+                    rb = K * (2.f * sh * ch);
+                    rw2 = wn * kde_ex2(-K);
                 } else {
                     const float beta = sqrtf((float)(2.0 * KDE_LOG2E) * k);
-                    rec[t] = make_float4(beta * sh, beta * ch, wn, 0.f);
+                    ra = beta * sh;
+                    rb = beta * ch;
+                    rw2 = wn;
+                }
+                if (pairs) {
+                    float *ab = (float *)recAB + (t >> 1) * 4 + (t & 1);
+                    ab[0] = ra;
+                    ab[2] = rb;
+                    ((float *)recW)[t] = rw2;
+                } else {
+                    rec[t] = make_float4(ra, rb, rw2, 0.f);
                 }
             }
+        }
+        if (pairs && (n & 1) && tid == 0) {
+            // the odd particle's partner: no weight (a finite exponent times zero)
+            float *ab = (float *)recAB + (n >> 1) * 4 + 1;
+            ab[0] = 0.f;
+            ab[2] = 0.f;
+            ((float *)recW)[n] = 0.f;
         }
         __syncthreads();
         auto flush = [&](int r, float a) {
@@ -816,7 +915,13 @@ __global__ void __launch_bounds__(DEPP_THREADS, DEPP_MINB) deposit_persist_kerne
             const long long v = (es >= -100 && es <= 100) ? fix_pow2(a, es) : __double2ll_rn(ldexp((double)a, es));
             row[r] = first ? v : __ldcg(&row[r]) + v;
         };
-        if (P == 4) depp_sweep<4>(S, n, g_lo, R, cosf, rec, part, flush);
+        if (pairs) {
+            if (R <= 8) depp_sweep_pairs<8, 1>(S, n, g_lo, R, cosf, recAB, recW, part, flush);
+            else if (R <= 16) depp_sweep_pairs<16, 1>(S, n, g_lo, R, cosf, recAB, recW, part, flush);
+            else if (R <= 32) depp_sweep_pairs<32, 1>(S, n, g_lo, R, cosf, recAB, recW, part, flush);
+            else if (R <= 64) depp_sweep_pairs<32, 2>(S, n, g_lo, R, cosf, recAB, recW, part, flush);
+            else depp_sweep_pairs<32, 4>(S, n, g_lo, R, cosf, recAB, recW, part, flush);
+        } else if (P == 4) depp_sweep<4>(S, n, g_lo, R, cosf, rec, part, flush);
         else if (P == 2) depp_sweep<2>(S, n, g_lo, R, cosf, rec, part, flush);
         else depp_sweep<1>(S, n, g_lo, R, cosf, rec, part, flush);
     }

@@ -25,6 +25,7 @@
 // beyond the estimate is charged to later admissions.
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <thread>
@@ -375,9 +376,9 @@ extern "C" kde_status kde_server_submit(kde_server *S, const kde_request *req, i
     return KDE_OK;
 }
 
-extern "C" kde_status kde_server_wait_times(kde_server *S, int64_t ticket, double *times)
+extern "C" kde_status kde_server_wait_msg(kde_server *S, int64_t ticket, double *times, char *msg, int32_t msg_cap)
 {
-    if (!S) return KDE_EINVAL;
+    if (!S || msg_cap < 0 || (msg_cap > 0 && !msg)) return KDE_EINVAL;
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->tickets.find(ticket);
     if (it == S->tickets.end()) return KDE_EINVAL;
@@ -391,8 +392,19 @@ extern "C" kde_status kde_server_wait_times(kde_server *S, int64_t ticket, doubl
         times[3] = t.dev_end;
     }
     kde_status rc = t.status;
+    if (msg_cap > 0) {
+        const std::string m = rc == KDE_OK ? std::string() : (t.err.empty() ? std::string("request failed") : t.err);
+        const size_t n = m.size() < (size_t)msg_cap - 1 ? m.size() : (size_t)msg_cap - 1;
+        memcpy(msg, m.data(), n);
+        msg[n] = 0;
+    }
     S->tickets.erase(ticket);
     return rc;
+}
+
+extern "C" kde_status kde_server_wait_times(kde_server *S, int64_t ticket, double *times)
+{
+    return kde_server_wait_msg(S, ticket, times, nullptr, 0);
 }
 
 extern "C" kde_status kde_server_wait(kde_server *S, int64_t ticket, double *latency_ms, double *service_ms)

@@ -290,12 +290,24 @@ static cudaError_t scatter_launch(kde_ctx *ctx, int nblk, int threads, size_t sm
 // tile geometry of a sort of N keys into nbins bins: wpb warps of `unit` keys a block
 static void sort_geometry(int64_t N, int nbins, int &wpb, int &unit, int &nblk)
 {
-    // warps per block: the scatter's warp-private histograms must fit the shared-memory budget
+    // the scatter keeps wpb warp-private histograms of nbins entries and the scan's tile
+    // totals (one per SCAN_TILE count entries) in at most 100 KB of shared memory, and the
+    // count table has at most SORT_MAX_COUNTS entries: fewer warps a block for many bins,
+    // then longer units until both hold
     wpb = 8;
     while (wpb > 1 && (size_t)wpb * nbins * 4 > 96 * 1024) wpb >>= 1;
     unit = 256;
-    while ((int64_t)nbins * ((N + (int64_t)wpb * unit - 1) / ((int64_t)wpb * unit)) > SORT_MAX_COUNTS) unit *= 2;
-    nblk = (int)((N + (int64_t)wpb * unit - 1) / ((int64_t)wpb * unit));
+    for (;;) {
+        const int64_t tile = (int64_t)wpb * unit;
+        const int64_t nb = (N + tile - 1) / tile;
+        const int64_t ncounts = (int64_t)nbins * nb;
+        const int64_t ntiles = (ncounts + SCAN_TILE - 1) / SCAN_TILE;
+        if (ncounts <= SORT_MAX_COUNTS && (int64_t)wpb * nbins * 4 + ntiles * 4 <= 100 * 1024) {
+            nblk = (int)nb;
+            return;
+        }
+        unit *= 2;
+    }
 }
 
 // the two count tables of the PIC step (one consumed by this step's sort while the
