@@ -58,11 +58,13 @@ __global__ void __launch_bounds__(POI_THREADS)
 // cluster of FIELD_C CTAs.  CTA q owns the node slice [q Ng / C, (q + 1) Ng / C):
 // its warps take the rows in turn (headers staged in shared memory), add every
 // row entry that falls in the slice into the slice's int64 sums (shared-memory
-// atomics: exact), then the CTAs read each other's slices through distributed
-// shared memory, so every CTA holds the whole charge density; the mean is removed
-// in FP64 (same order in every CTA) and each CTA solves the circular convolution
-// for its slice as poisson_kernel does.  Replaces the row reduction, the
-// accumulator round trip and the Poisson launch of the step.
+// atomics: exact).  Each CTA converts its slice to the total charge density in
+// FP64 and sums it; the slice sums are exchanged through distributed shared
+// memory and added in rank order (the same mean in every CTA); each CTA stores its
+// slice minus the mean in FP32, gathers every other slice through distributed
+// shared memory and solves the circular convolution for its own slice as
+// poisson_kernel does.  Replaces the row reduction, the accumulator round trip and
+// the Poisson launch of the step.
 // ---------------------------------------------------------------------------
 #define FIELD_C 8
 #define FIELD_THREADS 1024
@@ -79,8 +81,9 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
     __shared__ long long sacc[FIELD_MAXS];
     __shared__ float rt[KDE_MAX_NG];
     __shared__ float gs[KDE_MAX_NG];
+    __shared__ float rsl[FIELD_MAXS];  // the slice's total density minus the mean
     __shared__ double red[FIELD_THREADS / 32];
-    __shared__ double s_mean;
+    __shared__ double s_psum, s_mean;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = FIELD_THREADS / 32;
     constexpr int RB = 16;  // rows of a warp whose loads are in flight together
@@ -114,21 +117,12 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
             if (t) atomicAdd((unsigned long long *)&sacc[g - a], (unsigned long long)t);
         }
     }
-    cluster.sync();
-    // the whole density from every CTA's slice, the total charge density with its mean
-    // removed (FP64, the same order in every CTA)
-    auto total = [&](int g) -> double {
-        // the CTA whose slice [Ng o / C, Ng (o + 1) / C) holds node g
-        int o = (int)((int64_t)g * FIELD_C / Ng);
-        while (o > 0 && (int)((int64_t)Ng * o / FIELD_C) > g) --o;
-        while (o < FIELD_C - 1 && (int)((int64_t)Ng * (o + 1) / FIELD_C) <= g) ++o;
-        const long long *remote = cluster.map_shared_rank(sacc, o);
-        return background + charge * ((double)remote[g - (int)((int64_t)Ng * o / FIELD_C)] * acc_inv);
-    };
-    // FP64 is slow on this part: the sum runs on the warps that hold nodes, the mean on one warp
+    __syncthreads();
+    // the slice's total charge density in FP64 (FP64 is slow on this part: one value a
+    // thread, warp sums, the block sum in warp order on one warp)
     double local = 0.0;
-    for (int g = tid; g < Ng; g += FIELD_THREADS) local += total(g);
-    if (warp * 32 < Ng) {
+    for (int g = tid; g < b - a; g += FIELD_THREADS) local += background + charge * ((double)sacc[g] * acc_inv);
+    if (warp * 32 < b - a) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     }
@@ -138,11 +132,28 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
         double v = red[lane];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_mean = v / Ng;
+        if (lane == 0) s_psum = v;
+    }
+    cluster.sync();  // every slice sum is ready
+    if (tid == 0) {
+        // the mean from the slice sums in rank order: the same value in every CTA
+        double m = 0.0;
+        for (int o = 0; o < FIELD_C; ++o) m += *cluster.map_shared_rank(&s_psum, o);
+        s_mean = m / Ng;
     }
     __syncthreads();
     const double mean = s_mean;
-    for (int g = tid; g < Ng; g += FIELD_THREADS) rt[g] = (float)(total(g) - mean);
+    for (int g = tid; g < b - a; g += FIELD_THREADS)
+        rsl[g] = (float)(background + charge * ((double)sacc[g] * acc_inv) - mean);
+    cluster.sync();  // every slice's density is ready
+    // the whole density from every CTA's slice
+    for (int g = tid; g < Ng; g += FIELD_THREADS) {
+        // the CTA whose slice [Ng o / C, Ng (o + 1) / C) holds node g (Ng C < 2^31)
+        int o = g * FIELD_C / Ng;
+        while (o > 0 && Ng * o / FIELD_C > g) --o;
+        while (o < FIELD_C - 1 && Ng * (o + 1) / FIELD_C <= g) ++o;
+        rt[g] = cluster.map_shared_rank(rsl, o)[g - Ng * o / FIELD_C];
+    }
     cluster.sync();  // every remote read is done before any CTA moves on (and may exit)
     // E_j = sum_l G[(j - l) mod Ng] rho'_l for the slice: one node a warp at a time
     for (int j = a + warp; j < b; j += NW) {

@@ -238,8 +238,8 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherAr
     // limit with eight particles a lane, and other warps cover the load latency)
     float nm[GAT2_NP], kap[GAT2_NP];
     uint32_t uu[GAT2_NP];
-    int lo = 0x3fffffff, hi = -0x3fffffff;
-    float kmax = 0.f;
+    int lo = 0x3fffffff, hi = -0x3fffffff;  // the warp's first and last cell, then its window
+    float kmax = 0.f, kmin = (float)KDE_KAPPA_MAX;
 #pragma unroll
     for (int h = 0; h < GAT2_NP; ++h) {
         const int64_t j = base + h * 32 + lane;
@@ -254,10 +254,10 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherAr
         nm[h] = A.norm ? (valid ? A.norm[j] : 0.f) : (A.kappa ? kde_norm_tab(A.ntab, k) : A.norm_u);
         if (valid) {
             kmax = fmaxf(kmax, k);
+            kmin = fminf(kmin, k);
             const int cell = kde_cell(uu[h], Ng);
-            const int W = window_nodes_g(k, Ng, A.xcut);
-            lo = min(lo, cell - W);
-            hi = max(hi, cell + W);
+            lo = min(lo, cell);
+            hi = max(hi, cell);
         }
     }
 #pragma unroll
@@ -265,6 +265,14 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherAr
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    }
+    // one window for the warp: the widest kernel's reach around its cell range (it holds
+    // every particle's own window, since the widest kernel has the smallest kappa)
+    if (lo <= hi) {
+        const int W = window_nodes_g(kmin, Ng, A.xcut);
+        lo -= W;
+        hi += W;
     }
     if (lane == 0) kred[warp] = kmax;
     __syncthreads();
