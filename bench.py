@@ -396,6 +396,8 @@ def run_ours(args, rank, world, local_rank):
             sub["ad_schedule"] = {"error": str(e)}
 
     try:
+        if args.no_cpu_baseline:
+            raise RuntimeError("skipped (--no-cpu-baseline)")
         # one width-update period (CV + 50 PIC steps) of a 2^18-particle sample: 10-30 s of CPU work
         cpu_v, cpu_dt, cores, sample = oracle_sample(LANDAU["period"], 1 << 18)
         cpu = {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
@@ -468,8 +470,9 @@ PROFILED_TRAFFIC = {"deposit_persist_kernel": None, "gather2_kernel": None}
 
 def run_cv_sweep(args, rank, world, local_rank):
     """The CV-sweep workload: N = 2^18 positions from 0.7 U + 0.3 vonMises(pi, 20) on
-    [0, 2 pi), 64 candidates log-spaced in [1, 1e4]; one step = one kde_cv call (pair
-    sums, integral term, argmin, leave-one-out pass).  value = CV definition pairs/s."""
+    [0, 2 pi), 64 candidates log-spaced in [1, 1e4]; one step = one kde_cv call (the form
+    --cv names: pair sums and integral term, or the exact Fourier form, or the cost rule's
+    choice; argmin and leave-one-out pass).  value = CV definition pairs/s."""
     import torch
 
     import kde_inputs as I
@@ -486,14 +489,14 @@ def run_cv_sweep(args, rank, world, local_rank):
     ctx = kp.Context(local_rank)
     loo = torch.empty(N, device=dev)
     for _ in range(args.warmup):
-        ctx.cv(u, L, cand, loo=loo)
+        ctx.cv(u, L, cand, loo=loo, pairs=args.cv == "pairs", spectral=args.cv == "spectral")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ms = []
     ctx.profile_enable(True)
     for _ in range(args.steps):
         flush.zero_()
         t0 = time.perf_counter()
-        ctx.cv(u, L, cand, loo=loo)
+        ctx.cv(u, L, cand, loo=loo, pairs=args.cv == "pairs", spectral=args.cv == "spectral")
         ms.append(1e3 * (time.perf_counter() - t0))
     cv_ms, cv_n = ctx.profile_read("cv_pairs")
     _, launches = ctx.profile_read("all")
@@ -971,10 +974,11 @@ def main():
     ap.add_argument("--serve-cv-nmax-log2", type=int, default=17, help="serving: largest CV request (log2 N)")
     ap.add_argument("--ens-steps", type=int, default=20, help="ensemble: timed steps per replay")
     ap.add_argument("--quick", action="store_true", help="default line without the sub-records")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle's timed sample (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the gather's default tile shape")
     ap.add_argument("--cv", default="auto", choices=["auto", "pairs", "spectral"],
-                    help="CV evaluation in the width schedule: the library's cost rule (auto), O(N^2) pair "
-                         "sums or the exact Fourier form")
+                    help="CV evaluation (the Landau width schedule and the cv_sweep workload): the library's "
+                         "cost rule (auto), O(N^2) pair sums or the exact Fourier form")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

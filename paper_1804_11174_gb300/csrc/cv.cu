@@ -1022,59 +1022,97 @@ extern "C" kde_status kde_cv(kde_ctx *ctx, const uint32_t *u, const float *kappa
 // Silverman particle-wise widths (Sec. II.C)
 // ---------------------------------------------------------------------------
 #define AD_BLOCKS 256
-template <typename T>
-__global__ void adapt_apply_kernel(const float *loo, int64_t N, double xs, const double *kstar_dev, double kstar_h,
-                                   const double *part, double alpha, double kmin, double kmax, T *kappa_out,
-                                   T *norm_out, const float2 *ntab)
+// scalars of the Silverman step: K0 = (2 pi / L) norm(kappa*) (the kernel's value at its
+// own particle), kappa*, the log-mean of the pilot, and the FP32 forms of the pilot's
+// coefficients f = a loo + b, a = (n - 1) / n, b = K0 / n.  Worked out once by one
+// thread (the FP64 Bessel series is slow on this part), read by every thread after.
+struct AdaptPar {
+    double K0, ks, logg;
+    float a, b, ks_f, logg_f;
+};
+
+__global__ void adapt_par_kernel(int64_t N, double xs, const double *kstar_dev, double kstar_h, AdaptPar *P)
 {
-    __shared__ double s_logg, s_K0, s_ks;
-    if (threadIdx.x == 0) {
-        double ks = kstar_dev ? *kstar_dev : kstar_h;
-        double s = 0.0;
-        for (int b = 0; b < AD_BLOCKS; ++b) s += part[b];
-        s_logg = s / (double)N;
-        s_ks = ks;
-        s_K0 = xs * kde_norm(ks);
-    }
+    const double ks = kstar_dev ? *kstar_dev : kstar_h, n = (double)N;
+    const double K0 = xs * kde_norm(ks);
+    P->K0 = K0;
+    P->ks = ks;
+    P->a = (float)((n - 1.0) / n);
+    P->b = (float)(K0 / n);
+    P->ks_f = (float)ks;
+}
+
+// log-mean of the pilot: after the block partials of adapt_logsum_dev_kernel, one block
+// adds them by a fixed tree
+__global__ void __launch_bounds__(256) adapt_mean_kernel(const double *part, int64_t N, AdaptPar *P)
+{
+    __shared__ double red[AD_BLOCKS];
+    red[threadIdx.x] = part[threadIdx.x];
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const double n = (double)N;
-    double f = ((n - 1.0) * (double)loo[i] + s_K0) / n;
-    // lambda = (f/g)^-alpha, kappa = kappa* / lambda^2; FP32 widths take FP32 base-2 logarithms
-    // (the log-mean of adapt_logsum_dev_kernel<true> is in the same base), FP64 widths FP64 ones
-    double k;
-    if constexpr (sizeof(T) == 4)
-        k = s_ks * (double)exp2f((float)(2.0 * alpha) * (log2f((float)f) - (float)s_logg));
-    else
-        k = s_ks * exp(2.0 * alpha * (log(f) - s_logg));
-    k = k < kmin ? kmin : (k > kmax ? kmax : k);
-    kappa_out[i] = (T)k;
-    if (norm_out) {
-        // FP32 widths take the tabulated norm, FP64 widths the FP64 Bessel series
-        if constexpr (sizeof(T) == 4) norm_out[i] = (T)kde_norm_tab(ntab, (float)k);
-        else norm_out[i] = (T)kde_norm((double)(T)k);
+    for (int o = AD_BLOCKS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        P->logg = red[0] / (double)N;
+        P->logg_f = (float)P->logg;
     }
 }
 
-// the log-mean needs K0 = (2 pi / L) norm(kappa*) before kappa* is known on the host;
-// one thread of a block works it out (the FP64 Bessel series is slow here).  F32: base-2
-// logarithms in FP32 summed in FP64, for FP32 widths; otherwise natural FP64 logarithms
+template <typename T>
+__global__ void adapt_apply_kernel(const float *loo, int64_t N, const AdaptPar *__restrict__ P, double alpha,
+                                   double kmin, double kmax, T *kappa_out, T *norm_out, const float2 *ntab)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    // lambda = (f/g)^-alpha, kappa = kappa* / lambda^2; FP32 widths in FP32 with base-2
+    // logarithms (the log-mean of adapt_logsum_dev_kernel<true> is in the same base), FP64
+    // widths in FP64 with natural ones
+    T k;
+    if constexpr (sizeof(T) == 4) {
+        const float f = fmaf(P->a, loo[i], P->b);
+        float kf = P->ks_f * exp2f((float)(2.0 * alpha) * (log2f(f) - P->logg_f));
+        kf = kf < (float)kmin ? (float)kmin : (kf > (float)kmax ? (float)kmax : kf);
+        k = kf;
+    } else {
+        const double n = (double)N;
+        const double f = ((n - 1.0) * (double)loo[i] + P->K0) / n;
+        double kd = P->ks * exp(2.0 * alpha * (log(f) - P->logg));
+        kd = kd < kmin ? kmin : (kd > kmax ? kmax : kd);
+        k = kd;
+    }
+    kappa_out[i] = k;
+    if (norm_out) {
+        // FP32 widths take the tabulated norm, FP64 widths the FP64 Bessel series
+        if constexpr (sizeof(T) == 4) norm_out[i] = (T)kde_norm_tab(ntab, (float)k);
+        else norm_out[i] = (T)kde_norm((double)k);
+    }
+}
+
+// block partials of the pilot's log-sum.  F32: base-2 logarithms of the FP32 pilot,
+// added in FP32 in runs of 16 and the runs in FP64, for FP32 widths; otherwise natural
+// FP64 logarithms of the FP64 pilot
 template <bool F32>
-__global__ void adapt_logsum_dev_kernel(const float *loo, int64_t N, double xs, const double *kstar_dev, double kstar_h,
-                                        double *part)
+__global__ void adapt_logsum_dev_kernel(const float *loo, int64_t N, const AdaptPar *__restrict__ P, double *part)
 {
     __shared__ double red[256];
-    __shared__ double s_K0;
     const double n = (double)N;
-    if (threadIdx.x == 0) s_K0 = xs * kde_norm(kstar_dev ? *kstar_dev : kstar_h);
-    __syncthreads();
-    const double K0 = s_K0;
     double s = 0.0;
+    float fs = 0.f;
+    int run = 0;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)AD_BLOCKS * 256) {
-        const double f = ((n - 1.0) * (double)loo[i] + K0) / n;
-        s += F32 ? (double)log2f((float)f) : log(f);
+        if (F32) {
+            fs += log2f(fmaf(P->a, loo[i], P->b));
+            if (++run == 16) {
+                s += (double)fs;
+                fs = 0.f;
+                run = 0;
+            }
+        } else {
+            s += log(((n - 1.0) * (double)loo[i] + P->K0) / n);
+        }
     }
+    s += (double)fs;
     red[threadIdx.x] = s;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
@@ -1088,21 +1126,24 @@ kde_status kde_adapt_device(kde_ctx *ctx, const float *loo, int64_t N, double L,
                             double kstar_host, double alpha, double kmin, double kmax, void *kappa_out,
                             void *norm_out, bool f64)
 {
-    double *part = (double *)kde_ws(ctx, WS_CV_RED, AD_BLOCKS * 8);
+    double *part = (double *)kde_ws(ctx, WS_CV_RED, AD_BLOCKS * 8 + sizeof(AdaptPar) + 64);
     if (!part) return KDE_ENOMEM;
+    AdaptPar *P = (AdaptPar *)(part + AD_BLOCKS);
     const double xs = KDE_TWO_PI / L;
-    if (f64) adapt_logsum_dev_kernel<false><<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part);
-    else adapt_logsum_dev_kernel<true><<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part);
+    adapt_par_kernel<<<1, 1, 0, ctx->stream>>>(N, xs, kstar_dev, kstar_host, P);
+    KDE_LAUNCHED(ctx, "adapt_par_kernel");
+    if (f64) adapt_logsum_dev_kernel<false><<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, P, part);
+    else adapt_logsum_dev_kernel<true><<<AD_BLOCKS, 256, 0, ctx->stream>>>(loo, N, P, part);
     KDE_LAUNCHED(ctx, "adapt_logsum_dev_kernel");
+    adapt_mean_kernel<<<1, AD_BLOCKS, 0, ctx->stream>>>(part, N, P);
+    KDE_LAUNCHED(ctx, "adapt_mean_kernel");
     unsigned grid = (unsigned)((N + 255) / 256);
     if (f64)
-        adapt_apply_kernel<double><<<grid, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part, alpha, kmin,
-                                                                   kmax, (double *)kappa_out, (double *)norm_out,
-                                                                   ctx->norm_tab);
+        adapt_apply_kernel<double><<<grid, 256, 0, ctx->stream>>>(loo, N, P, alpha, kmin, kmax, (double *)kappa_out,
+                                                                   (double *)norm_out, ctx->norm_tab);
     else
-        adapt_apply_kernel<float><<<grid, 256, 0, ctx->stream>>>(loo, N, xs, kstar_dev, kstar_host, part, alpha, kmin,
-                                                                  kmax, (float *)kappa_out, (float *)norm_out,
-                                                                  ctx->norm_tab);
+        adapt_apply_kernel<float><<<grid, 256, 0, ctx->stream>>>(loo, N, P, alpha, kmin, kmax, (float *)kappa_out,
+                                                                  (float *)norm_out, ctx->norm_tab);
     KDE_LAUNCHED(ctx, "adapt_apply_kernel");
     return KDE_OK;
 }

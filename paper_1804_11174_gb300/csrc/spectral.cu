@@ -111,18 +111,53 @@ __global__ void __launch_bounds__(SP_THREADS)
         if (m0 + q <= Me) part[(size_t)blockIdx.x * M + (m0 + q - 1)] = make_double2(cr[q], ci[q]);
 }
 
-// S_m = sum over chunks in chunk order (modes up to *mlim when given)
-__global__ void spec_reduce_kernel(const double2 *part, int nchunks, int M, const int *mlim, double2 *S)
+// S_m = sum over the chunks (modes up to *mlim when given) in a fixed order, in two
+// stages: block (32 modes, chunk group g) -- warp w adds chunks c0 + w, c0 + w + 8, ...
+// of the group in order, then the eight warp sums in warp order -- and then the
+// SPR_G group sums in group order
+#define SPR_G 8
+__global__ void __launch_bounds__(256) spec_reduce_kernel(const double2 *part, int nchunks, int M, const int *mlim,
+                                                          double2 *gpart)
+{
+    __shared__ double2 ws[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Me = mlim ? min(M, *mlim) : M;
+    const int m = (int)blockIdx.x * 32 + lane;
+    const int c0 = (int)((int64_t)nchunks * blockIdx.y / SPR_G), c1 = (int)((int64_t)nchunks * (blockIdx.y + 1) / SPR_G);
+    double sr = 0.0, si = 0.0;
+    if (m < Me) {
+#pragma unroll 4
+        for (int c = c0 + warp; c < c1; c += 8) {
+            const double2 p = part[(size_t)c * M + m];
+            sr += p.x;
+            si += p.y;
+        }
+    }
+    ws[warp][lane] = make_double2(sr, si);
+    __syncthreads();
+    if (warp == 0 && m < Me) {
+        double2 t = ws[0][lane];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) {
+            t.x += ws[w][lane].x;
+            t.y += ws[w][lane].y;
+        }
+        gpart[(size_t)blockIdx.y * M + m] = t;
+    }
+}
+
+__global__ void spec_reduce2_kernel(const double2 *gpart, int M, const int *mlim, double2 *S)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= (mlim ? min(M, *mlim) : M)) return;
-    double sr = 0.0, si = 0.0;
-    for (int c = 0; c < nchunks; ++c) {
-        double2 p = part[(size_t)c * M + m];
-        sr += p.x;
-        si += p.y;
+    double2 t = gpart[m];
+#pragma unroll
+    for (int g = 1; g < SPR_G; ++g) {
+        const double2 p = gpart[(size_t)g * M + m];
+        t.x += p.x;
+        t.y += p.y;
     }
-    S[m] = make_double2(sr, si);
+    S[m] = t;
 }
 
 // one CTA per candidate (caller's order): Bessel ratios (sequential recurrence,
@@ -281,7 +316,8 @@ static kde_status spec_structure(kde_ctx *ctx, const uint32_t *u, int64_t N, int
     while (((N + chunk - 1) / chunk > 1024 || (N + chunk - 1) / chunk * M > (1 << 22)) && chunk < SP_MAXCHUNK)
         chunk *= 2;
     const int nchunks = (int)((N + chunk - 1) / chunk);
-    double2 *part = (double2 *)kde_ws(ctx, WS_SP_PART, (size_t)nchunks * M * sizeof(double2));
+    double2 *part = (double2 *)kde_ws(ctx, WS_SP_PART, (size_t)(nchunks + SPR_G) * M * sizeof(double2));
+    double2 *gpart = part + (size_t)nchunks * M;  // the chunk groups' sums
     double2 *S = (double2 *)kde_ws(ctx, WS_SP_S, (size_t)M * sizeof(double2));
     if (!part || !S) return KDE_ENOMEM;
     static bool attr = false;
@@ -298,8 +334,10 @@ static kde_status spec_structure(kde_ctx *ctx, const uint32_t *u, int64_t N, int
             u, N, chunk, M, mlim, part);
     }
     KDE_LAUNCHED(ctx, "spec_sf_kernel");
-    spec_reduce_kernel<<<(M + 255) / 256, 256, 0, ctx->stream>>>(part, nchunks, M, mlim, S);
+    spec_reduce_kernel<<<dim3((unsigned)((M + 31) / 32), SPR_G), 256, 0, ctx->stream>>>(part, nchunks, M, mlim, gpart);
     KDE_LAUNCHED(ctx, "spec_reduce_kernel");
+    spec_reduce2_kernel<<<(M + 255) / 256, 256, 0, ctx->stream>>>(gpart, M, mlim, S);
+    KDE_LAUNCHED(ctx, "spec_reduce2_kernel");
     *S_out = S;
     return KDE_OK;
 }
