@@ -51,6 +51,9 @@ enum WsSlot {
     WS_SORT_P1,
     WS_SORT_P2,
     WS_SORT_P3,
+    WS_SORT_P1B,  // the PIC step's second set of sorted widths, norms and labels
+    WS_SORT_P2B,
+    WS_SORT_P3B,
     WS_SORT_PERM,
     WS_NORM,
     WS_ACC,

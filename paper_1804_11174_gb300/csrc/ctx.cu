@@ -335,7 +335,8 @@ extern "C" kde_status kde_reserve(kde_ctx *ctx, int64_t N, int32_t Ng, int32_t n
     const size_t big[][2] = {
         {WS_SORT_COUNTS, (size_t)(1 << 22) * 8}, {WS_SORT_STARTS, 2048 * 4 + 64}, {WS_SORT_U, (size_t)Np * 4},
         {WS_SORT_P0, (size_t)Np * 8}, {WS_SORT_P1, (size_t)Np * 8}, {WS_SORT_P2, (size_t)Np * 8},
-        {WS_SORT_P3, (size_t)Np * 4}, {WS_SORT_PERM, (size_t)Np * 4}, {WS_NORM, (size_t)Np * 8},
+        {WS_SORT_P3, (size_t)Np * 4}, {WS_SORT_P1B, (size_t)Np * 8}, {WS_SORT_P2B, (size_t)Np * 8},
+        {WS_SORT_P3B, (size_t)Np * 4}, {WS_SORT_PERM, (size_t)Np * 4}, {WS_NORM, (size_t)Np * 8},
         {WS_ACC, (size_t)(n_cand > 0 ? n_cand : 1) * 8192 * 8 + 64}, {WS_GRID0, KDE_MAX_NG * 8},
         {WS_GRID1, KDE_MAX_NG * 8}, {WS_GREEN, 2 * KDE_MAX_NG * 8}, {WS_WMAX, 64}, {WS_PIC_E, (size_t)Np * 4}, {WS_PIC_LOO, (size_t)Np * 4},
         {WS_PIC_KS, 64}};

@@ -200,15 +200,22 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
     // the width update (CV) shares the sort slots; size them for it up front and
     // fetch the pointers again after every update, since a slot may be regrown
     const size_t npad = (size_t)((N + 255) / 256) * 256;
-    uint32_t *us = nullptr, *ids = nullptr;
-    T *vs = nullptr, *ks = nullptr, *ns = nullptr;
+    // two sets of sorted widths, norms and labels, used in turn: within a call the push
+    // writes them back to the state only on the call's last step, and each step sorts
+    // them from wherever the previous step left them
+    uint32_t *us = nullptr, *ids2[2] = {nullptr, nullptr};
+    T *vs = nullptr, *ks2[2] = {nullptr, nullptr}, *ns2[2] = {nullptr, nullptr};
     auto fetch_ws = [&]() -> bool {
         us = (uint32_t *)kde_ws(ctx, WS_SORT_U, npad * 4);
         vs = (T *)kde_ws(ctx, WS_SORT_P0, npad * sizeof(T));
-        ks = per ? (T *)kde_ws(ctx, WS_SORT_P1, npad * sizeof(T)) : nullptr;
-        ns = per ? (T *)kde_ws(ctx, WS_SORT_P2, npad * sizeof(T)) : nullptr;
-        ids = st->id ? (uint32_t *)kde_ws(ctx, WS_SORT_P3, npad * 4) : nullptr;
-        return us && vs && (!per || (ks && ns)) && (!st->id || ids);
+        bool ok = us && vs;
+        for (int b = 0; b < 2; ++b) {
+            ks2[b] = per ? (T *)kde_ws(ctx, b ? WS_SORT_P1B : WS_SORT_P1, npad * sizeof(T)) : nullptr;
+            ns2[b] = per ? (T *)kde_ws(ctx, b ? WS_SORT_P2B : WS_SORT_P2, npad * sizeof(T)) : nullptr;
+            ids2[b] = st->id ? (uint32_t *)kde_ws(ctx, b ? WS_SORT_P3B : WS_SORT_P3, npad * 4) : nullptr;
+            ok = ok && (!per || (ks2[b] && ns2[b])) && (!st->id || ids2[b]);
+        }
+        return ok;
     };
     if (!fetch_ws()) return KDE_ENOMEM;
     long long *acc = (long long *)kde_ws(ctx, WS_ACC, (size_t)Ng * 8);
@@ -233,6 +240,11 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
     // the FP32 gather + push adds the next step's sort counts; a step whose table was
     // overwritten since (first step of the call, CV or AD sorts) counts afresh
     bool counted = false;
+    // where the current widths, norms and labels are: the state's arrays, or one of the
+    // two sorted sets
+    const T *k_cur = per ? (const T *)st->kappa : nullptr;
+    const T *n_cur = per ? (const T *)norm_arr : nullptr;
+    const uint32_t *id_cur = st->id;
     for (int s = 0; s < n_steps; ++s) {
         const int64_t step = st->step;
         const bool update = sched && step % st->width_every == 0;
@@ -246,6 +258,8 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
                                       ks_dev));
             KDE_TRY(kde_adapt_device(ctx, loo, N, L, ks_dev, 0.0, st->alpha, st->kappa_min, st->kappa_max, st->kappa,
                                      norm_arr, sizeof(T) == 8));
+            k_cur = (const T *)st->kappa;  // the new widths and norms are in the state's arrays
+            n_cur = (const T *)norm_arr;
             if (!fetch_ws()) return KDE_ENOMEM;
         }
         if (adsched) {
@@ -283,14 +297,22 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
             if (st->h_target > 0.0) h_ad = st->adjust_rate * st->h_target + (1.0 - st->adjust_rate) * h_ad;
             st->kappa_uniform = 1.0 / (h_ad * h_ad);
         }
+        // this step's sorted set: the one the current arrays are not in
+        auto holds = [&](int b) {
+            return (per && (k_cur == ks2[b] || n_cur == ns2[b])) || (st->id && id_cur == ids2[b]);
+        };
+        const int wsel = holds(0) ? 1 : 0;
+        T *ks = ks2[wsel], *ns = ns2[wsel];
+        uint32_t *ids = ids2[wsel];
+        const bool last = s == n_steps - 1;
         SortPayload pl[4];
         int npl = 0;
         pl[npl++] = SortPayload{st->v, vs, (int)sizeof(T)};
         if (per) {
-            pl[npl++] = SortPayload{st->kappa, ks, (int)sizeof(T)};
-            pl[npl++] = SortPayload{norm_arr, ns, (int)sizeof(T)};
+            pl[npl++] = SortPayload{k_cur, ks, (int)sizeof(T)};
+            pl[npl++] = SortPayload{n_cur, ns, (int)sizeof(T)};
         }
-        if (st->id) pl[npl++] = SortPayload{st->id, ids, 4};
+        if (st->id) pl[npl++] = SortPayload{id_cur, ids, 4};
         {
             KdeRange r_("kdepic sort by cell");
             KDE_TRY(kde_sort_by_bin(ctx, st->u, N, Ng, us, pl, npl, nullptr, counted));
@@ -348,11 +370,12 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
         pa.v_in = vs;
         pa.u_out = st->u;
         pa.v_out = st->v;
-        pa.kappa_out = per ? st->kappa : nullptr;
+        // widths, norms and labels go back to the state only on the call's last step
+        pa.kappa_out = (per && last) ? st->kappa : nullptr;
         pa.norm_in = ns;
-        pa.norm_out = per ? norm_arr : nullptr;
+        pa.norm_out = (per && last) ? norm_arr : nullptr;
         pa.id_in = ids;
-        pa.id_out = st->id;
+        pa.id_out = last ? st->id : nullptr;
         pa.kick = (step == 0 && !(st->flags & PIC_NO_BACKSTEP)) ? 0.5 : 1.0;
         pa.qm_dt = st->qm * st->dt;
         pa.dt_scale = st->dt * 4294967296.0 / L;
@@ -378,6 +401,11 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
                                          KDE_TWO_PI / Ng, nullptr, nullptr, &pa));
         }
         counted = pa.counts != nullptr;
+        if (!last) {  // the sorted set now holds the current widths, norms and labels
+            k_cur = ks;
+            n_cur = ns;
+            id_cur = ids;
+        }
         st->step = step + 1;
     }
     return KDE_OK;

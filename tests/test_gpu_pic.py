@@ -283,3 +283,25 @@ def test_truncation_tuner_choice_is_used_by_the_step(kp):
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("width_every", [0, 3])
+def test_long_call_equals_single_steps(ctx, kp, width_every):
+    # within one call the sorted widths, norms and labels alternate between two workspace
+    # sets and reach the state only on the call's last step: one 7-step call must equal
+    # seven 1-step calls bit for bit, width updates (every 3 steps) included
+    L, Ng, dt, N = 4 * math.pi, 256, 0.1, 70_001
+    u, v = I.landau_load(46, N, L, 0.05, 1.0)
+    kw = dict(kappa=np.ones(N) * 3.0)
+    if width_every:
+        kw.update(width_every=width_every, cand=I.log_candidates(1.0, 1e4, 16), alpha=0.5, kappa_min=1.0,
+                  kappa_max=1e5)
+    a = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 7, **kw)
+    b = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 7, **kw)
+    ctx.pic_step(a, 7)
+    for _ in range(7):
+        ctx.pic_step(b, 1)
+    ctx.sync()
+    names = ("u", "v", "id", "energy", "kappa") + (("kappa_star",) if width_every else ())
+    for t in names:
+        assert torch.equal(getattr(a, t), getattr(b, t)), t
