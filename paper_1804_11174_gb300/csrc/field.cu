@@ -59,11 +59,10 @@ __global__ void __launch_bounds__(POI_THREADS)
 // its warps take the rows in turn (headers staged in shared memory), add every
 // row entry that falls in the slice into the slice's int64 sums (shared-memory
 // atomics: exact).  Each CTA converts its slice to the total charge density in
-// FP64 and sums it; the slice sums are exchanged through distributed shared
-// memory and added in rank order (the same mean in every CTA); each CTA stores its
-// slice minus the mean in FP32, gathers every other slice through distributed
-// shared memory and solves the circular convolution for its own slice as
-// poisson_kernel does.  Replaces the row reduction, the accumulator round trip and
+// FP64 and sums it; after one cluster barrier every CTA adds the slice sums in rank
+// order (the same mean in every CTA), gathers every slice minus the mean through
+// distributed shared memory and solves the circular convolution for its own slice
+// as poisson_kernel does.  Replaces the row reduction, the accumulator round trip and
 // the Poisson launch of the step.
 // ---------------------------------------------------------------------------
 #define FIELD_C 8
@@ -81,12 +80,11 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
     __shared__ long long sacc[FIELD_MAXS];
     __shared__ float rt[KDE_MAX_NG];
     __shared__ float gs[KDE_MAX_NG];
-    __shared__ float rsl[FIELD_MAXS];  // the slice's total density minus the mean
     __shared__ double red[FIELD_THREADS / 32];
     __shared__ double s_psum, s_mean;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = FIELD_THREADS / 32;
-    constexpr int RB = 16;  // rows of a warp whose loads are in flight together
+    constexpr int RB = 20;  // rows of a warp whose loads are in flight together (608 rows: one batch)
     const int q = (int)cluster.block_rank();
     const int a = (int)((int64_t)Ng * q / FIELD_C), b = (int)((int64_t)Ng * (q + 1) / FIELD_C);
     kde_pdl_wait();  // the rows come from the deposit before
@@ -118,10 +116,16 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
         }
     }
     __syncthreads();
-    // the slice's total charge density in FP64 (FP64 is slow on this part: one value a
-    // thread, warp sums, the block sum in warp order on one warp)
+    // the slice's total charge density in FP64, in place of its integer sums (the other
+    // CTAs read it there), and its sum: one value a thread, warp sums, the block sum in
+    // warp order on one warp (FP64 is slow on this part)
+    double *dsl = (double *)sacc;
     double local = 0.0;
-    for (int g = tid; g < b - a; g += FIELD_THREADS) local += background + charge * ((double)sacc[g] * acc_inv);
+    for (int g = tid; g < b - a; g += FIELD_THREADS) {
+        const double t = background + charge * ((double)sacc[g] * acc_inv);
+        dsl[g] = t;
+        local += t;
+    }
     if (warp * 32 < b - a) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
@@ -134,25 +138,24 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) s_psum = v;
     }
-    cluster.sync();  // every slice sum is ready
-    if (tid == 0) {
+    cluster.sync();  // every slice and slice sum is ready
+    if (warp == 0) {
         // the mean from the slice sums in rank order: the same value in every CTA
+        const double p = lane < FIELD_C ? *cluster.map_shared_rank(&s_psum, lane) : 0.0;
         double m = 0.0;
-        for (int o = 0; o < FIELD_C; ++o) m += *cluster.map_shared_rank(&s_psum, o);
-        s_mean = m / Ng;
+#pragma unroll
+        for (int o = 0; o < FIELD_C; ++o) m += __shfl_sync(0xffffffffu, p, o);
+        if (lane == 0) s_mean = m / Ng;
     }
     __syncthreads();
     const double mean = s_mean;
-    for (int g = tid; g < b - a; g += FIELD_THREADS)
-        rsl[g] = (float)(background + charge * ((double)sacc[g] * acc_inv) - mean);
-    cluster.sync();  // every slice's density is ready
-    // the whole density from every CTA's slice
+    // the whole density minus the mean from every CTA's slice
     for (int g = tid; g < Ng; g += FIELD_THREADS) {
         // the CTA whose slice [Ng o / C, Ng (o + 1) / C) holds node g (Ng C < 2^31)
         int o = g * FIELD_C / Ng;
         while (o > 0 && Ng * o / FIELD_C > g) --o;
         while (o < FIELD_C - 1 && Ng * (o + 1) / FIELD_C <= g) ++o;
-        rt[g] = cluster.map_shared_rank(rsl, o)[g - Ng * o / FIELD_C];
+        rt[g] = (float)(cluster.map_shared_rank(dsl, o)[g - Ng * o / FIELD_C] - mean);
     }
     cluster.sync();  // every remote read is done before any CTA moves on (and may exit)
     // E_j = sum_l G[(j - l) mod Ng] rho'_l for the slice: one node a warp at a time
