@@ -462,10 +462,11 @@ def ad_record(kp, ctx, dev, args, flush):
             "kappa_final": float(st4.c.kappa_uniform), "log_p_first_last": [float(lp[0]), float(lp[-1])]}
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels as
-# last captured by ncu on the Landau step (see profiles/); None until captured for the
-# current build of the kernel
-PROFILED_TRAFFIC = {"deposit_persist_kernel": None, "gather2_kernel": None}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels, from
+# one ncu capture of each on this Landau step (a PIC step after the tuner's runs; the gather
+# with its push on a step that is not a call's last); None once a kernel changes after its
+# capture
+PROFILED_TRAFFIC = {"deposit_persist_kernel": 12666624 + 0, "gather2_kernel": 16898048 + 256}
 
 
 def run_cv_sweep(args, rank, world, local_rank):
