@@ -77,59 +77,78 @@ __global__ void sort_count_kernel(const uint32_t *__restrict__ u, int64_t N, int
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) counts[(size_t)b * nblk + blockIdx.x] = hist[b];
 }
 
-// exclusive scan of each SCAN_TILE-element tile in place (coalesced rounds of
-// SCAN_THREADS elements, all loads issued first); the tile totals go to tot.  The
+// exclusive scan of each SCAN_TILE-element tile in place: each thread scans a run of
+// SCAN_TILE / SCAN_THREADS consecutive entries in registers (16-byte loads and stores
+// where aligned), then one block scan of the run totals; the tile totals go to tot.  The
 // scatter scans the (few) tile totals itself, so no block waits for another.
 __global__ void __launch_bounds__(SCAN_THREADS) sort_scan_kernel(unsigned int *a, int64_t n, unsigned int *tot,
                                                                  unsigned int *zero_out)
 {
-    constexpr int R = SCAN_TILE / SCAN_THREADS;
+    constexpr int R = SCAN_TILE / SCAN_THREADS;  // consecutive entries a thread
     __shared__ unsigned int wsum[SCAN_THREADS / 32];
     kde_pdl_wait();  // the counts come from the kernel before
     kde_pdl_trigger();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // block-wide exclusive scan of one value a thread; returns the prefix, adds the total to carry
-    auto block_scan = [&](unsigned int v, unsigned int &carry) -> unsigned int {
-        unsigned int inc = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        unsigned int woff = 0, total = 0;
-#pragma unroll
-        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
-            woff += w < warp ? wsum[w] : 0u;
-            total += wsum[w];
-        }
-        __syncthreads();
-        const unsigned int r = carry + woff + inc - v;
-        carry += total;
-        return r;
-    };
-    const int64_t t0 = (int64_t)blockIdx.x * SCAN_TILE;
+    const int64_t i0 = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)tid * R;
+    // vector loads and stores where the run is whole and 16-byte aligned
+    const bool vec = i0 + R <= n && ((uintptr_t)(a + i0) & 15u) == 0;
     unsigned int v[R];
+    if (vec) {
+#pragma unroll
+        for (int q = 0; q < R / 4; ++q) {
+            const uint4 w = reinterpret_cast<const uint4 *>(a + i0)[q];
+            v[4 * q] = w.x;
+            v[4 * q + 1] = w.y;
+            v[4 * q + 2] = w.z;
+            v[4 * q + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = i0 + r < n ? a[i0 + r] : 0u;
+    }
+    // the thread's run scanned in registers, then one block scan of the run totals
+    unsigned int run = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int64_t i = t0 + (int64_t)r * SCAN_THREADS + tid;
-        v[r] = i < n ? a[i] : 0u;
+        const unsigned int x = v[r];
+        v[r] = run;
+        run += x;
     }
-    unsigned int carry = 0;
+    unsigned int inc = run;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int64_t i = t0 + (int64_t)r * SCAN_THREADS + tid;
-        const unsigned int x = block_scan(v[r], carry);
-        if (i < n) a[i] = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
     }
-    if (tid == 0) tot[blockIdx.x] = carry;
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    unsigned int woff = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+        woff += w < warp ? wsum[w] : 0u;
+        total += wsum[w];
+    }
+    const unsigned int base = woff + inc - run;
+    if (vec) {
+#pragma unroll
+        for (int q = 0; q < R / 4; ++q)
+            reinterpret_cast<uint4 *>(a + i0)[q] =
+                make_uint4(base + v[4 * q], base + v[4 * q + 1], base + v[4 * q + 2], base + v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (i0 + r < n) a[i0 + r] = base + v[r];
+    }
+    if (tid == 0) tot[blockIdx.x] = total;
     // the next step's count table (added to by the PIC gather) starts from zero
     if (zero_out) {
+        if (i0 + R <= n && ((uintptr_t)(zero_out + i0) & 15u) == 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int64_t i = t0 + (int64_t)r * SCAN_THREADS + tid;
-            if (i < n) zero_out[i] = 0u;
+            for (int q = 0; q < R / 4; ++q) reinterpret_cast<uint4 *>(zero_out + i0)[q] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (i0 + r < n) zero_out[i0 + r] = 0u;
         }
     }
 }
