@@ -445,13 +445,15 @@ static kde_status gat2_launch(kde_ctx *ctx, const GatherArgs<float> &A)
 static kde_status gat2_variant(kde_ctx *ctx, const GatherArgs<float> &A, int v)
 {
     // all with four particles a lane: the warps' particle sets, and so their node windows
-    // and kernel forms, are the same in every variant.  (Eight particles a lane, which
-    // makes a Landau-size run one wave, measured 10% slower: the 64-register bound leaves
-    // the node loop less room.)
+    // and kernel forms, are the same in every variant.  Launch bounds of 6, 7 and 8 blocks
+    // an SM; the default 7 (71 registers) puts a Landau-size run (2048 blocks) in two
+    // nearly full waves and measured best or within 1% of best from whole-grid to
+    // five-node windows.  (Eight particles a lane, which makes a Landau-size run one
+    // wave, measured 10% slower: the 64-register bound leaves the node loop less room.)
     switch (v) {
     case 1: return gat2_launch<4, 4, 4, 8>(ctx, A);
     case 2: return gat2_launch<4, 8, 4, 6>(ctx, A);
-    default: return gat2_launch<4, 8, 4, 5>(ctx, A);
+    default: return gat2_launch<4, 8, 4, 7>(ctx, A);
     }
 }
 
