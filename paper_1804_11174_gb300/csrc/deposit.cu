@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(DEP_THREADS) deposit_chunk_kernel(DepSrc<T> S)
 // ---------------------------------------------------------------------------
 #define DEPP_THREADS 256
 #define DEPP_WARPS 8
-#define DEPP_MINB 3  // CTAs an SM (80 registers a thread); measured 7% faster than 4 at 64 registers
+#define DEPP_MINB 3  // CTAs an SM (80 registers a thread): 7% faster than 4 at 64 registers
 #define DEPP_SUB 2304  // records a sub-chunk: a 2^20-particle run has one sub-chunk a CTA
 #define DEPP_PART 512
 #define DEPP_RED_THREADS 1024

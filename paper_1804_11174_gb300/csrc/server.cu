@@ -94,7 +94,7 @@ static int64_t request_ws_bytes(const kde_request &r)
     if (r.kind == KDE_REQ_CV)
         return N * (32 + 5 * (int64_t)r.n_cand) + (int64_t)r.n_cand * 8192 * 10 + (4 << 20);
     // sort slots (two sets of widths and norms for PIC runs), and the persistent deposit's
-    // int64 rows: four CTAs an SM, up to 160 SMs
+    // int64 rows (an upper bound: 640 rows of Ng entries)
     return N * 56 + Ng * (64 + 640 * 8) + (16 << 20);
 }
 
