@@ -23,7 +23,8 @@
 #define SP_SUB 256
 #define SP_MAXM 16384
 #define SP_MAXCHUNK 16384
-#define SP_Q 4  // consecutive modes a thread in the structure factor
+#define SP_Q 8         // consecutive modes a thread in the structure factor
+#define SP_SF_THREADS 128  // threads of a structure-factor block (SP_Q SP_SF_THREADS modes)
 
 // modes needed for a width: A_m ~ exp(-m^2 / (2 kappa)) < 1e-17 beyond sqrt(78.4 kappa)
 __host__ __device__ inline int spec_modes(double kappa)
@@ -55,17 +56,17 @@ __device__ void spec_ratios(double kappa, int M, double *A)
 // a rotation with e^{i theta_j} (tabulated per particle in shared memory), which costs
 // four FP32 operations instead of a sincospi and adds at most an ulp or two per step.
 // The partials are laid out with stride M; modes above *mlim (when given) are skipped.
-__global__ void __launch_bounds__(SP_THREADS)
+__global__ void __launch_bounds__(SP_SF_THREADS)
     spec_sf_kernel(const uint32_t *__restrict__ u, int64_t N, int64_t chunk, int M, const int *mlim, double2 *part)
 {
     extern __shared__ __align__(8) uint32_t us[];
     float2 *e1 = (float2 *)(us + ((chunk + 1) & ~1LL));  // (cos, sin) of theta_j
     const int Me = mlim ? min(M, *mlim) : M;
-    const int mb = 1 + (int)blockIdx.y * SP_THREADS * SP_Q;
+    const int mb = 1 + (int)blockIdx.y * SP_SF_THREADS * SP_Q;
     if (mb > Me) return;  // the whole mode block is above the limit
     const int64_t j0 = (int64_t)blockIdx.x * chunk;
     const int n = (int)(N - j0 < chunk ? N - j0 : chunk);
-    for (int k = threadIdx.x; k < n; k += SP_THREADS) {
+    for (int k = threadIdx.x; k < n; k += SP_SF_THREADS) {
         const uint32_t uk = u[j0 + k];
         us[k] = uk;
         float s1, c1;
@@ -329,8 +330,8 @@ static kde_status spec_structure(kde_ctx *ctx, const uint32_t *u, int64_t N, int
     }
     {
         KdeProfScope _ps(ctx, PROF_SPECTRAL);
-        dim3 grid((unsigned)nchunks, (unsigned)((M + SP_THREADS * SP_Q - 1) / (SP_THREADS * SP_Q)));
-        spec_sf_kernel<<<grid, SP_THREADS, (size_t)((chunk + 1) & ~1LL) * 4 + (size_t)chunk * 8, ctx->stream>>>(
+        dim3 grid((unsigned)nchunks, (unsigned)((M + SP_SF_THREADS * SP_Q - 1) / (SP_SF_THREADS * SP_Q)));
+        spec_sf_kernel<<<grid, SP_SF_THREADS, (size_t)((chunk + 1) & ~1LL) * 4 + (size_t)chunk * 8, ctx->stream>>>(
             u, N, chunk, M, mlim, part);
     }
     KDE_LAUNCHED(ctx, "spec_sf_kernel");
