@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(GAT2_WARPS * 32, MINB) gather2_kernel(GatherAr
         // the push's inputs of four particles at a time first (one load latency per group;
         // the stores below alias nothing the loads read, but the compiler cannot know
         // that), then the stores
-        constexpr int HB = GAT2_NP < 4 ? GAT2_NP : 4;
+        constexpr int HB = GAT2_NP % 4 == 0 ? 4 : (GAT2_NP % 3 == 0 ? 3 : 2);
 #pragma unroll
         for (int h0 = 0; h0 < GAT2_NP; h0 += HB) {
         float vin[HB], kin[HB], nin[HB];
