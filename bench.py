@@ -466,7 +466,7 @@ def ad_record(kp, ctx, dev, args, flush):
 # one ncu capture of each on this Landau step (a PIC step after the tuner's runs; the gather
 # with its push on a step that is not a call's last); None once a kernel changes after its
 # capture
-PROFILED_TRAFFIC = {"deposit_persist_kernel": None, "gather2_kernel": 16898048 + 256}
+PROFILED_TRAFFIC = {"deposit_persist_kernel": 12666368 + 0, "gather2_kernel": 16898816 + 0}
 
 
 def run_cv_sweep(args, rank, world, local_rank):
