@@ -121,6 +121,11 @@ kde_status kde_set_autotune(kde_ctx *ctx, int32_t enable);
 kde_status kde_autotune_entries(const kde_ctx *ctx, int32_t *n_out);
 kde_status kde_autotune_table(const kde_ctx *ctx, int32_t cap, uint64_t *keys, int32_t *kinds, double *values,
                               int32_t *n_out);
+/* Stores n autotuner choices in the layout kde_autotune_table reports (a tuning table saved
+ * from an earlier run): later calls with those keys use them without tuning.  KDE_EINVAL, and
+ * nothing stored, unless every entry is a gather tile shape 0-2 or a cut exponent 24, 20 or 18. */
+kde_status kde_autotune_set(kde_ctx *ctx, int32_t n, const uint64_t *keys, const int32_t *kinds,
+                            const double *values);
 
 /* Truncation of the FP32 deposit and gather (Eq. kde, evaluated over a finite window;
  * no counterpart in the paper, whose sums run over all nodes).  Every FP32 deposit and

@@ -14,6 +14,7 @@ Function names follow the C entry points: `Context.deposit` calls
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -127,6 +128,7 @@ def load_library(path: str | None = None):
         "kde_set_launch_overlap": (S, [_P, ctypes.c_int32]),
         "kde_set_truncation": (S, [_P, ctypes.c_double]),
         "kde_autotune_table": (S, [_P, ctypes.c_int32, _P, _P, _P, _P]),
+        "kde_autotune_set": (S, [_P, ctypes.c_int32, _P, _P, _P]),
         "kde_set_wait_limit": (S, [_P, _I64]),
         "kde_autotune_entries": (S, [_P, _P]),
     }
@@ -351,6 +353,24 @@ class Context:
                         "value": int(v) if t == 0 else float(v)})
         return out
 
+    def autotune_save(self, path):
+        """Writes the autotuner's choices (autotune_table) to a JSON file."""
+        with open(path, "w") as f:
+            json.dump(self.autotune_table(), f, indent=1)
+
+    def autotune_load(self, path):
+        """kde_autotune_set from a JSON file written by autotune_save: the keys it lists are
+        not tuned again."""
+        with open(path) as f:
+            tab = json.load(f)
+        keys = np.array([e["Ng"] | (e["log2_N"] << 16) | (e["width_class"] << 24) for e in tab], dtype=np.uint64)
+        kinds = np.array([0 if e["kind"] == "gather_shape" else 1 for e in tab], dtype=np.int32)
+        vals = np.array([e["value"] for e in tab], dtype=np.float64)
+        n = len(tab)
+        self._check("kde_autotune_set", self.lib.kde_autotune_set(self.h, n, keys.ctypes.data if n else None,
+                                                                  kinds.ctypes.data if n else None,
+                                                                  vals.ctypes.data if n else None))
+
     def set_launch_overlap(self, on: bool = True):
         """kde_set_launch_overlap: programmatic dependent launches in the FP32 step chain."""
         self._check("kde_set_launch_overlap", self.lib.kde_set_launch_overlap(self.h, int(on)))
@@ -469,6 +489,44 @@ class PicState:
     @property
     def step(self) -> int:
         return self.c.step
+
+    _ARRAYS = ("u", "v", "kappa", "kappa_norm", "id", "energy", "kappa_star", "ad_log_p")
+
+    def save(self, path):
+        """Checkpoint the run to one .npz file: the particle arrays, the histories, the
+        candidate list and every scalar of the state (step counter, widths, the width
+        schedule's and the AD schedule's state).  Host-side copies only."""
+        out = {}
+        for name in self._ARRAYS:
+            t = getattr(self, name)
+            if t is not None:
+                out["a_" + name] = t.detach().cpu().numpy()
+        if self.cand is not None:
+            out["cand"] = self.cand
+        scal = {f: getattr(self.c, f) for f, t in _PicState._fields_ if t is not _P}
+        out["scalars"] = np.array(json.dumps(scal))
+        out["max_steps"] = np.array(self.max_steps)
+        np.savez(path, **out)
+
+    @classmethod
+    def load(cls, path, device="cuda:0"):
+        """The state saved by save(), on `device`; stepping it continues the saved run bit
+        for bit."""
+        torch = _torch()
+        z = np.load(path, allow_pickle=False)
+        a = {k[2:]: torch.from_numpy(z[k].copy()).to(device) for k in z.files if k.startswith("a_")}
+        scal = json.loads(str(z["scalars"]))
+        st = cls.__new__(cls)
+        st.u, st.v = a["u"], a["v"]
+        st.kappa, st.kappa_norm, st.id = a.get("kappa"), a.get("kappa_norm"), a.get("id")
+        st.energy, st.kappa_star, st.ad_log_p = a["energy"], a["kappa_star"], a["ad_log_p"]
+        st.cand = z["cand"] if "cand" in z.files else None
+        st.max_steps = int(z["max_steps"])
+        c = _PicState()
+        for f, v in scal.items():
+            setattr(c, f, v)
+        st.c = c
+        return st
 
 
 class Ensemble:

@@ -281,6 +281,23 @@ extern "C" kde_status kde_autotune_table(const kde_ctx *ctx, int32_t cap, uint64
     return KDE_OK;
 }
 
+extern "C" kde_status kde_autotune_set(kde_ctx *ctx, int32_t n, const uint64_t *keys, const int32_t *kinds,
+                                       const double *values)
+{
+    if (!ctx || n < 0 || (n > 0 && (!keys || !kinds || !values))) return KDE_EINVAL;
+    for (int32_t i = 0; i < n; ++i) {
+        const bool shape = kinds[i] == 0 && values[i] >= 0.0 && values[i] < 3.0 && values[i] == (double)(int)values[i];
+        const bool cut = kinds[i] == 1 && (values[i] == 24.0 || values[i] == 20.0 || values[i] == 18.0);
+        if (!shape && !cut)
+            return kde_fail(ctx, KDE_EINVAL, "kde_autotune_set: entry %d is neither a tile shape 0-2 nor a cut 24/20/18", i);
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        if (kinds[i] == 0) ctx->gat2_tuned[keys[i]] = (int)values[i];
+        else ctx->cut_tuned[keys[i]] = (float)values[i];
+    }
+    return KDE_OK;
+}
+
 extern "C" kde_status kde_set_launch_overlap(kde_ctx *ctx, int32_t enable)
 {
     if (!ctx) return KDE_EINVAL;

@@ -50,6 +50,7 @@ def test_null_context_is_rejected_on_the_host(kp):
     assert lib.kde_autotune_entries(None, ctypes.addressof(n)) == 1 and n.value == -1
     assert lib.kde_autotune_table(None, 0, None, None, None, ctypes.addressof(n)) == 1 and n.value == -1
     assert lib.kde_set_truncation(None, ctypes.c_double(20.0)) == 1
+    assert lib.kde_autotune_set(None, 0, None, None, None) == 1
     assert lib.kde_set_launch_overlap(None, 1) == 1
     assert lib.kde_sync(None) == 1
     assert lib.kde_destroy(None) == 1

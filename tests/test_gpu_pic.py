@@ -305,3 +305,61 @@ def test_long_call_equals_single_steps(ctx, kp, width_every):
     names = ("u", "v", "id", "energy", "kappa") + (("kappa_star",) if width_every else ())
     for t in names:
         assert torch.equal(getattr(a, t), getattr(b, t)), t
+
+
+@pytest.mark.parametrize("schedule", ["widths", "ad"])
+def test_checkpoint_file_resumes_bit_for_bit(ctx, kp, tmp_path, schedule):
+    # 12 steps in one go against 6 steps, a checkpoint file, a fresh state loaded from it
+    # and 6 more steps: the same run bit for bit (the particle arrays, the histories and
+    # the width or Anderson-Darling schedule's scalars all come back)
+    L, Ng, dt, N = 4 * math.pi, 256, 0.1, 40_000
+    u, v = I.landau_load(47, N, L, 0.05, 1.0)
+    cand = I.log_candidates(1.0, 1e3, 16)
+    if schedule == "widths":
+        kw = dict(kappa=np.ones(N), width_every=4, cand=cand, alpha=0.5, kappa_min=1.0, kappa_max=1e5)
+    else:
+        kw = dict(kappa_uniform=50.0, cand=cand, width_ad=True, cv_spectral=True)
+    a = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 12, **kw)
+    b = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 12, **kw)
+    ctx.pic_step(a, 12)
+    ctx.pic_step(b, 6)
+    ctx.sync()
+    path = tmp_path / "state.npz"
+    b.save(path)
+    c = kp.PicState.load(path, device=DEV)
+    assert c.step == 6
+    ctx.pic_step(c, 6)
+    ctx.sync()
+    for t in ("u", "v", "id", "energy", "kappa_star", "ad_log_p") + (("kappa",) if schedule == "widths" else ()):
+        assert torch.equal(getattr(a, t), getattr(c, t)), t
+    assert a.c.kappa_uniform == c.c.kappa_uniform and a.c.n_opt == c.c.n_opt
+
+
+def test_autotune_table_saved_and_loaded(kp, tmp_path):
+    # a context that loads a saved tuning table runs the same steps without tuning and gives
+    # the same run bit for bit
+    L, Ng, dt, N = 4 * math.pi, 512, 0.1, 30_000
+    u, v = I.landau_load(48, N, L, 0.05, 1.0)
+    k = I.log_uniform(48, I.STREAM_KAPPA, N, 20.0, 2e3)
+    a, b = kp.Context(0), kp.Context(0)
+    try:
+        a.set_autotune(True)
+        sa = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 3, kappa=k)
+        a.pic_step(sa, 3)
+        a.sync()
+        path = tmp_path / "tuned.json"
+        a.autotune_save(path)
+        b.autotune_load(path)
+        assert sorted(map(str, b.autotune_table())) == sorted(map(str, a.autotune_table()))
+        sb = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 3, kappa=k)
+        b.pic_step(sb, 3)  # tuning is off on b: the loaded table decides
+        b.sync()
+        for t in ("u", "v", "energy", "kappa"):
+            assert torch.equal(getattr(sa, t), getattr(sb, t)), t
+        bad = tmp_path / "bad.json"
+        bad.write_text('[{"Ng": 64, "log2_N": 10, "width_class": 0, "kind": "cut_log2", "value": 12.0}]')
+        with pytest.raises(kp.KdeError):  # not one of the tuner's cuts: nothing stored
+            b.autotune_load(bad)
+    finally:
+        a.close()
+        b.close()
