@@ -187,6 +187,23 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def over_ranks(x, dist, device, op="max"):
+    """x reduced over the ranks (the largest time, or the sum of work); x itself without a
+    process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replicas_rate(units_all_ranks, t_ms_slowest):
+    """Whole-job throughput of independent replicas: the units of every rank over the slowest
+    rank's time."""
+    return units_all_ranks / (t_ms_slowest * 1e-3)
+
+
 def timed(fn, flush, reps):
     """CUDA-event times (ms) of reps calls of fn on the current stream, L2 flushed before each."""
     import torch
@@ -314,13 +331,10 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    t_step = float(np.mean(step_ms))
-    if dist:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = over_ranks(float(np.mean(step_ms)), dist, dev, "max")
     pairs_period = float(np.mean(pairs))
-    value = world * pairs_period / (t_step * 1e-3)
+    pairs_all = over_ranks(pairs_period, dist, dev, "sum")
+    value = replicas_rate(pairs_all, t_step)
 
     # ---- e2e: the same period through the C ABI from pinned host buffers (pic_step_host:
     #      host -> device copies of u, v, kappa, id, the period, copies back, inside the call) ----
@@ -335,8 +349,8 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         ctx.pic_step_host(host, P)
     e_ms = timed(lambda: ctx.pic_step_host(host, P), flush, max(1, min(args.steps, 5)))
-    e_t = float(np.mean(e_ms))
-    e2e = {"value": world * pairs_period / (e_t * 1e-3), "unit": UNIT, "ms_per_step": e_t,
+    e_t = over_ranks(float(np.mean(e_ms)), dist, dev, "max")
+    e2e = {"value": replicas_rate(pairs_all, e_t), "unit": UNIT, "ms_per_step": e_t,
            "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16 + P * 8 * 2,
            "path": "pic_step_host (C ABI, pinned host buffers; copies inside the call)"}
 
