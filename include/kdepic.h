@@ -134,7 +134,8 @@ kde_status kde_autotune_set(kde_ctx *ctx, int32_t n, const uint64_t *keys, const
  * 3.6e-8 (c = 24, the default), 5.8e-7 (20), 2.3e-6 (18) and 9.2e-6 (16) of the total,
  * over all widths (worst near kappa = 6-9; von Mises tail integrals).  log2_cut = 0
  * returns to the default, with pic_step's cut chosen by the autotuner when it is on.
- * KDE_EINVAL unless log2_cut is 0 or in [16, 40].  FP64 paths always cut at 2^-64. */
+ * KDE_EINVAL unless log2_cut is 0 or in [16, 40].  FP64 paths always cut at 2^-64; the CV's
+ * pair sums and kde_deposit_noalloc (which takes no context) keep 2^-24. */
 kde_status kde_set_truncation(kde_ctx *ctx, double log2_cut);
 
 /* Launch overlap (no counterpart in the paper: a speed facility of this library).
