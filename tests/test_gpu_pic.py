@@ -363,3 +363,22 @@ def test_autotune_table_saved_and_loaded(kp, tmp_path):
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("Ng", [1, 2, 5, 7, 9, 13])
+def test_tiny_grids_one_step(ctx, kp, oracle, Ng):
+    # grids smaller than (or not a multiple of) the field kernel's eight node slices: empty
+    # slices, slices of one node, and the one- and two-node grids where no mode carries a field
+    L, dt, N = 4 * math.pi, 0.1, 1500
+    u, v = I.landau_load(5, N, L, 0.05, 1.0)
+    v32 = v.astype(np.float32)
+    st = make_state(kp, u, v32, L, Ng, dt, 2, kappa_uniform=3.0)
+    ctx.pic_step(st, 2)
+    ctx.sync()
+    r = oracle.pic_run(I.from_fixed(u, L), v32, L, Ng, dt, 2, kappa_u=3.0)
+    e, re = st.energy.cpu().numpy()[:2], r["energy"]
+    np.testing.assert_allclose(e, re, rtol=1e-5, atol=1e-12 * max(1.0, float(np.abs(re).max())))
+    x, vv, _ = unsort(st, L)
+    dxp = np.abs((x - r["x"] + L / 2) % L - L / 2)
+    assert dxp.max() <= 1e-6 * L
+    assert np.linalg.norm(vv - r["v"]) <= 1e-5 * np.linalg.norm(r["v"])
