@@ -471,9 +471,10 @@ kde_status kde_deposit_rows_f32(kde_ctx *ctx, const uint32_t *u, const float *ka
                                 float norm_u, int64_t N, int Ng, double coef, float w_u, double bound, DepRows *out,
                                 float xcut = 0.f);
 // the PIC step's field from those rows: rho_total = background + charge * rho with its
-// mean removed, E by the spectral or finite-difference Green's function (FP32 output)
+// mean removed (so the constant background drops out), E by the spectral or
+// finite-difference Green's function (FP32 output)
 kde_status kde_field_from_rows(kde_ctx *ctx, const long long *rows, const int2 *hdr, int G, int Ng, double L,
-                               double acc_inv, double charge, double background, bool fd, float *E_out);
+                               double acc_inv, double charge, bool fd, float *E_out);
 
 // Poisson solve of rho_total = background + charge * rho, rho given as a real
 // array or as int64 accumulators (value = acc * acc_inv)

@@ -58,21 +58,36 @@ __global__ void __launch_bounds__(POI_THREADS)
 // cluster of FIELD_C CTAs.  CTA q owns the node slice [q Ng / C, (q + 1) Ng / C):
 // its warps take the rows in turn (headers staged in shared memory), add every
 // row entry that falls in the slice into the slice's int64 sums (shared-memory
-// atomics: exact).  Each CTA converts its slice to the total charge density in
-// FP64 and sums it; after one cluster barrier every CTA adds the slice sums in rank
-// order (the same mean in every CTA), gathers every slice minus the mean through
-// distributed shared memory and solves the circular convolution for its own slice
-// as poisson_kernel does.  Replaces the row reduction, the accumulator round trip and
-// the Poisson launch of the step.
+// atomics: exact) and, on the way, the slice's total: each lane's partial sum t
+// is split into four 16-bit fields whose warp sums (one redux each) cannot
+// overflow, and recombined into the sums of t >> 32 and t mod 2^32, which stay
+// exact in int64 over the whole grid.  After one cluster barrier every CTA
+// gathers every node's sum through distributed shared memory as
+// rho'_g = charge acc_inv (n_g - M) with M the grid mean sum_l n_l / Ng to FP32
+// precision (the background is a constant and drops out; so does the tiny
+// remainder of the mean, which the zero-sum Green's function annihilates), and
+// solves the circular convolution for its own slice as poisson_kernel does.  No
+// step uses FP64, which is slow on this part.  The second cluster barrier, which
+// keeps every CTA's shared memory alive until the others have read it, is split:
+// a CTA arrives once its remote reads are done and waits only before it exits.
+// Replaces the row reduction, the accumulator round trip and the Poisson launch
+// of the step.
 // ---------------------------------------------------------------------------
 #define FIELD_C 8
 #define FIELD_THREADS 1024
 #define FIELD_MAXG 1024
 #define FIELD_MAXS ((KDE_MAX_NG + FIELD_C - 1) / FIELD_C)
 
+// 4-byte asynchronous copy global -> shared (completes by cp.async.wait_all)
+__device__ __forceinline__ void field_copy_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
 __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
-    field_rows_kernel(const long long *__restrict__ rows, const int2 *__restrict__ hdr, int G, int Ng, double acc_inv,
-                      double charge, double background, const float *__restrict__ Gf, float *E)
+    field_rows_kernel(const long long *__restrict__ rows, const int2 *__restrict__ hdr, int G, int Ng,
+                      float scale62, float inv_ng, const float *__restrict__ Gf, float *E)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -80,8 +95,7 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
     __shared__ long long sacc[FIELD_MAXS];
     __shared__ float rt[KDE_MAX_NG];
     __shared__ float gs[KDE_MAX_NG];
-    __shared__ double red[FIELD_THREADS / 32];
-    __shared__ double s_psum, s_mean;
+    __shared__ long long s_hl[2];  // the slice's sums of t >> 32 and of t mod 2^32
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = FIELD_THREADS / 32;
     constexpr int RB = 20;  // rows of a warp whose loads are in flight together (608 rows: one batch)
@@ -90,8 +104,10 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
     kde_pdl_wait();  // the rows come from the deposit before
     kde_pdl_trigger();
     for (int k = tid; k < G; k += FIELD_THREADS) sh[k] = hdr[k];
-    for (int g = tid; g < Ng; g += FIELD_THREADS) gs[g] = Gf[g];  // used after the row sums
+    // the Green's function arrives in shared memory while the rows are summed
+    for (int g = tid; g < Ng; g += FIELD_THREADS) field_copy_async4(&gs[g], &Gf[g]);
     for (int g = tid; g < b - a; g += FIELD_THREADS) sacc[g] = 0;
+    if (tid < 2) s_hl[tid] = 0;
     __syncthreads();
     // rows of warp w: w, w + 32, ...; for each row the slice nodes its window covers
     for (int k0 = warp; k0 < G; k0 += RB * NW) {
@@ -113,51 +129,50 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
 #pragma unroll
             for (int i = 0; i < RB; ++i) t += v[i];
             if (t) atomicAdd((unsigned long long *)&sacc[g - a], (unsigned long long)t);
+            // t = f3 2^48 + f2 2^32 + f1 2^16 + f0 (f3 signed, |f3| < 2^15; the others in
+            // [0, 2^16)): 32 lanes' sums of each field fit 32 bits
+            const unsigned long long ut = (unsigned long long)t;
+            const unsigned int f0 = __reduce_add_sync(0xffffffffu, (unsigned int)(ut & 0xffffu));
+            const unsigned int f1 = __reduce_add_sync(0xffffffffu, (unsigned int)((ut >> 16) & 0xffffu));
+            const unsigned int f2 = __reduce_add_sync(0xffffffffu, (unsigned int)((ut >> 32) & 0xffffu));
+            const int f3 = __reduce_add_sync(0xffffffffu, (int)(t >> 48));
+            if (lane == 0) {
+                const long long hi = (long long)f2 + (long long)f3 * 65536ll, lo = (long long)f0 + (long long)f1 * 65536ll;
+                if (hi) atomicAdd((unsigned long long *)&s_hl[0], (unsigned long long)hi);
+                if (lo) atomicAdd((unsigned long long *)&s_hl[1], (unsigned long long)lo);
+            }
         }
     }
-    __syncthreads();
-    // the slice's total charge density in FP64, in place of its integer sums (the other
-    // CTAs read it there), and its sum: one value a thread, warp sums, the block sum in
-    // warp order on one warp (FP64 is slow on this part)
-    double *dsl = (double *)sacc;
-    double local = 0.0;
-    for (int g = tid; g < b - a; g += FIELD_THREADS) {
-        const double t = background + charge * ((double)sacc[g] * acc_inv);
-        dsl[g] = t;
-        local += t;
-    }
-    if (warp * 32 < b - a) {
+    cluster.sync();  // every slice and slice sum is ready (the barrier also orders this CTA's atomics)
+    // the whole density minus the mean from every CTA's slice; lanes 0 .. C-1 of a warp
+    // fetch the CTAs' slice sums, issued together with the node loads, and add them in
+    // FP32 in a fixed order; n_g - M is exact in int64 and rounds once to FP32
+    for (int g0 = warp * 32; g0 < Ng; g0 += FIELD_THREADS) {
+        const int g = g0 + lane;
+        long long hi = 0, lo = 0, n = 0;
+        if (lane < FIELD_C) {
+            const long long *r = cluster.map_shared_rank(s_hl, lane);
+            hi = r[0];
+            lo = r[1];
+        }
+        if (g < Ng) {
+            // the CTA whose slice [Ng o / C, Ng (o + 1) / C) holds node g (Ng C < 2^31)
+            int o = g * FIELD_C / Ng;
+            while (o > 0 && Ng * o / FIELD_C > g) --o;
+            while (o < FIELD_C - 1 && Ng * (o + 1) / FIELD_C <= g) ++o;
+            n = cluster.map_shared_rank(sacc, o)[g - Ng * o / FIELD_C];
+        }
+        float s = fmaf(__ll2float_rn(hi), 4294967296.f, __ll2float_rn(lo));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const long long mean = __float2ll_rn(s * inv_ng);
+        // (n_g - M) charge acc_inv as (n_g - M) 2^-62 (exact) times charge acc_inv 2^62
+        if (g < Ng) rt[g] = __ll2float_rn(n - mean) * 0x1p-62f * scale62;
     }
-    if (lane == 0) red[warp] = local;
+    // this CTA's remote reads are done; it waits for the others' only before it exits
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
-        double v = red[lane];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_psum = v;
-    }
-    cluster.sync();  // every slice and slice sum is ready
-    if (warp == 0) {
-        // the mean from the slice sums in rank order: the same value in every CTA
-        const double p = lane < FIELD_C ? *cluster.map_shared_rank(&s_psum, lane) : 0.0;
-        double m = 0.0;
-#pragma unroll
-        for (int o = 0; o < FIELD_C; ++o) m += __shfl_sync(0xffffffffu, p, o);
-        if (lane == 0) s_mean = m / Ng;
-    }
-    __syncthreads();
-    const double mean = s_mean;
-    // the whole density minus the mean from every CTA's slice
-    for (int g = tid; g < Ng; g += FIELD_THREADS) {
-        // the CTA whose slice [Ng o / C, Ng (o + 1) / C) holds node g (Ng C < 2^31)
-        int o = g * FIELD_C / Ng;
-        while (o > 0 && Ng * o / FIELD_C > g) --o;
-        while (o < FIELD_C - 1 && Ng * (o + 1) / FIELD_C <= g) ++o;
-        rt[g] = (float)(cluster.map_shared_rank(dsl, o)[g - Ng * o / FIELD_C] - mean);
-    }
-    cluster.sync();  // every remote read is done before any CTA moves on (and may exit)
     // E_j = sum_l G[(j - l) mod Ng] rho'_l for the slice: one node a warp at a time
     for (int j = a + warp; j < b; j += NW) {
         float s2 = 0.f;
@@ -169,10 +184,12 @@ __global__ void __cluster_dims__(FIELD_C, 1, 1) __launch_bounds__(FIELD_THREADS)
         for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         if (lane == 0) E[j] = s2;
     }
+    __syncwarp();
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 kde_status kde_field_from_rows(kde_ctx *ctx, const long long *rows, const int2 *hdr, int G, int Ng, double L,
-                               double acc_inv, double charge, double background, bool fd, float *E_out)
+                               double acc_inv, double charge, bool fd, float *E_out)
 {
     if (G > FIELD_MAXG) return kde_fail(ctx, KDE_ENOTSUP, "field: %d deposit rows exceed %d", G, FIELD_MAXG);
     const float *Gf = (const float *)kde_green_table(ctx, Ng, L, fd, false);
@@ -180,7 +197,7 @@ kde_status kde_field_from_rows(kde_ctx *ctx, const long long *rows, const int2 *
     {
         KdeProfScope _ps(ctx, PROF_POISSON);
         KDE_CUDA(ctx, kde_launch(ctx, true, field_rows_kernel, dim3(FIELD_C), dim3(FIELD_THREADS), 0, rows, hdr, G, Ng,
-                                 acc_inv, charge, background, Gf, E_out),
+                                 (float)(charge * acc_inv * 0x1p62), 1.f / (float)Ng, Gf, E_out),
                  "field_rows_kernel");
     }
     KDE_LAUNCHED(ctx, "field_rows_kernel");

@@ -89,7 +89,7 @@ static kde_status tune_err(kde_ctx *ctx, const float *a, const float *b, int64_t
 
 static kde_status tune_cut(kde_ctx *ctx, const uint32_t *us, const float *ks, float kappa_u, const float *ns,
                            float norm_u, int64_t N, int Ng, double L, double coef, float w_u, double bound,
-                           double charge, double background, bool fd, float &cut)
+                           double charge, bool fd, float &cut)
 {
     const size_t ngp = ((size_t)Ng + 63) / 64 * 64, npd = ((size_t)N + 63) / 64 * 64;
     unsigned char *w = (unsigned char *)kde_ws(ctx, WS_TUNE, (2 * ngp + 2 * npd) * 4 + 4 * CUT_NCAND * 8);
@@ -106,8 +106,7 @@ static kde_status tune_cut(kde_ctx *ctx, const uint32_t *us, const float *ks, fl
     auto run = [&](int c, float *E, float *g) -> kde_status {
         DepRows dr{};
         KDE_TRY(kde_deposit_rows_f32(ctx, us, ks, kappa_u, ns, norm_u, N, Ng, coef, w_u, bound, &dr, kCutCand[c]));
-        KDE_TRY(kde_field_from_rows(ctx, dr.rows, dr.hdr, dr.G, Ng, L, 1.0 / kde_acc_scale(bound), charge, background,
-                                    fd, E));
+        KDE_TRY(kde_field_from_rows(ctx, dr.rows, dr.hdr, dr.G, Ng, L, 1.0 / kde_acc_scale(bound), charge, fd, E));
         return kde_gather_sorted<float>(ctx, us, ks, kappa_u, ns, norm_u, N, Eref, Ng, KDE_TWO_PI / Ng, g, nullptr,
                                         nullptr, kCutCand[c]);
     };
@@ -335,8 +334,8 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
                     if (cap == cudaStreamCaptureStatusNone) {
                         KdeRange r_("kdepic truncation tuner");
                         KDE_TRY(tune_cut(ctx, us, (const float *)ks, (float)st->kappa_uniform, (const float *)ns,
-                                         (float)norm_u, N, Ng, L, coef, (float)w_u, bound, st->charge,
-                                         st->background, fd, cut));
+                                         (float)norm_u, N, Ng, L, coef, (float)w_u, bound, st->charge, fd,
+                                         cut));
                         ctx->cut_tuned[key] = cut;
                     }
                 }
@@ -351,7 +350,7 @@ static kde_status pic_run(kde_ctx *ctx, pic_state *st, int n_steps)
             {
                 KdeRange r_("kdepic field (row sums + Poisson)");
                 KDE_TRY(kde_field_from_rows(ctx, dr.rows, dr.hdr, dr.G, Ng, L, 1.0 / kde_acc_scale(bound), st->charge,
-                                            st->background, fd, (float *)E));
+                                            fd, (float *)E));
             }
         } else {
             {
