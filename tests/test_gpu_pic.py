@@ -382,3 +382,29 @@ def test_tiny_grids_one_step(ctx, kp, oracle, Ng):
     dxp = np.abs((x - r["x"] + L / 2) % L - L / 2)
     assert dxp.max() <= 1e-6 * L
     assert np.linalg.norm(vv - r["v"]) <= 1e-5 * np.linalg.norm(r["v"])
+
+
+@pytest.mark.parametrize("case", ["g1000", "g4096_fd", "g3001_half_charge", "spike"])
+def test_large_grids_one_step(ctx, kp, oracle, case):
+    # the field kernel on grids up to the library's 4096 nodes: uneven node slices (1000, 3001),
+    # windows of a few nodes (per-particle widths up to 2e4), either sign of the charge, both
+    # Green's functions, and a spike of all particles in one place (node sums near the top of
+    # the fixed-point range, where the exact integer total matters most)
+    L, dt, N = 4 * math.pi, 0.05, 20000
+    Ng, fd, charge = {"g1000": (1000, False, 1.0), "g4096_fd": (4096, True, -1.0),
+                      "g3001_half_charge": (3001, False, -0.5), "spike": (256, False, -1.0)}[case]
+    u, v = I.landau_load(6, N, L, 0.05, 1.0)
+    if case == "spike":
+        u = np.full(N, u[N // 3], np.uint32)
+    v32 = v.astype(np.float32)
+    kap = I.log_uniform(6, I.STREAM_KAPPA, N, 50.0, 2e4).astype(np.float32)
+    st = make_state(kp, u, v32, L, Ng, dt, 2, kappa=kap, qm=charge, charge=charge, background=-charge, fd=fd)
+    ctx.pic_step(st, 2)
+    ctx.sync()
+    r = oracle.pic_run(I.from_fixed(u, L), v32, L, Ng, dt, 2, kappa=kap.astype(np.float64), qm=charge,
+                       charge=charge, background=-charge, fd=fd)
+    np.testing.assert_allclose(st.energy.cpu().numpy()[:2], r["energy"], rtol=1e-5)
+    x, vv, _ = unsort(st, L)
+    dxp = np.abs((x - r["x"] + L / 2) % L - L / 2)
+    assert dxp.max() <= 1e-6 * L
+    assert np.linalg.norm(vv - r["v"]) <= 1e-5 * np.linalg.norm(r["v"])
