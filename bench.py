@@ -48,19 +48,25 @@ def workload_name(w):
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 50 ms, each stamped on arrival.
+    Started before the timed region (the tool takes a moment to start); begin() and end()
+    mark the timed region, and stop() keeps the samples that arrived inside it (or, when
+    the region is shorter than the interval, the samples nearest to it, and says so)."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -69,7 +75,13 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def begin(self):
+        self.t0 = time.perf_counter()
+
+    def end(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
@@ -79,24 +91,39 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        return self.summarise(self.lines, self.t0, self.t1)
+
+    @staticmethod
+    def summarise(lines, t0=None, t1=None):
+        rows = []
+        for t, ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
             try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
+                rows.append((t, float(parts[0]), float(parts[1]), parts[4:8]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[4:8]):
+        if not rows:
+            return None
+        window = "whole run"
+        if t0 is not None and t1 is not None:
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            if inside:
+                rows, window = inside, "timed region"
+            else:  # a region shorter than the interval: the samples on either side of it
+                before = [r for r in rows if r[0] < t0][-1:]
+                after = [r for r in rows if r[0] > t1][:1]
+                if before or after:
+                    rows, window = before + after, "nearest to the timed region"
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, val in zip(names, r[3]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": float(np.median([r[1] for r in rows])), "sm_max_mhz": float(max(r[2] for r in rows)),
+                "reasons": sorted(reasons), "samples": len(rows), "window": window}
 
 
 # ---------------------------------------------------------------------------
@@ -293,6 +320,8 @@ def run_ours(args, rank, world, local_rank):
     st, u0, v0, cand = landau_state(kp, dev, w, w["seed"] + rank, P * (args.warmup + 2 * args.steps + 1),
                                     cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()  # before the warm-up: the sampler is running when the timed region starts
     for _ in range(args.warmup):
         ctx.pic_step(st, P)
     torch.cuda.synchronize()
@@ -306,8 +335,7 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
+    clocks.begin()
     ctx.profile_enable(False)  # no events between the kernels (they would serialise the launch overlap);
     #                            this also zeroes the launch counter
     wall0 = time.perf_counter()
@@ -319,6 +347,7 @@ def run_ours(args, rank, world, local_rank):
         pairs.append(2.0 * P * grid_window_pairs(st.kappa.cpu().numpy(), Ng, cut))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    clocks.end()
     _, launches = ctx.profile_read("all")
     # per-kernel durations: CUDA events around every kernel over the same number of
     # periods, run right after the timed ones on the same state
@@ -973,7 +1002,7 @@ def run_landau_stats(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="landau", choices=["landau", "cv_sweep", "serve", "ensemble", "shapes",

@@ -49,3 +49,26 @@ def test_landau_theory_root():
     assert landau_theory(2.0, k=0.25) == pytest.approx(-0.15336, abs=2e-5)  # depends on k v_th only
     g1, g2 = landau_theory(0.4, k=1.0), landau_theory(0.4, k=1.0, factor=0.98)
     assert math.isfinite(g1) and math.isfinite(g2) and g1 != g2
+
+
+def test_clock_samples_kept_for_the_timed_region():
+    # the sampler's summary from stamped nvidia-smi lines (fields: sm, max sm, power,
+    # active, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap)
+    from bench import ClockSampler
+
+    def line(sm, cap="Not Active", hw="Not Active"):
+        return "%d, 2070, 900.0, 0x0, %s, Not Active, Not Active, %s" % (sm, hw, cap)
+
+    lines = [(0.00, line(1200)), (0.05, line(2070)), (0.10, line(2070, cap="Active")),
+             (0.15, line(2055)), (0.20, line(900, hw="Active")), (0.25, "garbled")]
+    s = ClockSampler.summarise(lines, 0.04, 0.16)
+    assert s["window"] == "timed region" and s["samples"] == 3
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["reasons"] == ["sw_power_cap"]
+    # a region between two samples: the neighbours on either side
+    s = ClockSampler.summarise(lines, 0.16, 0.17)
+    assert s["window"] == "nearest to the timed region" and s["samples"] == 2
+    assert s["reasons"] == ["hw_slowdown"]
+    # no marks: every sample
+    s = ClockSampler.summarise(lines)
+    assert s["window"] == "whole run" and s["samples"] == 5
+    assert ClockSampler.summarise([(0.0, "garbled")]) is None
