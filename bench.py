@@ -36,12 +36,13 @@ sys.path.insert(0, ROOT)
 METRIC = "deposit+gather particle·node pairs/s; CV pairs/s; serve p50/p99 vs plain"
 UNIT = "pairs/s"
 
-LANDAU = dict(N=1 << 20, Ng=256, L=4 * math.pi, dt=0.1, period=50, n_cand=64, kmin_c=1.0, kmax_c=1e4, alpha=0.5,
-              kappa_min=1.0, kappa_max=1e5, seed=0)
+LANDAU = dict(N=1 << 20, Ng=256, L=4 * math.pi, dt=0.1, period=50, run_steps=1000, n_cand=64, kmin_c=1.0,
+              kmax_c=1e4, alpha=0.5, kappa_min=1.0, kappa_max=1e5, seed=0)
 
 
 def workload_name(w):
-    return "landau_damping N=2^20 Ng=256 dt=0.1 widths every 50 steps (CV over 64 candidates in [1,1e4], alpha=0.5)"
+    return ("landau_damping N=2^20 Ng=256 dt=0.1, 1000 steps from the initial load, widths every 50 steps "
+            "(CV over 64 candidates in [1,1e4], alpha=0.5)")
 
 
 # ---------------------------------------------------------------------------
@@ -312,26 +313,40 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device(dev))
 
     w = LANDAU
-    N, Ng, L, dt, P = w["N"], w["Ng"], w["L"], w["dt"], w["period"]
+    N, Ng, L, dt, P, RUN = w["N"], w["Ng"], w["L"], w["dt"], w["period"], w["run_steps"]
     ctx = kp.Context(local_rank)
     ctx.reserve(N, Ng, w["n_cand"])
-    ctx.set_autotune(not args.no_autotune)  # gather tile shape tuned in the first warm-up step
-    # each rank simulates its own realisation (independent replicas, weak scaling)
-    st, u0, v0, cand = landau_state(kp, dev, w, w["seed"] + rank, P * (args.warmup + 2 * args.steps + 1),
+    ctx.set_autotune(not args.no_autotune)  # gather shape and truncation cut tuned on the first step
+    # each rank simulates its own realisation (independent replicas, weak scaling).  A bench
+    # step is the whole 1000-step run from the initial load: every step repeats it from a
+    # snapshot of that load (restored outside the timed region), so the work is the same
+    # whatever the number of steps
+    st, u0, v0, cand = landau_state(kp, dev, w, w["seed"] + rank, RUN,
                                     cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
+    snap = st.snapshot()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()  # before the warm-up: the sampler is running when the timed region starts
-    for _ in range(args.warmup):
+    # first warm-up run period by period: the widths in force in each period (set by its
+    # first-step update) give the in-radius pair count of its 50 deposits and 50 gathers,
+    # at the truncation cut in force (the autotuner's choice for this key, else 2^-24)
+    cut, pairs = 24.0, []
+    for p in range(RUN // P):
         ctx.pic_step(st, P)
+        if p == 0:
+            for e in ctx.autotune_table():
+                if e["kind"] == "cut_log2" and (e["Ng"], e["log2_N"], e["width_class"]) == (
+                        Ng, N.bit_length() - 1, 0):
+                    cut = e["value"]
+        pairs.append(2.0 * P * grid_window_pairs(st.kappa.cpu().numpy(), Ng, cut))
+    energy_ref = st.energy.clone()
+    for _ in range(args.warmup - 1):
+        st.restore(snap)
+        ctx.pic_step(st, RUN)
     torch.cuda.synchronize()
-    # the truncation cut in force (the autotuner's choice for this key, else 2^-24)
-    cut = 24.0
-    for e in ctx.autotune_table():
-        if e["kind"] == "cut_log2" and (e["Ng"], e["log2_N"], e["width_class"]) == (Ng, N.bit_length() - 1, 0):
-            cut = e["value"]
 
-    # ---- the production width-update period: CV (cost rule) + Silverman + 50 PIC steps ----
+    # ---- the config's run: 20 production width-update periods (CV by the cost rule + Silverman
+    #      widths + 50 PIC steps), one pic_step call ----
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -339,20 +354,19 @@ def run_ours(args, rank, world, local_rank):
     ctx.profile_enable(False)  # no events between the kernels (they would serialise the launch overlap);
     #                            this also zeroes the launch counter
     wall0 = time.perf_counter()
-    step_ms, pairs = [], []
+    step_ms, repeat_ok = [], True
     for _ in range(args.steps):
-        step_ms += timed(lambda: ctx.pic_step(st, P), flush, 1)
-        # widths in force during the period (set by its first-step update), for the
-        # in-radius pair count of its 50 deposits and 50 gathers
-        pairs.append(2.0 * P * grid_window_pairs(st.kappa.cpu().numpy(), Ng, cut))
+        st.restore(snap)
+        step_ms += timed(lambda: ctx.pic_step(st, RUN), flush, 1)
+        repeat_ok = repeat_ok and bool(torch.equal(st.energy, energy_ref))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clocks.end()
     _, launches = ctx.profile_read("all")
-    # per-kernel durations: CUDA events around every kernel over the same number of
-    # periods, run right after the timed ones on the same state
+    # per-kernel durations: CUDA events around every kernel over one more run
+    st.restore(snap)
     ctx.profile_enable(True)
-    prof_ms = timed(lambda: ctx.pic_step(st, P), flush, args.steps)
+    prof_ms = timed(lambda: ctx.pic_step(st, RUN), flush, 1)
     prof = {k: ctx.profile_read(k) for k in ("deposit", "gather", "sort", "poisson", "spectral", "cv_pairs",
                                               "cv_grid", "cv_loo")}
     ctx.profile_enable(False)
@@ -361,26 +375,30 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     t_step = over_ranks(float(np.mean(step_ms)), dist, dev, "max")
-    pairs_period = float(np.mean(pairs))
-    pairs_all = over_ranks(pairs_period, dist, dev, "sum")
+    pairs_run = float(np.sum(pairs))
+    pairs_all = over_ranks(pairs_run, dist, dev, "sum")
     value = replicas_rate(pairs_all, t_step)
 
-    # ---- e2e: the same period through the C ABI from pinned host buffers (pic_step_host:
-    #      host -> device copies of u, v, kappa, id, the period, copies back, inside the call) ----
-    st_h, _, _, _ = landau_state(kp, dev, w, w["seed"] + rank, P * (args.warmup + 2 * args.steps + 1),
-                                 cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
-    host = kp.PicState(st_h.u.cpu().pin_memory(), st_h.v.cpu().pin_memory(), L, Ng, dt,
-                       kappa=st_h.kappa.cpu().pin_memory(), ids=st_h.id.cpu().pin_memory(), width_every=P,
+    # ---- e2e: the same run through the C ABI from pinned host buffers (pic_step_host: host ->
+    #      device copies of u, v, kappa, id, the run, copies back of them and of the histories,
+    #      inside the call) ----
+    sd = snap[0]
+    host = kp.PicState(sd["u"].cpu().pin_memory(), sd["v"].cpu().pin_memory(), L, Ng, dt,
+                       kappa=sd["kappa"].cpu().pin_memory(), ids=sd["id"].cpu().pin_memory(), width_every=P,
                        cand=cand, alpha=w["alpha"], kappa_min=w["kappa_min"], kappa_max=w["kappa_max"],
-                       max_steps=P * (args.warmup + args.steps + 1),
-                       cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
-    del st_h
-    for _ in range(args.warmup):
-        ctx.pic_step_host(host, P)
-    e_ms = timed(lambda: ctx.pic_step_host(host, P), flush, max(1, min(args.steps, 5)))
+                       max_steps=RUN, cv_spectral=args.cv == "spectral", cv_pairs=args.cv == "pairs")
+    hsnap = host.snapshot()
+    for _ in range(max(1, min(args.warmup, 2))):
+        host.restore(hsnap)
+        ctx.pic_step_host(host, RUN)
+    e_ms = []
+    for _ in range(max(1, min(args.steps, 5))):
+        host.restore(hsnap)
+        e_ms += timed(lambda: ctx.pic_step_host(host, RUN), flush, 1)
     e_t = over_ranks(float(np.mean(e_ms)), dist, dev, "max")
+    n_hist = sum(t is not None for t in (host.energy, host.kappa_star, host.ad_log_p))
     e2e = {"value": replicas_rate(pairs_all, e_t), "unit": UNIT, "ms_per_step": e_t,
-           "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16 + P * 8 * 2,
+           "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16 + n_hist * RUN * 8,
            "path": "pic_step_host (C ABI, pinned host buffers; copies inside the call)"}
 
     if rank != 0:
@@ -392,7 +410,7 @@ def run_ours(args, rank, world, local_rank):
     ex2_peak = ops_p / (ms_p * 1e-3)
     fm_ms, fm_ops = ctx.probe_fma(1 << 14)
     kr = {}
-    per_launch = pairs_period / (2.0 * P)  # in-radius pairs of one deposit (or one gather)
+    per_launch = pairs_run / (2.0 * RUN)  # in-radius pairs of one deposit (or one gather), run average
     for name, key in (("deposit_persist_kernel", "deposit"), ("gather2_kernel", "gather")):
         ms_k, n_k = prof[key]
         if n_k:
@@ -454,18 +472,21 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(w), "N": N, "Ng": Ng, "dt": dt, "pic_steps_per_step": P,
-                   "n_cand": w["n_cand"], "cv_form": cv_form,
-                   "value_def": "in-radius deposit+gather (particle, node) pairs of the period / period time",
+        "config": {"workload": workload_name(w), "N": N, "Ng": Ng, "dt": dt, "pic_steps_per_step": RUN,
+                   "width_period": P, "n_cand": w["n_cand"], "cv_form": cv_form,
+                   "value_def": "in-radius deposit+gather (particle, node) pairs of the 1000-step run / run time",
                    "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "gather_tile_shape": "default" if args.no_autotune else "autotuned",
-                   "truncation_cut_log2": cut},
-        "pairs_per_step": pairs_period,
-        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
-        "kernel_timing": "CUDA events around each kernel on the library's stream over %d further periods "
-                         "right after the timed ones (%.3f ms a period with the events, which serialise the "
-                         "launch overlap)" % (args.steps, float(np.mean(prof_ms))),
+                   "truncation_cut_log2": cut,
+                   "repeat": "every step restarts from a snapshot of the initial load (restored outside the "
+                             "timed region); its energy history equals the first run's bit for bit: %s" % repeat_ok},
+        "pairs_per_step": pairs_run,
+        "pairs_per_period": pairs,
+        "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]},
+        "kernel_timing": "CUDA events around each kernel on the library's stream over one further run right "
+                         "after the timed ones (%.3f ms with the events, which serialise the launch overlap)"
+                         % float(np.mean(prof_ms)),
         "wall_s": wall,
         "clocks": clk,
         "e2e": e2e,

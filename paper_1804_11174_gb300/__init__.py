@@ -492,6 +492,21 @@ class PicState:
 
     _ARRAYS = ("u", "v", "kappa", "kappa_norm", "id", "energy", "kappa_star", "ad_log_p")
 
+    def snapshot(self):
+        """Copies of the state's arrays (each on its own device) and of every scalar of the
+        state; restore() puts them back, after which stepping repeats the run bit for bit."""
+        arrs = {n: getattr(self, n).clone() for n in self._ARRAYS if getattr(self, n) is not None}
+        scal = {f: getattr(self.c, f) for f, t in _PicState._fields_ if t is not _P}
+        return arrs, scal
+
+    def restore(self, snap):
+        """Put back a snapshot() of this state (copies into the state's own tensors)."""
+        arrs, scal = snap
+        for n, t in arrs.items():
+            getattr(self, n).copy_(t)
+        for f, v in scal.items():
+            setattr(self.c, f, v)
+
     def save(self, path):
         """Checkpoint the run to one .npz file: the particle arrays, the histories, the
         candidate list and every scalar of the state (step counter, widths, the width

@@ -408,3 +408,21 @@ def test_large_grids_one_step(ctx, kp, oracle, case):
     dxp = np.abs((x - r["x"] + L / 2) % L - L / 2)
     assert dxp.max() <= 1e-6 * L
     assert np.linalg.norm(vv - r["v"]) <= 1e-5 * np.linalg.norm(r["v"])
+
+
+def test_snapshot_restore_repeats_the_run(ctx, kp):
+    # the bench repeats the Landau run from a snapshot of its load: a restored state steps
+    # bit for bit as the first time (width updates, histories and the step counter included)
+    L, Ng, dt, N, P = 4 * math.pi, 64, 0.1, 20000, 10
+    u, v = I.landau_load(8, N, L, 0.05, 1.0)
+    st = make_state(kp, u, v.astype(np.float32), L, Ng, dt, 3 * P, kappa=np.ones(N, np.float32),
+                    width_every=P, cand=I.log_candidates(1.0, 1e3, 16))
+    snap = st.snapshot()
+    ctx.pic_step(st, 3 * P)
+    first = {t: getattr(st, t).clone() for t in ("u", "v", "kappa", "id", "energy", "kappa_star")}
+    assert st.step == 3 * P
+    st.restore(snap)
+    assert st.step == 0
+    ctx.pic_step(st, 3 * P)
+    for t, x in first.items():
+        assert torch.equal(getattr(st, t), x), t
