@@ -3,15 +3,17 @@
 
 Default line (`--workload landau`): the Landau-damping run with particle-wise widths --
 N = 2^20 electrons, Ng = 256 nodes, L = 4 pi (k = 0.5), density 1 + 0.05 cos(kx),
-Maxwellian v_th = 1, dt = 0.1; every 50 steps the width is re-selected by leave-one-out
-CV over 64 candidates log-spaced in [1, 1e4] and Silverman's particle-wise widths
-(alpha = 0.5) are recomputed.  One benchmark step is one such 50-step period on the
-library's production path: the CV in the cheaper of its two exact forms (the library's
-cost rule takes the Fourier form here), the Silverman widths, then 50 x (sort, deposit,
-Poisson, gather + push + field energy).  All of it runs in libkdepic's CUDA kernels.
+Maxwellian v_th = 1, dt = 0.1, 1000 steps; every 50 steps the width is re-selected by
+leave-one-out CV over 64 candidates log-spaced in [1, 1e4] and Silverman's particle-wise
+widths (alpha = 0.5) are recomputed.  One benchmark step is the whole 1000-step run from the
+initial load (restored from a device snapshot before each step, outside the timed region) on
+the library's production path: per 50-step period the CV in the cheaper of its two exact
+forms (the library's cost rule takes the Fourier form here), the Silverman widths, then
+50 x (sort, deposit, Poisson, gather + push + field energy).  All of it runs in libkdepic's
+CUDA kernels.
 
-`value` = the in-radius (particle, node) pairs of the period's 50 deposits and 50 gathers
-divided by the period's device time.  Sub-records of the same line: the O(N^2) pair-sum
+`value` = the in-radius (particle, node) pairs of the run's 1000 deposits and 1000 gathers
+divided by the run's device time.  Sub-records of the same line: the O(N^2) pair-sum
 CV at the CV-sweep configuration (`cv_pairs`), the 256-realisation ensemble
 (`ensemble`), the 10,000-request serving stream (`serve`) and the Sec. II.D schedule
 (`ad_schedule`).  `--impl reference` times the FP64 CPU oracle on a bounded sample of the
