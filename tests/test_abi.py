@@ -56,3 +56,29 @@ def test_null_context_is_rejected_on_the_host(kp):
     assert lib.kde_destroy(None) == 1
     assert lib.kde_set_stream(None, None) == 1
     assert lib.kde_last_error(None) == b"null context"
+
+
+def test_pic_state_snapshot_restore_on_host(kp, tmp_path):
+    # the state's own copy helpers (no library call): a restored snapshot and a reloaded
+    # checkpoint give back every array and every scalar of the state
+    import numpy as np
+    import torch
+    N = 64
+    st = kp.PicState(torch.arange(N, dtype=torch.int32), torch.linspace(-1, 1, N), 4.0, 16, 0.1,
+                     kappa=torch.full((N,), 3.0), ids=torch.arange(N, dtype=torch.int32), width_every=5,
+                     cand=np.array([1.0, 10.0]), max_steps=8)
+    snap = st.snapshot()
+    st.u += 7
+    st.v.mul_(2)
+    st.kappa.fill_(9.0)
+    st.energy[3] = 1.5
+    st.c.step, st.c.n_opt, st.c.h_target = 6, 2, 0.25
+    st.save(tmp_path / "s.npz")
+    st.restore(snap)
+    assert st.c.step == 0 and st.c.n_opt == 0 and st.c.h_target == 0.0
+    assert torch.equal(st.u, torch.arange(N, dtype=torch.int32)) and torch.equal(st.v, torch.linspace(-1, 1, N))
+    assert torch.all(st.kappa == 3.0) and torch.all(st.energy == 0)
+    back = kp.PicState.load(tmp_path / "s.npz", device="cpu")
+    assert back.c.step == 6 and back.c.n_opt == 2 and back.c.h_target == 0.25
+    assert torch.equal(back.u, torch.arange(N, dtype=torch.int32) + 7) and float(back.energy[3]) == 1.5
+    assert back.c.width_every == 5 and back.c.Ng == 16 and back.c.N == N
